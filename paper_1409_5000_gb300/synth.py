@@ -1,0 +1,259 @@
+"""Seeded synthetic inputs: backgrounds plus an embedded target.
+
+This module is shared by the CUDA path's tests and benchmarks and by the
+FP64 oracle's tests.  It holds none of the method's arithmetic, only the
+graph generators (compiled from ``csrc/synth.c``) and the recipes that
+shape the workloads like the paper's experiments:
+
+* Erdos-Renyi backgrounds with a sparse target OR-ed into each of N
+  realisations (paper, "Multiple backgrounds scenario", eq. 5, Table 1);
+* ER / Watts-Strogatz / Barabasi-Albert single backgrounds with a planted
+  clique (paper, "Single background scenario", Table 3).
+
+Every graph is a simple undirected graph given as a symmetric CSR pattern
+(``row_ptr`` uint32[n+1], ``col`` uint32[nnz], rows sorted, no self-loops,
+no duplicates), i.e. the 0/1 adjacency matrix A of the paper's "Signal
+processing on graphs" section.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 14095000
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        from ._build import synth_lib_path, build_synth
+
+        path = synth_lib_path()
+        if not os.path.exists(path):
+            build_synth()
+        lib = ctypes.CDLL(path)
+        vp, u32, u64, i64, dbl = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                  ctypes.c_int64, ctypes.c_double)
+        lib.cbs_mix.restype = u64
+        lib.cbs_mix.argtypes = [u64, u64, u64]
+        lib.cbs_er_begin.restype = vp
+        lib.cbs_er_begin.argtypes = [u32, dbl, u64]
+        lib.cbs_ba_begin.restype = vp
+        lib.cbs_ba_begin.argtypes = [u32, u32, u64]
+        lib.cbs_ws_begin.restype = vp
+        lib.cbs_ws_begin.argtypes = [u32, u32, dbl, u64]
+        lib.cbs_empty_begin.restype = vp
+        lib.cbs_empty_begin.argtypes = [u32]
+        lib.cbs_add_edges.restype = ctypes.c_int
+        lib.cbs_add_edges.argtypes = [vp, vp, vp, u64]
+        lib.cbs_finish_count.restype = i64
+        lib.cbs_finish_count.argtypes = [vp]
+        lib.cbs_finish_fill.restype = ctypes.c_int
+        lib.cbs_finish_fill.argtypes = [vp, vp, vp]
+        lib.cbs_n.restype = u32
+        lib.cbs_n.argtypes = [vp]
+        lib.cbs_free.restype = None
+        lib.cbs_free.argtypes = [vp]
+        lib.cbs_target_edges.restype = i64
+        lib.cbs_target_edges.argtypes = [vp, u32, u32, ctypes.c_int, u64, vp, vp, u64]
+        lib.cbs_sample_nodes.restype = ctypes.c_int
+        lib.cbs_sample_nodes.argtypes = [u32, u32, u64, vp]
+        _LIB = lib
+    return _LIB
+
+
+def seed_for(config: int, realisation: int, salt: int = 0) -> int:
+    """Deterministic 64-bit seed for (config, realisation, salt)."""
+    return int(_lib().cbs_mix(SEED_BASE + salt, config, realisation))
+
+
+@dataclass
+class Graph:
+    """Symmetric CSR pattern of a simple undirected graph."""
+
+    n: int
+    row_ptr: np.ndarray  # uint32[n+1]
+    col: np.ndarray  # uint32[nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.row_ptr.astype(np.int64))
+
+
+@dataclass
+class Ensemble:
+    """N realisations sharing one embedded target (paper eq. 5)."""
+
+    graphs: list
+    target: np.ndarray  # uint32[k], sorted node indices of the target
+    target_edges: np.ndarray  # uint32[e, 2]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_max(self) -> int:
+        return max(g.n for g in self.graphs)
+
+
+def _finish(h, extra_edges=None) -> Graph:
+    lib = _lib()
+    if not h:
+        raise ValueError("graph generator rejected its arguments or ran out of memory")
+    if extra_edges is not None and len(extra_edges):
+        e = np.ascontiguousarray(extra_edges, dtype=np.uint32)
+        u = np.ascontiguousarray(e[:, 0])
+        v = np.ascontiguousarray(e[:, 1])
+        rc = lib.cbs_add_edges(h, u.ctypes.data, v.ctypes.data, len(u))
+        if rc != 0:
+            lib.cbs_free(h)
+            raise ValueError(f"cbs_add_edges failed ({rc})")
+    nnz = lib.cbs_finish_count(h)
+    if nnz < 0:
+        lib.cbs_free(h)
+        raise MemoryError("cbs_finish_count failed")
+    n = int(lib.cbs_n(h))
+    row_ptr = np.empty(n + 1, dtype=np.uint32)
+    col = np.empty(max(nnz, 1), dtype=np.uint32)[:nnz]
+    rc = lib.cbs_finish_fill(h, row_ptr.ctypes.data, col.ctypes.data if nnz else
+                             np.empty(1, np.uint32).ctypes.data)
+    if rc != 0:
+        raise ValueError("graph too large for uint32 row offsets")
+    return Graph(int(n), row_ptr, col)
+
+
+def er(n: int, p: float, seed: int, extra_edges=None) -> Graph:
+    """Erdos-Renyi G(n, p) (paper: ER backgrounds, Table 1)."""
+    return _finish(_lib().cbs_er_begin(n, float(p), seed), extra_edges)
+
+
+def ba(n: int, m: int, seed: int, extra_edges=None) -> Graph:
+    """Barabasi-Albert, m0 = m seed nodes (paper: BA background, Table 3)."""
+    return _finish(_lib().cbs_ba_begin(n, m, seed), extra_edges)
+
+
+def ws(n: int, k: int, p: float, seed: int, extra_edges=None) -> Graph:
+    """Watts-Strogatz small world (paper: SW backgrounds, Tables 2-3)."""
+    return _finish(_lib().cbs_ws_begin(n, k, float(p), seed), extra_edges)
+
+
+def from_edges(n: int, edges) -> Graph:
+    """Simple graph from an undirected edge list (duplicates collapse)."""
+    return _finish(_lib().cbs_empty_begin(n), np.asarray(edges, dtype=np.uint32).reshape(-1, 2))
+
+
+def sample_nodes(range_: int, k: int, seed: int) -> np.ndarray:
+    out = np.empty(k, dtype=np.uint32)
+    if _lib().cbs_sample_nodes(range_, k, seed, out.ctypes.data) != 0:
+        raise ValueError("k > range")
+    return out
+
+
+def target_edges(nodes: np.ndarray, extra: int, clique: bool, seed: int) -> np.ndarray:
+    """Target sub-graph on `nodes`: random tree + `extra` edges, or a clique."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint32)
+    k = len(nodes)
+    cap = max(1, k * (k - 1) // 2)
+    eu = np.empty(cap, dtype=np.uint32)
+    ev = np.empty(cap, dtype=np.uint32)
+    cnt = _lib().cbs_target_edges(nodes.ctypes.data, k, extra, int(clique), seed,
+                                  eu.ctypes.data, ev.ctypes.data, cap)
+    if cnt < 0:
+        raise ValueError("target edge generation failed")
+    return np.stack([eu[:cnt], ev[:cnt]], axis=1)
+
+
+def _threads() -> int:
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def er_ensemble(sizes, dbar: float, k: int, extra: int, config: int,
+                clique: bool = False, threads: int | None = None) -> Ensemble:
+    """N ER realisations (one per entry of `sizes`) sharing one target.
+
+    The target node set is drawn once, uniformly from [0, min(sizes)); its
+    edges (random tree + `extra` edges, or a clique) are OR-ed into every
+    realisation (paper, "Multiple backgrounds scenario").  p = dbar/(n-1).
+    """
+    sizes = [int(s) for s in sizes]
+    nodes = sample_nodes(min(sizes), k, seed_for(config, 0, salt=1))
+    tedges = target_edges(nodes, extra, clique, seed_for(config, 0, salt=2))
+
+    def one(r):
+        n = sizes[r]
+        return er(n, dbar / (n - 1), seed_for(config, r + 1), tedges)
+
+    with ThreadPoolExecutor(threads or _threads()) as ex:
+        graphs = list(ex.map(one, range(len(sizes))))
+    return Ensemble(graphs, nodes, tedges, dict(kind="er", dbar=dbar, config=config))
+
+
+def single_background(kind: str, n: int, k: int, config: int, clique: bool = True,
+                      extra: int = 0, dbar: float = 10.0, ba_m: int = 5, ws_k: int = 10,
+                      ws_p: float = 0.1) -> Ensemble:
+    """One ER / WS / BA background with a planted target (paper Table 3)."""
+    nodes = sample_nodes(n, k, seed_for(config, 0, salt=1))
+    tedges = target_edges(nodes, extra, clique, seed_for(config, 0, salt=2))
+    s = seed_for(config, 1)
+    if kind == "er":
+        g = er(n, dbar / (n - 1), s, tedges)
+    elif kind == "ba":
+        g = ba(n, ba_m, s, tedges)
+    elif kind == "ws":
+        g = ws(n, ws_k, ws_p, s, tedges)
+    else:
+        raise ValueError(kind)
+    return Ensemble([g], nodes, tedges, dict(kind=kind, config=config))
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes.  Shapes follow the paper's experiments, scaled up; the
+# exact parameters are those of the project's five benchmark configurations.
+# ---------------------------------------------------------------------------
+
+def er_ensemble_small():
+    """10 x ER(500, p=0.016) + 15-node tree(+8) target; m=20, k=15."""
+    ens = er_ensemble([500] * 10, 0.016 * 499, 15, 8, config=1)
+    ens.meta.update(m=20, k=15)
+    return ens
+
+
+def single_clique_100k(kind: str):
+    """ER(d=10) / BA(m=5) / WS(k=10,p=0.1) at n=1e5 + 12-clique; m=30, k=12."""
+    ens = single_background(kind, 100_000, 12, config=2 + {"er": 0, "ba": 10, "ws": 20}[kind],
+                            clique=True, dbar=10.0, ba_m=5, ws_k=10, ws_p=0.1)
+    ens.meta.update(m=30, k=12)
+    return ens
+
+
+def er_ensemble_uneven(n_inst: int = 256, n_lo: int = 20_000, n_hi: int = 400_000,
+                       dbar: float = 20.0, k: int = 30, extra: int = 15, config: int = 3):
+    """N ER realisations, n ~ U[n_lo, n_hi] per instance, dbar=20, 30-node
+    tree(+15) target on [0, n_lo); m=25, k=30."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(config, 0, salt=3)))
+    sizes = rng.integers(n_lo, n_hi + 1, size=n_inst)
+    ens = er_ensemble(sizes, dbar, k, extra, config=config)
+    ens.meta.update(m=25, k=k)
+    return ens
+
+
+def ba_clique_large(n: int = 10_000_000, m_ba: int = 8, k: int = 20, config: int = 4):
+    """BA(n, m=8) + 20-clique; m=40, k=20."""
+    ens = single_background("ba", n, k, config=config, clique=True, ba_m=m_ba)
+    ens.meta.update(m=40, k=k)
+    return ens
+
+
+def er_ensemble_grad(n_inst: int = 64, n: int = 100_000, dbar: float = 16.0, k: int = 25,
+                     extra: int = 10, config: int = 5):
+    """N ER(1e5, dbar=16) + 25-node tree(+10) target; m=30, k=25."""
+    ens = er_ensemble([n] * n_inst, dbar, k, extra, config=config)
+    ens.meta.update(m=30, k=k)
+    return ens

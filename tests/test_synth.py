@@ -1,0 +1,84 @@
+"""Seeded generators: structure, determinism, and the paper's target shape."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1409_5000_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _check_simple(g):
+    rp = g.row_ptr.astype(np.int64)
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == len(g.col)
+    assert np.all(g.col < g.n)
+    for i in range(g.n):
+        r = g.col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(r.astype(np.int64)) > 0)  # sorted, no duplicates
+        assert not np.any(r == i)  # no self-loops
+    # symmetry
+    src = np.repeat(np.arange(g.n), np.diff(rp))
+    a = set(zip(src.tolist(), g.col.tolist()))
+    assert all((v, u) in a for (u, v) in a)
+
+
+@pytest.mark.parametrize("kind", ["er", "ba", "ws"])
+def test_generators_simple_and_deterministic(kind):
+    mk = {"er": lambda s: synth.er(300, 0.03, s), "ba": lambda s: synth.ba(300, 3, s),
+          "ws": lambda s: synth.ws(300, 6, 0.2, s)}[kind]
+    g1, g2, g3 = mk(11), mk(11), mk(12)
+    _check_simple(g1)
+    assert np.array_equal(g1.row_ptr, g2.row_ptr) and np.array_equal(g1.col, g2.col)
+    assert not (np.array_equal(g1.row_ptr, g3.row_ptr) and np.array_equal(g1.col, g3.col))
+
+
+def test_degree_conventions():
+    g = synth.ba(2000, 4, 1)
+    assert g.nnz == 2 * 4 * (2000 - 4)  # m edges per new node
+    g = synth.ws(1000, 10, 0.1, 1)
+    assert g.nnz == 1000 * 10  # rewiring keeps the edge count
+    g = synth.er(4000, 10 / 3999, 1)
+    assert abs(g.nnz / 4000 - 10) < 0.3  # mean degree dbar = p (n-1)
+
+
+def test_target_planted_in_every_realisation():
+    ens = synth.er_ensemble([200, 300, 250], 4.0, 10, 3, config=77)
+    assert len(ens.target_edges) == 9 + 3
+    assert np.all(ens.target < 200)
+    for g in ens.graphs:
+        rp = g.row_ptr
+        for u, v in ens.target_edges:
+            assert v in g.col[rp[u]:rp[u + 1]]
+
+
+def test_clique_target():
+    nodes = synth.sample_nodes(100, 12, 5)
+    e = synth.target_edges(nodes, 0, True, 1)
+    assert len(e) == 12 * 11 // 2
+
+
+def test_paper_sparse_target_shape():
+    """A random tree on 20 nodes plus 2 extra edges has the paper's stated
+    average degree 2.1 and density 0.11."""
+    vals = {}
+    with open(os.path.join(GOLDEN, "paper_sparse_target.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    k = int(vals["nodes"])
+    e = synth.target_edges(np.arange(k, dtype=np.uint32), 2, False, 3)
+    n_e = len(e)
+    assert round(2 * n_e / k, 2) == vals["avg_degree"]
+    assert round(n_e / (k * (k - 1) / 2), 2) == vals["density"]
+    # connected (a spanning tree is inside)
+    g = synth.from_edges(k, e)
+    seen, stack = {0}, [0]
+    while stack:
+        u = stack.pop()
+        for v in g.col[g.row_ptr[u]:g.row_ptr[u + 1]]:
+            if int(v) not in seen:
+                seen.add(int(v))
+                stack.append(int(v))
+    assert len(seen) == k
