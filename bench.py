@@ -1,0 +1,381 @@
+"""Benchmark: summed Lanczos total communicability + top-k on one GB300.
+
+One step = one pass of the hot path over one batch of synthetic input:
+the Krylov (Lanczos) approximation of e^{A_r} 1 for every realisation r
+(paper eq. 4 and its Krylov evaluation), the ensemble sum (eq. 5) and the
+top-k selection, i.e. cb_ensemble_scores + cb_topk.
+
+Default workload: 256 Erdos-Renyi realisations with n drawn uniformly from
+[20 000, 400 000] (mean degree 20, ~1.0e9 directed CSR entries in total), a
+30-node sparse target (random tree + 15 edges) OR-ed into each, Krylov depth
+m = 25, FP32 Krylov vectors with FP64 scalars and sums, top-30.
+
+Metric: edge-Lanczos-steps/s = (sum_r nnz_r * m) / time per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload ensemble|large|small] [--skip-extra]
+With N > 1 it expects torchrun (one process per GPU); every rank runs the
+same workload as an independent replica (weak scaling, no collective on the
+data path) and rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import os
+
+# The oracle (CPU baseline / reference arm) is timed single-threaded.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1409_5000_gb300 import synth  # noqa: E402
+
+METRIC = "edge-Lanczos-steps/s"
+UNIT = "edge*steps/s"
+
+
+def workload(name):
+    if name == "ensemble":
+        ens = synth.er_ensemble_uneven()
+        desc = dict(workload="er-ensemble-256-uneven-n20k-400k-d20-m25", n_inst=256,
+                    n_range=[20_000, 400_000], dbar=20, target="tree30+15", m=25, k=30)
+    elif name == "large":
+        ens = synth.ba_clique_large()
+        desc = dict(workload="ba-1e7-m8-clique20-m40", n_inst=1, n=10_000_000, ba_m=8,
+                    target="clique20", m=40, k=20)
+    elif name == "small":
+        ens = synth.er_ensemble_small()
+        desc = dict(workload="er-ensemble-10x500-p0.016-m20", n_inst=10, n=500, p=0.016,
+                    target="tree15+8", m=20, k=15)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return ens, desc
+
+
+def alg_bytes_spmv(ens, fp64=False):
+    """Algorithmic bytes of one Lanczos SpMV launch over all realisations:
+    4 nnz (u32 cols) + 4 (n+1) (row_ptr) + 3 n vector elements (read v_j,
+    read v_{j-1}, write u), FP32 (FP64) elements."""
+    esz = 8 if fp64 else 4
+    return sum(4 * g.nnz + 4 * (g.n + 1) + 3 * esz * g.n for g in ens.graphs)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_oracle_sample(ens, m, budget_s=15.0, max_inst=None, want=None):
+    """Time the FP64 oracle (as it stands) on the first realisations of the
+    workload until ~budget_s of CPU time; returns (value, sample, results)."""
+    import oracle.communicability as oc
+
+    t_tot, units, done, results = 0.0, 0, 0, {}
+    for r, g in enumerate(ens.graphs):
+        if max_inst is not None and done >= max_inst:
+            break
+        t0 = time.perf_counter()
+        theta, y, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, m)
+        t_tot += time.perf_counter() - t0
+        units += g.nnz * m
+        done += 1
+        if want is not None and r in want:
+            results[r] = (theta, y)
+        if t_tot >= budget_s:
+            break
+    return units / t_tot, done, t_tot, results
+
+
+def run_reference(args, ens, desc, rank, world):
+    if rank != 0:
+        return
+    m = desc["m"]
+    # each step: the oracle on a bounded sample of the workload's realisations
+    per_step = max(1, min(len(ens.graphs), 6 if desc["workload"].startswith("er-ensemble-256") else 1))
+    if desc["workload"].startswith("ba-1e7"):
+        raise SystemExit("reference arm on the 1e7-node graph takes minutes per step; use the default")
+    for _ in range(args.warmup):
+        cpu_oracle_sample(ens, m, budget_s=1e9, max_inst=1)
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        v, done, t, _ = cpu_oracle_sample(ens, m, budget_s=1e9, max_inst=per_step)
+        units += sum(g.nnz * m for g in ens.graphs[:done])
+    dt = time.perf_counter() - t0
+    value = units / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": dict(desc, sample=f"first {per_step} realisations per step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {per_step} realisations of the workload per step, FP64 "
+                                       f"Lanczos with full reorthogonalisation, m={m}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "large", "small"])
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the e2e, plain-FP64 and CPU-baseline legs")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    ens, desc = workload(args.workload)
+    m, k = desc["m"], desc["k"]
+
+    if args.impl == "reference":
+        run_reference(args, ens, desc, rank, world)
+        return
+
+    import torch
+
+    from paper_1409_5000_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    units = sum(g.nnz for g in ens.graphs) * m  # edge-Lanczos-steps per step
+    gs = B.GraphSet(ens.graphs)
+    S = torch.empty(gs.n_max, dtype=torch.float64, device=dev)
+    ls = torch.empty(1, dtype=torch.float64, device=dev)
+    idx = torch.empty(k, dtype=torch.int32, device=dev)
+    val = torch.empty(k, dtype=torch.float64, device=dev)
+
+    def step():
+        B.ensemble_scores(gs, m, B.CB_FP32, out=(S, ls))
+        B.topk(S, k, out=(idx, val))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units / (ms * 1e-3)
+
+    # per-kernel times (CUDA events around each launch, same stream), separate pass
+    B.cb_profile_enable(1)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    fam = {}
+    for name, kid in [("spmv", B.CB_K_SPMV), ("finalize", B.CB_K_FINALIZE), ("tridiag", B.CB_K_TRIDIAG),
+                      ("combine", B.CB_K_COMBINE), ("topk", B.CB_K_TOPK), ("init", B.CB_K_INIT)]:
+        t, c = B.cb_profile_read(kid)
+        fam[name] = (t, c)
+    B.cb_profile_enable(0)
+    tot = sum(t for t, _ in fam.values())
+    spmv_ms, spmv_n = fam["spmv"]
+    spmv_avg = spmv_ms / max(spmv_n, 1)
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "spmv_kernel (Lanczos SpMV step)", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                "frac_of_8TBs_nominal": achieved / 8000.0, "traffic": None,
+                "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
+                "kernel_shares": {kname: round(t / tot, 4) for kname, (t, _) in fam.items()}}
+    launches_per_step = 2 + 2 * m + 1 + 1 + 15
+
+    extra = {}
+    ls1 = torch.empty(1, dtype=torch.float64, device=dev)
+    if rank == 0 and not args.skip_extra:
+        # plain per-graph FP64 path: one cb_communicability call per realisation
+        y_out = torch.empty(gs.n_max, dtype=torch.float64, device=dev)
+        for r in range(min(2, len(gs.n))):
+            B.cb_communicability(gs.h, r, m, B.CB_FP64, y_out.data_ptr(), ls1.data_ptr(), None,
+                                 stream.cuda_stream)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for r in range(len(gs.n)):
+            B.cb_communicability(gs.h, r, m, B.CB_FP64, y_out.data_ptr(), ls1.data_ptr(), None,
+                                 stream.cuda_stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1)
+        extra["plain_fp64_per_graph"] = {"ms": plain_ms, "speedup_batched_fp32": plain_ms / ms,
+                                         "note": "N x cb_communicability(FP64), ensemble sum and top-k excluded"}
+        # restore the FP32 workspace before the e2e leg
+        step()
+        torch.cuda.synchronize()
+
+    e2e = None
+    if rank == 0 and not args.skip_extra:
+        pinned = [synth.Graph(g.n, torch.from_numpy(g.row_ptr.view(np.int32)).pin_memory(),
+                              torch.from_numpy(g.col.view(np.int32)).pin_memory())
+                  for g in ens.graphs]
+        h2d = sum(4 * (g.n + 1) + 4 * g.nnz for g in ens.graphs)
+        d2h = 4 * k + 8 * k + 8
+        host_idx = torch.empty(k, dtype=torch.int32).pin_memory()
+        host_val = torch.empty(k, dtype=torch.float64).pin_memory()
+        host_ls = torch.empty(1, dtype=torch.float64).pin_memory()
+
+        class _PG:
+            def __init__(self, g, pg):
+                self.n, self.row_ptr, self.col = g.n, pg.row_ptr, pg.col
+
+        pgs = [_PG(g, pg) for g, pg in zip(ens.graphs, pinned)]
+        n_e2e = max(1, min(args.steps, 3))
+
+        def e2e_step():
+            with B.GraphSet(pgs) as g2:
+                S2 = torch.empty(g2.n_max, dtype=torch.float64, device=dev)
+                l2 = torch.empty(1, dtype=torch.float64, device=dev)
+                B.ensemble_scores(g2, m, B.CB_FP32, out=(S2, l2))
+                i2, v2 = B.topk(S2, k)
+                host_idx.copy_(i2, non_blocking=True)
+                host_val.copy_(v2, non_blocking=True)
+                host_ls.copy_(l2, non_blocking=True)
+                torch.cuda.synchronize()
+
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": n_e2e,
+               "api": "cb_graph_upload(pinned host) + cb_ensemble_scores + cb_topk + D2H + cb_graph_free"}
+
+    cpu = None
+    if rank == 0 and not args.skip_extra and world == 1:
+        v, done, t, res = cpu_oracle_sample(ens, m, budget_s=15.0, want={0, 1})
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {done} of {len(ens.graphs)} realisations, FP64 Lanczos with full "
+                         f"reorthogonalisation, m={m}, {t:.1f} s"}
+        # parity on the sampled realisations (CUDA FP32 per-graph call vs oracle)
+        worst = 0.0
+        for r, (th_o, y_o) in res.items():
+            y_g = torch.empty(ens.graphs[r].n, dtype=torch.float64, device=dev)
+            B.cb_communicability(gs.h, r, m, B.CB_FP32, y_g.data_ptr(), ls1.data_ptr(), None,
+                                 stream.cuda_stream)
+            torch.cuda.synchronize()
+            th_g = float(ls1.item())
+            a = y_g.cpu().numpy() * math.exp(th_g - th_o)
+            head = y_o >= 1e-3 * y_o.max()
+            worst = max(worst, float(np.max(np.abs(a - y_o)[head] / y_o[head])))
+        extra["parity_sample"] = {"realisations": sorted(res), "fp32_head_max_rel": worst, "tol": 1e-4}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(desc, l2="inputs larger than L2 (cols %.1f GB)" % (
+                    4 * sum(g.nnz for g in ens.graphs) / 1e9), parallelism=f"replicas{world}",
+                    precision="FP32 Krylov vectors, FP64 scalars / tridiagonal / ensemble sum"),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    gs.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

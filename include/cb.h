@@ -1,0 +1,187 @@
+/*
+ * cb.h -- C ABI of the GB300 (sm_103a) summed-communicability library.
+ *
+ * Method (Fioriti & Chinnici, arXiv 1409.5000):
+ *   - A is the symmetric 0/1 adjacency matrix of a simple undirected graph
+ *     (section "Signal processing on graphs").
+ *   - Every node i is scored by its Estrada-Benzi total communicability
+ *     EBTC_i = (e^A 1)_i, the row sums of e^A (eq. 4).
+ *   - e^A 1 is evaluated with a Krylov (Lanczos) approximation
+ *     ("Identification algorithm": the row sums come directly from e^A 1
+ *     at linear cost).
+ *   - Scores are summed over N background realisations that carry the same
+ *     embedded target (eq. 5).
+ *   - The k largest summed scores are the recovered target ("the largest
+ *     20 EBTC values").
+ *
+ * Conventions shared by every call:
+ *   - Return value: CB_OK (0) or one of the CB_ERR_* codes below.  On error
+ *     cb_last_error() returns a message for the calling host thread.
+ *   - Streams: `stream` is a cudaStream_t passed as void*; NULL means the
+ *     legacy default stream.  Unless a call says otherwise it is
+ *     asynchronous: it enqueues work on `stream` and returns.  Device
+ *     buffers passed in must stay valid until that work completes.
+ *   - Pointers: "device" means a CUDA device pointer on the current device
+ *     (for example torch tensor storage); "host" means ordinary or pinned
+ *     host memory.
+ *   - Scores may exceed the FP64 range (e^lambda_max for large graphs).
+ *     They are therefore returned as a scaled vector y plus one log scale:
+ *     score_i = exp(log_scale) * y_i.
+ *   - Precision: CB_FP32 keeps Krylov vectors and SpMV sums in FP32, and the
+ *     recurrence scalars, tridiagonal solve and cross-realisation sums in
+ *     FP64.  CB_FP64 computes everything in FP64.
+ */
+#ifndef CB_H_
+#define CB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CB_OK 0
+#define CB_ERR_ARG 1       /* invalid argument (null pointer, size, index) */
+#define CB_ERR_CUDA 2      /* a CUDA runtime call failed */
+#define CB_ERR_OOM 3       /* device allocation failed */
+#define CB_ERR_TIMEOUT 4   /* a bounded device-side wait gave up */
+#define CB_ERR_NONFINITE 5 /* a recurrence scalar became NaN or Inf */
+#define CB_ERR_STATE 6     /* call not valid in the current state */
+
+/* precision modes */
+#define CB_FP32 0
+#define CB_FP64 1
+
+/* cb_graph_upload flags */
+#define CB_VALIDATE 1u    /* check CSR invariants on the host before upload */
+#define CB_DEVICE_PTRS 2u /* row_ptr[r] / col[r] are device pointers */
+
+/* largest Krylov depth accepted by the compute calls */
+#define CB_MAX_M 128
+/* largest k accepted by cb_topk */
+#define CB_MAX_TOPK 4096
+
+typedef struct cb_graph cb_graph;
+
+/* Per-realisation report, filled when a compute call is given a non-NULL
+ * report array (the call then synchronises `stream` before returning). */
+typedef struct {
+  uint32_t m_eff;   /* Lanczos steps kept (< m after an exact breakdown) */
+  int32_t status;   /* CB_OK or CB_ERR_NONFINITE for this realisation */
+  double theta;     /* lambda_max(T_m_eff): this realisation's log scale */
+  double beta_last; /* last residual norm beta_m (0 after breakdown) */
+  double beta0;     /* ||1|| = sqrt(n_r) */
+} cb_inst_report;
+
+/*
+ * cb_graph_upload -- store N graphs (one per background realisation) on the
+ * current device as pattern-only CSR.
+ *   n_inst     number of realisations N (>= 1).
+ *   n[r]       node count of realisation r (>= 1).  Host array.
+ *   nnz[r]     directed CSR entries of realisation r (2|E_r|, < 2^32).
+ *              Host array.
+ *   row_ptr[r] uint32[n[r]+1] row offsets (row_ptr[r][0] = 0).  Host
+ *              pointers unless CB_DEVICE_PTRS is set.
+ *   col[r]     uint32[nnz[r]] column indices, each row sorted or unsorted.
+ *              Host pointers unless CB_DEVICE_PTRS is set.
+ *   flags      CB_VALIDATE: check that row_ptr is monotone, cols are in
+ *              range, there are no self-loops and the pattern is symmetric
+ *              (host arrays only; O(nnz log) host time).
+ *   stream     used for the copies.  The call synchronises `stream` before
+ *              returning, so the input arrays may be freed afterwards.
+ *   out        receives the handle.
+ * The pattern must be symmetric (A = A^T, paper section "Signal processing
+ * on graphs"); duplicates and self-loops are the caller's responsibility.
+ * The library owns all device memory of the handle until cb_graph_free().
+ * Realisations may have different n; realisation r then contributes 0 to
+ * nodes i >= n[r] in the ensemble sum.
+ */
+int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
+                    const uint32_t *const *row_ptr, const uint32_t *const *col,
+                    uint32_t flags, void *stream, cb_graph **out);
+
+/* Release a handle and its device memory (synchronises the device). */
+int cb_graph_free(cb_graph *h);
+
+/* Number of realisations / node count of realisation r / largest n. */
+uint32_t cb_graph_num_instances(const cb_graph *h);
+uint32_t cb_graph_num_nodes(const cb_graph *h, uint32_t r);
+uint32_t cb_graph_max_nodes(const cb_graph *h);
+
+/*
+ * cb_communicability -- total communicability of one realisation,
+ * EBTC = e^A 1 (eq. 4), by the m-step Lanczos approximation
+ *   e^A 1 ~= beta0 V_m exp(T_m) e1,  beta0 = sqrt(n),
+ * returned as y_scaled[i] * exp(*log_scale), log_scale = lambda_max(T_m).
+ *   h, inst    handle and realisation index (< N).
+ *   m          Krylov depth, 1 <= m <= CB_MAX_M.  The recurrence stops
+ *              early at an exact breakdown (invariant Krylov subspace).
+ *   prec       CB_FP32 or CB_FP64.
+ *   y_scaled   device, double[n[inst]], written.
+ *   log_scale  device, double[1], written.
+ *   rep        optional host cb_inst_report[1] (forces a synchronise).
+ * This is the plain per-graph path: one realisation per call.
+ */
+int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, double *y_scaled,
+                       double *log_scale, cb_inst_report *rep, void *stream);
+
+/*
+ * cb_ensemble_scores -- the summed score of eq. 5 over all N realisations
+ * of the handle, all computed in one batched pass:
+ *   EBTC(i) = sum_r EBTC_r(i) = exp(*log_scale) * S[i],
+ *   log_scale = max_r theta_r, each term weighted by exp(theta_r - log_scale)
+ *   and summed in realisation order in FP64.
+ *   m, prec    as cb_communicability.
+ *   n_out      length of S; n_out >= max_r n[r].  Entries >= max n are 0.
+ *   S          device, double[n_out], written.
+ *   log_scale  device, double[1], written.
+ *   rep        optional host cb_inst_report[N] (forces a synchronise).
+ */
+int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out, double *S,
+                       double *log_scale, cb_inst_report *rep, void *stream);
+
+/*
+ * cb_topk -- indices and values of the k largest entries of S ("the
+ * largest 20 EBTC values"; the paper sorts, this selects by radix).
+ *   S    device, double[n], read.
+ *   n    1 <= n < 2^32.  k: 1 <= k <= min(n, CB_MAX_TOPK).
+ *   idx  device, uint32[k], written; val device, double[k], written.
+ * Order: value descending, ties to the smaller index; -0.0 equals +0.0;
+ * NaN ranks below every number (so it is returned only if k exceeds the
+ * count of non-NaN entries).
+ * Asynchronous.  Device scratch (about 3 KB + 16 k bytes) comes from the
+ * stream-ordered allocator (cudaMallocAsync) and is freed on `stream`.
+ */
+int cb_topk(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val, void *stream);
+
+/*
+ * Kernel timing for measurement tools.  While enabled, every launch of the
+ * kernel families below is bracketed by a CUDA event pair recorded on the
+ * stream it is launched on; cb_profile_read() synchronises those events and
+ * returns the summed duration (ms) and the launch count of one family.
+ * cb_profile_enable(1) also clears earlier records.  Off by default; not
+ * thread-safe; it adds two event records per launch while on.
+ */
+#define CB_K_SPMV 0     /* Lanczos SpMV step (dominant kernel) */
+#define CB_K_FINALIZE 1 /* Lanczos finalize (axpy + norm) */
+#define CB_K_TRIDIAG 2  /* FP64 tridiagonal exp */
+#define CB_K_COMBINE 3  /* basis combine / ensemble sum */
+#define CB_K_TOPK 4     /* top-k selection (all its passes) */
+#define CB_K_INIT 5     /* basis / scalar initialisation */
+#define CB_K_COUNT 6
+int cb_profile_enable(int on);
+int cb_profile_read(int kernel, double *total_ms, uint64_t *launches);
+
+/* Message describing the last error on this host thread ("" if none). */
+const char *cb_last_error(void);
+
+/* Library ABI version (major << 16 | minor). */
+uint32_t cb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CB_H_ */

@@ -1,0 +1,270 @@
+"""Thin Python binding of libcb (argument marshalling only).
+
+The functions ``cb_*`` mirror the C ABI declared in ``include/cb.h`` one to
+one and take raw integers (device pointers, stream handles).  The helpers
+below them (:class:`GraphSet`, :func:`ensemble_scores`, ...) only allocate
+torch tensors for the outputs and pass their pointers; every step of the
+computation runs in the CUDA library.
+
+The library is loaded on first use.  If ``_lib/libcb.so`` has not been
+built, loading raises :class:`RuntimeError`; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from ._build import cb_lib_path, INCLUDE
+
+CB_OK, CB_ERR_ARG, CB_ERR_CUDA, CB_ERR_OOM, CB_ERR_TIMEOUT, CB_ERR_NONFINITE, CB_ERR_STATE = range(7)
+CB_FP32, CB_FP64 = 0, 1
+CB_VALIDATE, CB_DEVICE_PTRS = 1, 2
+CB_MAX_M, CB_MAX_TOPK = 128, 4096
+
+
+class CBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libcb error {code}: {msg}")
+        self.code = code
+
+
+class InstReport(ctypes.Structure):
+    _fields_ = [("m_eff", ctypes.c_uint32), ("status", ctypes.c_int32), ("theta", ctypes.c_double),
+                ("beta_last", ctypes.c_double), ("beta0", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded libcb (ctypes.CDLL)."""
+    global _LIB
+    if _LIB is None:
+        path = cb_lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcb.so not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        L.cb_graph_upload.restype = i32
+        L.cb_graph_upload.argtypes = [u32, vp, vp, pp, pp, u32, vp, ctypes.POINTER(vp)]
+        L.cb_graph_free.restype = i32
+        L.cb_graph_free.argtypes = [vp]
+        L.cb_graph_num_instances.restype = u32
+        L.cb_graph_num_instances.argtypes = [vp]
+        L.cb_graph_num_nodes.restype = u32
+        L.cb_graph_num_nodes.argtypes = [vp, u32]
+        L.cb_graph_max_nodes.restype = u32
+        L.cb_graph_max_nodes.argtypes = [vp]
+        L.cb_communicability.restype = i32
+        L.cb_communicability.argtypes = [vp, u32, u32, i32, vp, vp, vp, vp]
+        L.cb_ensemble_scores.restype = i32
+        L.cb_ensemble_scores.argtypes = [vp, u32, i32, u32, vp, vp, vp, vp]
+        L.cb_topk.restype = i32
+        L.cb_topk.argtypes = [vp, u32, u32, vp, vp, vp]
+        L.cb_last_error.restype = ctypes.c_char_p
+        L.cb_last_error.argtypes = []
+        L.cb_version.restype = u32
+        L.cb_version.argtypes = []
+        L.cb_profile_enable.restype = i32
+        L.cb_profile_enable.argtypes = [i32]
+        L.cb_profile_read.restype = i32
+        L.cb_profile_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint64)]
+        _LIB = L
+    return _LIB
+
+
+def declared_functions():
+    """Names of the functions declared in include/*.h."""
+    names = []
+    for fn in sorted(os.listdir(INCLUDE)):
+        if fn.endswith(".h"):
+            with open(os.path.join(INCLUDE, fn)) as f:
+                src = f.read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(cb_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def _check(rc):
+    if rc != CB_OK:
+        raise CBError(rc, lib().cb_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+# ---------------------------------------------------------------------------
+# One-to-one wrappers of the C ABI
+# ---------------------------------------------------------------------------
+
+def cb_graph_upload(n, nnz, row_ptr_ptrs, col_ptrs, flags, stream):
+    """Returns the handle (int).  Pointer lists hold integers."""
+    N = len(n)
+    n_arr = np.ascontiguousarray(n, dtype=np.uint32)
+    nnz_arr = np.ascontiguousarray(nnz, dtype=np.uint64)
+    rp = (ctypes.c_void_p * N)(*[ctypes.c_void_p(int(p)) for p in row_ptr_ptrs])
+    cp = (ctypes.c_void_p * N)(*[ctypes.c_void_p(int(p)) for p in col_ptrs])
+    out = ctypes.c_void_p()
+    _check(lib().cb_graph_upload(N, n_arr.ctypes.data, nnz_arr.ctypes.data,
+                                 ctypes.cast(rp, ctypes.POINTER(ctypes.c_void_p)),
+                                 ctypes.cast(cp, ctypes.POINTER(ctypes.c_void_p)), flags,
+                                 ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
+
+
+def cb_graph_free(h):
+    _check(lib().cb_graph_free(ctypes.c_void_p(h)))
+
+
+def cb_communicability(h, inst, m, prec, y_ptr, log_scale_ptr, report, stream):
+    rep = ctypes.c_void_p(ctypes.addressof(report)) if report is not None else None
+    _check(lib().cb_communicability(ctypes.c_void_p(h), inst, m, prec, ctypes.c_void_p(y_ptr),
+                                    ctypes.c_void_p(log_scale_ptr), rep, ctypes.c_void_p(stream)))
+
+
+def cb_ensemble_scores(h, m, prec, n_out, S_ptr, log_scale_ptr, report, stream):
+    rep = ctypes.c_void_p(ctypes.addressof(report)) if report is not None else None
+    _check(lib().cb_ensemble_scores(ctypes.c_void_p(h), m, prec, n_out, ctypes.c_void_p(S_ptr),
+                                    ctypes.c_void_p(log_scale_ptr), rep, ctypes.c_void_p(stream)))
+
+
+def cb_topk(S_ptr, n, k, idx_ptr, val_ptr, stream):
+    _check(lib().cb_topk(ctypes.c_void_p(S_ptr), n, k, ctypes.c_void_p(idx_ptr),
+                         ctypes.c_void_p(val_ptr), ctypes.c_void_p(stream)))
+
+
+CB_K_SPMV, CB_K_FINALIZE, CB_K_TRIDIAG, CB_K_COMBINE, CB_K_TOPK, CB_K_INIT = range(6)
+
+
+def cb_profile_enable(on):
+    _check(lib().cb_profile_enable(int(bool(on))))
+
+
+def cb_profile_read(kernel):
+    """(total_ms, launches) of one kernel family since cb_profile_enable(1)."""
+    t = ctypes.c_double()
+    c = ctypes.c_uint64()
+    _check(lib().cb_profile_read(kernel, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def cb_last_error():
+    return lib().cb_last_error().decode(errors="replace")
+
+
+def cb_version():
+    return int(lib().cb_version())
+
+
+# ---------------------------------------------------------------------------
+# Convenience layer over torch tensors (allocation + pointers only)
+# ---------------------------------------------------------------------------
+
+def _ptr(a):
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class GraphSet:
+    """A handle holding N realisations on the current CUDA device."""
+
+    def __init__(self, graphs, validate=False, stream=None):
+        """`graphs`: sequence of objects with .n, .row_ptr, .col (numpy uint32
+        arrays, host or pinned torch tensors, or CUDA torch tensors)."""
+        import torch
+
+        graphs = list(graphs)
+        dev = [hasattr(g.col, "is_cuda") and g.col.is_cuda for g in graphs]
+        if any(dev) and not all(dev):
+            raise ValueError("all realisations must be on the host or all on the device")
+        flags = (CB_VALIDATE if validate else 0) | (CB_DEVICE_PTRS if all(dev) else 0)
+        keep = []
+        rps, cols = [], []
+        for g in graphs:
+            rp, c = g.row_ptr, g.col
+            if not hasattr(rp, "data_ptr"):
+                rp = np.ascontiguousarray(rp, dtype=np.uint32)
+                c = np.ascontiguousarray(c, dtype=np.uint32)
+                if c.size == 0:
+                    c = np.zeros(1, np.uint32)
+            keep += [rp, c]
+            rps.append(_ptr(rp))
+            cols.append(_ptr(c))
+        n = [int(g.n) for g in graphs]
+        nnz = [int(g.row_ptr[-1]) for g in graphs]
+        self.n = n
+        self.nnz = nnz
+        self.n_max = max(n)
+        self.device = torch.cuda.current_device()
+        self.h = cb_graph_upload(n, nnz, rps, cols, flags, _stream_handle(stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            cb_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def communicability(gs: GraphSet, inst: int, m: int, prec: int = CB_FP32, stream=None,
+                    report: bool = False):
+    """(log_scale, y) with e^A 1 ~= exp(log_scale) * y for realisation inst."""
+    import torch
+
+    y = torch.empty(gs.n[inst], dtype=torch.float64, device="cuda")
+    ls = torch.empty(1, dtype=torch.float64, device="cuda")
+    rep = InstReport() if report else None
+    cb_communicability(gs.h, inst, m, prec, y.data_ptr(), ls.data_ptr(), rep,
+                       _stream_handle(stream))
+    return (ls, y, rep) if report else (ls, y)
+
+
+def ensemble_scores(gs: GraphSet, m: int, prec: int = CB_FP32, n_out=None, out=None,
+                    stream=None, report: bool = False):
+    """(log_scale, S) with sum_r e^{A_r} 1 ~= exp(log_scale) * S (eq. 5)."""
+    import torch
+
+    n_out = gs.n_max if n_out is None else n_out
+    if out is None:
+        S = torch.empty(n_out, dtype=torch.float64, device="cuda")
+        ls = torch.empty(1, dtype=torch.float64, device="cuda")
+    else:
+        S, ls = out
+    rep = (InstReport * len(gs.n))() if report else None
+    cb_ensemble_scores(gs.h, m, prec, n_out, S.data_ptr(), ls.data_ptr(), rep,
+                       _stream_handle(stream))
+    return (ls, S, list(rep)) if report else (ls, S)
+
+
+def topk(S, k: int, out=None, stream=None):
+    """(idx uint32 as int32 tensor, val float64) of the k largest entries."""
+    import torch
+
+    if out is None:
+        idx = torch.empty(k, dtype=torch.int32, device=S.device)
+        val = torch.empty(k, dtype=torch.float64, device=S.device)
+    else:
+        idx, val = out
+    cb_topk(S.data_ptr(), S.numel(), k, idx.data_ptr(), val.data_ptr(), _stream_handle(stream))
+    return idx, val

@@ -1,0 +1,479 @@
+// C ABI entry points: graph upload / free, per-call dispatch, errors.
+//
+// Upload builds the pattern-only CSR store of the adjacency matrices (paper,
+// "Signal processing on graphs": symmetric 0/1 A) for N realisations and
+// the static launch tables of the Lanczos kernels:
+//   * every realisation's node range is padded to kNodeAlign elements in the
+//     Krylov vectors, so vector tiles start aligned;
+//   * SpMV tiles of kTileRows rows; rows with more than kHeavyDeg entries are
+//     listed as heavy rows and cut into kChunk-edge chunks;
+//   * finalize tiles of kFinRows nodes;
+//   * one reduction plan (slots and groups) per realisation and kernel kind.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <thread>
+
+#include "cb_internal.cuh"
+
+namespace cb {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return CB_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(CB_ERR_OOM, std::string(what) + ": out of device memory");
+  }
+  return set_error(CB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- optional launch timing -------------------------------------------
+struct ProfRec {
+  int kernel;
+  cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_begin(int kernel, cudaStream_t s) {
+  if (!g_prof_on) return -1;
+  ProfRec r{kernel, take_event(), take_event()};
+  cudaEventRecord(r.a, s);
+  g_prof.push_back(r);
+  return (int)g_prof.size() - 1;
+}
+
+void prof_end(int token, cudaStream_t s) {
+  if (token >= 0) cudaEventRecord(g_prof[token].b, s);
+}
+
+static void prof_clear() {
+  for (auto &r : g_prof) {
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof.clear();
+}
+
+static int pick_lanes(double avg_deg) {
+  if (const char *env = std::getenv("CB_LANES")) {
+    int v = std::atoi(env);
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) return v;
+  }
+  if (avg_deg < 3) return 1;
+  if (avg_deg < 6) return 2;
+  if (avg_deg < 24) return 4;
+  if (avg_deg < 64) return 8;
+  if (avg_deg < 128) return 16;
+  return 32;
+}
+
+template <typename P>
+static cudaError_t dalloc(P **p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P) + 16);
+}
+
+static void free_workspace(cb_graph *h) {
+  Workspace &W = h->ws;
+  if (W.V) cudaFree(W.V);
+  if (W.blob) cudaFree(W.blob);
+  W = Workspace{};
+}
+
+static void free_graph_arrays(cb_graph *h) {
+  cudaFree(h->col);
+  cudaFree(h->row_ptr);
+  cudaFree(h->d_inst);
+  cudaFree(h->d_tile_inst);
+  cudaFree(h->d_heavy);
+  cudaFree(h->d_chunk_heavy);
+  cudaFree(h->d_fin_inst);
+  h->col = nullptr;
+  h->row_ptr = nullptr;
+  h->d_inst = nullptr;
+  h->d_tile_inst = nullptr;
+  h->d_heavy = nullptr;
+  h->d_chunk_heavy = nullptr;
+  h->d_fin_inst = nullptr;
+}
+
+// Workspace for depth m in precision prec; reused when large enough.
+static int ensure_workspace(cb_graph *h, uint32_t m, int prec, cudaStream_t s) {
+  Workspace &W = h->ws;
+  if (W.V && W.prec == prec && W.m >= m) return CB_OK;
+  free_workspace(h);
+  const size_t esz = prec == CB_FP64 ? sizeof(double) : sizeof(float);
+  W.vec_stride = h->total_nodes_padded;
+  const size_t vbytes = (size_t)(m + 1) * W.vec_stride * esz;
+  cudaError_t e = cudaMalloc(&W.V, vbytes ? vbytes : 16);
+  if (e != cudaSuccess) {
+    W.V = nullptr;
+    return cuda_error(e, "workspace: Krylov basis");
+  }
+  const uint32_t N = h->n_inst, ms = m + 1;
+  const size_t nslots = std::max<size_t>(h->total_slots, 1);
+  const size_t ngroups = std::max<size_t>(h->total_groups, 1);
+  const size_t nchunks = std::max<size_t>(h->total_chunks, 1);
+  const size_t nheavy = std::max<size_t>(h->total_heavy, 1);
+  // doubles first, then 32-bit words
+  const size_t nd = 4 * (size_t)N * ms + N + nslots + ngroups + nchunks;
+  const size_t nw = 2 * (size_t)N + ngroups + N + nheavy;
+  const size_t bytes = nd * sizeof(double) + nw * sizeof(uint32_t) + 256;
+  e = cudaMalloc(&W.blob, bytes);
+  if (e != cudaSuccess) {
+    W.blob = nullptr;
+    free_workspace(h);
+    return cuda_error(e, "workspace: scalars");
+  }
+  double *d = reinterpret_cast<double *>(W.blob);
+  W.sc.alpha = d; d += (size_t)N * ms;
+  W.sc.beta = d; d += (size_t)N * ms;
+  W.sc.scale = d; d += (size_t)N * ms;
+  W.sc.gamma = d; d += (size_t)N * ms;
+  W.sc.theta = d; d += N;
+  W.part = d; d += nslots;
+  W.gpart = d; d += ngroups;
+  W.cpart = d; d += nchunks;
+  uint32_t *w = reinterpret_cast<uint32_t *>(d);
+  W.sc.meff = w; w += N;
+  W.sc.status = reinterpret_cast<int32_t *>(w); w += N;
+  W.gcnt = w; w += ngroups;
+  W.icnt = w; w += N;
+  W.hcnt = w; w += nheavy;
+  W.sc.ms = ms;
+  W.blob_bytes = bytes;
+  W.m = m;
+  W.prec = prec;
+  e = cudaMemsetAsync(W.blob, 0, bytes, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_workspace(h);
+    return cuda_error(e, "workspace: clear");
+  }
+  return CB_OK;
+}
+
+static int validate_host(uint32_t n, uint64_t nnz, const uint32_t *rp, const uint32_t *col,
+                         uint32_t r) {
+  char buf[256];
+  if (rp[0] != 0 || rp[n] != nnz) {
+    snprintf(buf, sizeof buf, "realisation %u: row_ptr[0] must be 0 and row_ptr[n] = nnz", r);
+    return set_error(CB_ERR_ARG, buf);
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) {
+      snprintf(buf, sizeof buf, "realisation %u: row_ptr decreases at row %u", r, i);
+      return set_error(CB_ERR_ARG, buf);
+    }
+    for (uint32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const uint32_t c = col[e];
+      if (c >= n || c == i) {
+        snprintf(buf, sizeof buf, "realisation %u: bad column %u in row %u", r, c, i);
+        return set_error(CB_ERR_ARG, buf);
+      }
+      // symmetric: i must appear in row c (rows need not be sorted)
+      bool found = false;
+      for (uint32_t f = rp[c]; f < rp[c + 1] && !found; ++f) found = (col[f] == i);
+      if (!found) {
+        snprintf(buf, sizeof buf, "realisation %u: pattern not symmetric at (%u,%u)", r, i, c);
+        return set_error(CB_ERR_ARG, buf);
+      }
+    }
+  }
+  return CB_OK;
+}
+
+}  // namespace cb
+
+using namespace cb;
+
+CB_API const char *cb_last_error(void) { return g_err.c_str(); }
+
+CB_API int cb_profile_enable(int on) {
+  prof_clear();
+  g_prof_on = on != 0;
+  return CB_OK;
+}
+
+CB_API int cb_profile_read(int kernel, double *total_ms, uint64_t *launches) {
+  if (!total_ms || !launches || kernel < 0 || kernel >= CB_K_COUNT)
+    return set_error(CB_ERR_ARG, "cb_profile_read: bad argument");
+  double t = 0.0;
+  uint64_t c = 0;
+  for (auto &r : g_prof) {
+    if (r.kernel != kernel) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return cuda_error(e, "cb_profile_read");
+    t += ms;
+    ++c;
+  }
+  *total_ms = t;
+  *launches = c;
+  return CB_OK;
+}
+CB_API uint32_t cb_version(void) { return (1u << 16) | 0u; }
+
+CB_API uint32_t cb_graph_num_instances(const cb_graph *h) { return h ? h->n_inst : 0; }
+CB_API uint32_t cb_graph_num_nodes(const cb_graph *h, uint32_t r) {
+  return (h && r < h->n_inst) ? h->inst[r].n : 0;
+}
+CB_API uint32_t cb_graph_max_nodes(const cb_graph *h) { return h ? h->n_max : 0; }
+
+CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
+                           const uint32_t *const *row_ptr, const uint32_t *const *col,
+                           uint32_t flags, void *stream, cb_graph **out) {
+  if (!out) return set_error(CB_ERR_ARG, "cb_graph_upload: out is null");
+  *out = nullptr;
+  if (n_inst == 0 || !n || !nnz || !row_ptr || !col)
+    return set_error(CB_ERR_ARG, "cb_graph_upload: empty input or null array");
+  const bool dev = (flags & CB_DEVICE_PTRS) != 0;
+  if (dev && (flags & CB_VALIDATE))
+    return set_error(CB_ERR_ARG, "cb_graph_upload: CB_VALIDATE needs host arrays");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  cb_graph *h = new cb_graph();
+  cudaGetDevice(&h->device);
+  h->n_inst = n_inst;
+  h->inst.resize(n_inst);
+
+  // host views of row_ptr (device uploads copy them back for the tables)
+  std::vector<std::vector<uint32_t>> rp_host(dev ? n_inst : 0);
+  auto rp_of = [&](uint32_t r) -> const uint32_t * { return dev ? rp_host[r].data() : row_ptr[r]; };
+
+  uint64_t node_off = 0, edge_off = 0, rp_off = 0;
+  uint32_t tile_off = 0, fin_off = 0, slot_off = 0, group_off = 0;
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    if (n[r] == 0 || !row_ptr[r] || (nnz[r] && !col[r])) {
+      delete h;
+      return set_error(CB_ERR_ARG, "cb_graph_upload: realisation with n = 0 or null array");
+    }
+    if (nnz[r] >= 0xffffffffull) {
+      delete h;
+      return set_error(CB_ERR_ARG, "cb_graph_upload: nnz of one realisation must be < 2^32");
+    }
+    if (dev) {
+      rp_host[r].resize((size_t)n[r] + 1);
+      cudaError_t e = cudaMemcpy(rp_host[r].data(), row_ptr[r], ((size_t)n[r] + 1) * 4,
+                                 cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        delete h;
+        return cuda_error(e, "cb_graph_upload: read row_ptr");
+      }
+    }
+    const uint32_t *rp = rp_of(r);
+    if (rp[0] != 0 || rp[n[r]] != nnz[r]) {
+      delete h;
+      return set_error(CB_ERR_ARG, "cb_graph_upload: row_ptr[0] must be 0 and row_ptr[n] = nnz");
+    }
+    if (flags & CB_VALIDATE) {
+      int rc = validate_host(n[r], nnz[r], rp, col[r], r);
+      if (rc != CB_OK) {
+        delete h;
+        return rc;
+      }
+    }
+    InstDesc &I = h->inst[r];
+    std::memset(&I, 0, sizeof I);
+    I.n = n[r];
+    I.node_base = node_off;
+    I.edge_base = edge_off;
+    I.rp_base = rp_off;
+    node_off += ((uint64_t)n[r] + kNodeAlign - 1) / kNodeAlign * kNodeAlign;
+    edge_off += nnz[r];
+    rp_off += (uint64_t)n[r] + 1;
+    I.tile_base = tile_off;
+    I.n_tiles = (n[r] + kTileRows - 1) / kTileRows;
+    tile_off += I.n_tiles;
+    I.fin_base = fin_off;
+    I.n_fin = (n[r] + kFinRows - 1) / kFinRows;
+    fin_off += I.n_fin;
+    h->n_max = std::max(h->n_max, n[r]);
+  }
+  if (node_off >= (1ull << 40) || tile_off >= 0x7fffffffu) {
+    delete h;
+    return set_error(CB_ERR_ARG, "cb_graph_upload: input too large");
+  }
+  // heavy rows (degree > kHeavyDeg), in realisation and row order
+  uint32_t chunk_off = 0;
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    InstDesc &I = h->inst[r];
+    const uint32_t *rp = rp_of(r);
+    I.heavy_base = (uint32_t)h->heavy.size();
+    I.chunk_base = chunk_off;
+    for (uint32_t i = 0; i < I.n; ++i) {
+      const uint32_t deg = rp[i + 1] - rp[i];
+      if (deg > kHeavyDeg) {
+        const uint32_t nc = (deg + kChunk - 1) / kChunk;
+        h->heavy.push_back(HeavyRow{r, i, chunk_off, nc});
+        chunk_off += nc;
+      }
+    }
+    I.n_heavy = (uint32_t)h->heavy.size() - I.heavy_base;
+    I.n_chunks = chunk_off - I.chunk_base;
+    I.spmv.slot_base = slot_off;
+    I.spmv.n_slots = I.n_tiles + I.n_heavy;
+    I.spmv.group_base = group_off;
+    I.spmv.n_groups = (I.spmv.n_slots + kGroup - 1) / kGroup;
+    slot_off += I.spmv.n_slots;
+    group_off += I.spmv.n_groups;
+  }
+  // finalize reductions reuse the same buffers (never concurrent with SpMV)
+  uint32_t fslot = 0, fgroup = 0;
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    InstDesc &I = h->inst[r];
+    I.fin.slot_base = fslot;
+    I.fin.n_slots = I.n_fin;
+    I.fin.group_base = fgroup;
+    I.fin.n_groups = (I.n_fin + kGroup - 1) / kGroup;
+    fslot += I.fin.n_slots;
+    fgroup += I.fin.n_groups;
+  }
+  h->total_nodes_padded = node_off;
+  h->total_nnz = edge_off;
+  h->total_tiles = tile_off;
+  h->total_fin = fin_off;
+  h->total_heavy = (uint32_t)h->heavy.size();
+  h->total_chunks = chunk_off;
+  h->total_slots = std::max(slot_off, fslot);
+  h->total_groups = std::max(group_off, fgroup);
+  uint64_t nsum = 0;
+  for (uint32_t r = 0; r < n_inst; ++r) nsum += n[r];
+  h->lanes = pick_lanes((double)edge_off / (double)nsum);
+
+  // per-tile instance tables
+  std::vector<uint32_t> tile_inst(std::max<uint32_t>(tile_off, 1)), fin_inst(std::max<uint32_t>(fin_off, 1));
+  std::vector<uint32_t> chunk_heavy(std::max<uint32_t>(chunk_off, 1));
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    const InstDesc &I = h->inst[r];
+    std::fill(tile_inst.begin() + I.tile_base, tile_inst.begin() + I.tile_base + I.n_tiles, r);
+    std::fill(fin_inst.begin() + I.fin_base, fin_inst.begin() + I.fin_base + I.n_fin, r);
+  }
+  for (uint32_t q = 0; q < h->total_heavy; ++q)
+    for (uint32_t c = 0; c < h->heavy[q].n_chunks; ++c) chunk_heavy[h->heavy[q].chunk_base + c] = q;
+
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(dalloc(&h->col, edge_off + 4));
+  chk(dalloc(&h->row_ptr, rp_off));
+  chk(dalloc(&h->d_inst, n_inst));
+  chk(dalloc(&h->d_tile_inst, tile_inst.size()));
+  chk(dalloc(&h->d_fin_inst, fin_inst.size()));
+  chk(dalloc(&h->d_heavy, std::max<size_t>(h->heavy.size(), 1)));
+  chk(dalloc(&h->d_chunk_heavy, chunk_heavy.size()));
+  if (e != cudaSuccess) {
+    free_graph_arrays(h);
+    delete h;
+    return cuda_error(e, "cb_graph_upload: allocate");
+  }
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (uint32_t r = 0; r < n_inst && e == cudaSuccess; ++r) {
+    const InstDesc &I = h->inst[r];
+    if (nnz[r]) chk(cudaMemcpyAsync(h->col + I.edge_base, col[r], nnz[r] * 4, kind, s));
+    chk(cudaMemcpyAsync(h->row_ptr + I.rp_base, row_ptr[r], ((size_t)I.n + 1) * 4, kind, s));
+  }
+  chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), n_inst * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(h->d_tile_inst, tile_inst.data(), tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(h->d_fin_inst, fin_inst.data(), fin_inst.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!h->heavy.empty())
+    chk(cudaMemcpyAsync(h->d_heavy, h->heavy.data(), h->heavy.size() * sizeof(HeavyRow),
+                        cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(h->d_chunk_heavy, chunk_heavy.data(), chunk_heavy.size() * 4,
+                      cudaMemcpyHostToDevice, s));
+  chk(cudaMemsetAsync(h->col + edge_off, 0, 16, s));
+  chk(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) {
+    free_graph_arrays(h);
+    delete h;
+    return cuda_error(e, "cb_graph_upload: copy");
+  }
+  *out = h;
+  return CB_OK;
+}
+
+CB_API int cb_graph_free(cb_graph *h) {
+  if (!h) return set_error(CB_ERR_ARG, "cb_graph_free: null handle");
+  cudaError_t e = cudaDeviceSynchronize();
+  free_workspace(h);
+  free_graph_arrays(h);
+  delete h;
+  return cuda_error(e, "cb_graph_free");
+}
+
+static int fill_report(cb_graph *h, uint32_t r0, uint32_t r1, cb_inst_report *rep, cudaStream_t s) {
+  const uint32_t N = r1 - r0, ms = h->ws.sc.ms;
+  std::vector<uint32_t> meff(N);
+  std::vector<int32_t> st(N);
+  std::vector<double> th(N), be((size_t)N * ms);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(meff.data(), h->ws.sc.meff + r0, N * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(st.data(), h->ws.sc.status + r0, N * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(th.data(), h->ws.sc.theta + r0, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(be.data(), h->ws.sc.beta + (size_t)r0 * ms, (size_t)N * ms * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "report");
+  int rc = CB_OK;
+  for (uint32_t q = 0; q < N; ++q) {
+    rep[q].m_eff = meff[q];
+    rep[q].status = st[q];
+    rep[q].theta = th[q];
+    rep[q].beta_last = meff[q] ? be[(size_t)q * ms + meff[q] - 1] : 0.0;
+    rep[q].beta0 = std::sqrt((double)h->inst[r0 + q].n);
+    if (st[q] != CB_OK) rc = set_error(CB_ERR_NONFINITE, "a recurrence scalar became non-finite");
+  }
+  return rc;
+}
+
+CB_API int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, double *y_scaled,
+                              double *log_scale, cb_inst_report *rep, void *stream) {
+  if (!h || !y_scaled || !log_scale) return set_error(CB_ERR_ARG, "cb_communicability: null argument");
+  if (inst >= h->n_inst) return set_error(CB_ERR_ARG, "cb_communicability: realisation index out of range");
+  if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_communicability: need 1 <= m <= CB_MAX_M");
+  if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_communicability: bad precision");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = ensure_workspace(h, m, prec, s);
+  if (rc == CB_OK) rc = lanczos_run(h, inst, inst + 1, m, prec, s);
+  if (rc == CB_OK) rc = tridiag_run(h, inst, inst + 1, prec, s);
+  if (rc == CB_OK) rc = combine_single(h, inst, prec, y_scaled, log_scale, s);
+  if (rc == CB_OK && rep) rc = fill_report(h, inst, inst + 1, rep, s);
+  return rc;
+}
+
+CB_API int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out, double *S,
+                              double *log_scale, cb_inst_report *rep, void *stream) {
+  if (!h || !S || !log_scale) return set_error(CB_ERR_ARG, "cb_ensemble_scores: null argument");
+  if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_ensemble_scores: need 1 <= m <= CB_MAX_M");
+  if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_ensemble_scores: bad precision");
+  if (n_out < h->n_max) return set_error(CB_ERR_ARG, "cb_ensemble_scores: n_out < largest n");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = ensure_workspace(h, m, prec, s);
+  if (rc == CB_OK) rc = lanczos_run(h, 0, h->n_inst, m, prec, s);
+  if (rc == CB_OK) rc = tridiag_run(h, 0, h->n_inst, prec, s);
+  if (rc == CB_OK) rc = combine_ensemble(h, prec, n_out, S, log_scale, s);
+  if (rc == CB_OK && rep) rc = fill_report(h, 0, h->n_inst, rep, s);
+  return rc;
+}

@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of libcb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "cb.h"
+
+#define CB_API extern "C" __attribute__((visibility("default")))
+
+namespace cb {
+
+// ---------------------------------------------------------------------------
+// Layout constants
+// ---------------------------------------------------------------------------
+constexpr int kThreads = 256;        // threads per CTA in the SpMV / finalize kernels
+constexpr int kTileRows = 256;       // rows per SpMV tile
+constexpr int kFinRows = 2048;       // nodes per finalize tile (256 threads x 8)
+constexpr int kGroup = 32;           // reduction slots per last-arriver group
+constexpr uint32_t kHeavyDeg = 8192; // rows above this degree are split across CTAs
+constexpr uint32_t kChunk = 4096;    // edges per heavy-row chunk
+constexpr uint32_t kLongDeg = 1024;  // rows above this (<= kHeavyDeg) use the whole CTA
+constexpr int kNodeAlign = 32;       // per-instance node offset alignment (elements)
+
+// Two-level deterministic reduction plan of one instance for one kernel kind:
+// one partial per slot, slots grouped by kGroup; the last CTA to arrive in a
+// group sums the group, the last group of the instance sums the groups.
+struct RedPlan {
+  uint32_t slot_base, n_slots, group_base, n_groups;
+};
+
+// Per-realisation descriptor (device copy and host copy).
+struct InstDesc {
+  uint64_t node_base;  // offset of node 0 in every Krylov vector
+  uint64_t edge_base;  // offset of the first column index in col[]
+  uint64_t rp_base;    // offset of row_ptr[0] in the row_ptr array
+  uint32_t n;
+  uint32_t nnz_hi;     // unused (nnz < 2^32 per instance); keeps alignment
+  uint32_t tile_base, n_tiles;    // SpMV tiles (kTileRows rows each)
+  uint32_t heavy_base, n_heavy;   // heavy rows
+  uint32_t chunk_base, n_chunks;  // heavy-row chunks
+  uint32_t fin_base, n_fin;       // finalize tiles (kFinRows nodes each)
+  RedPlan spmv;                   // slots: n_tiles normal tiles, then n_heavy rows
+  RedPlan fin;                    // slots: n_fin tiles
+};
+
+struct HeavyRow {
+  uint32_t inst, row, chunk_base, n_chunks;
+};
+
+// Per-instance Krylov scalars, FP64.  Index j is the 0-based Lanczos step.
+struct Scalars {
+  double *alpha;  // [n_inst * ms]
+  double *beta;   // [n_inst * ms]   beta[j] = ||w_{j+1}||
+  double *scale;  // [n_inst * ms]   v_j = scale[j] * W_j
+  double *gamma;  // [n_inst * ms]   combine weights beta0 c_j scale_j
+  double *theta;  // [n_inst]
+  uint32_t *meff; // [n_inst]        steps kept; m until a breakdown
+  int32_t *status;// [n_inst]
+  uint32_t ms;    // stride (>= m + 1)
+};
+
+// Device workspace for one (m, precision) pair.
+struct Workspace {
+  int prec = -1;
+  uint32_t m = 0;
+  void *V = nullptr;       // (m + 1) vectors of vec_stride elements
+  uint64_t vec_stride = 0; // elements per Krylov vector (all instances)
+  Scalars sc{};
+  double *part = nullptr;  // reduction partials per slot
+  double *gpart = nullptr; // reduction partials per group
+  uint32_t *gcnt = nullptr;// arrival counters per group
+  uint32_t *icnt = nullptr;// arrival counters per instance
+  double *cpart = nullptr; // heavy-row chunk partials
+  uint32_t *hcnt = nullptr;// heavy-row arrival counters
+  size_t blob_bytes = 0;
+  void *blob = nullptr;    // single allocation backing sc/part/gpart/cnt
+};
+
+}  // namespace cb
+
+struct cb_graph {
+  int device = 0;
+  uint32_t n_inst = 0;
+  uint32_t n_max = 0;
+  uint64_t total_nodes_padded = 0;  // sum of padded node ranges
+  uint64_t total_nnz = 0;
+  uint32_t total_tiles = 0, total_heavy = 0, total_chunks = 0, total_fin = 0;
+  uint32_t total_slots = 0, total_groups = 0;
+  int lanes = 8;  // lanes per row for short rows (1, 2, 4, 8, 16, 32)
+  std::vector<cb::InstDesc> inst;        // host copy
+  std::vector<cb::HeavyRow> heavy;       // host copy
+  // device arrays
+  uint32_t *col = nullptr;
+  uint32_t *row_ptr = nullptr;
+  cb::InstDesc *d_inst = nullptr;
+  uint32_t *d_tile_inst = nullptr;       // instance of each normal tile
+  cb::HeavyRow *d_heavy = nullptr;
+  uint32_t *d_chunk_heavy = nullptr;     // heavy-row index of each chunk
+  uint32_t *d_fin_inst = nullptr;        // instance of each finalize tile
+  cb::Workspace ws;
+};
+
+namespace cb {
+// error plumbing (cb_api.cu)
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+
+// optional per-launch event timing (cb_api.cu); no-ops unless enabled
+int prof_begin(int kernel, cudaStream_t s);
+void prof_end(int token, cudaStream_t s);
+
+// kernel launchers (cb_lanczos.cu).  Range of realisations [r0, r1).
+int lanczos_run(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, int prec, cudaStream_t s);
+// tridiagonal exp (cb_tridiag.cu)
+int tridiag_run(cb_graph *h, uint32_t r0, uint32_t r1, int prec, cudaStream_t s);
+// combine (cb_combine.cu)
+int combine_single(cb_graph *h, uint32_t r, int prec, double *y, double *log_scale,
+                   cudaStream_t s);
+int combine_ensemble(cb_graph *h, int prec, uint32_t n_out, double *S, double *log_scale,
+                     cudaStream_t s);
+}  // namespace cb

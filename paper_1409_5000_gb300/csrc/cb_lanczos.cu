@@ -1,0 +1,365 @@
+// Batched Lanczos recurrence for e^A 1 on pattern-only CSR (sm_103a).
+//
+// The paper evaluates the total communicability e^A 1 (eq. 4) with a Krylov
+// method ("Identification algorithm").  This file runs the m-step Lanczos
+// recurrence that builds the Krylov basis of K_m(A, 1) and the tridiagonal
+// coefficients, for every realisation of a handle at once (eq. 5 sums
+// independent realisations, so they advance in lock step: one launch per
+// phase covers all of them).
+//
+// Basis storage.  Vector j of realisation r is kept unnormalised as W_j with
+// an FP64 scale, v_j = scale_j * W_j, in one array of (m+1) vectors; the
+// realisations' node ranges are concatenated with kNodeAlign padding.
+// W_0 = 1, scale_0 = 1/sqrt(n).
+//
+// Step j (0-based), two kernels:
+//   spmv:     u = scale_j (A W_j) - beta_{j-1} scale_{j-1} W_{j-1}
+//             alpha_j = scale_j (W_j . u);   W_{j+1} <- u
+//   finalize: w = W_{j+1} - alpha_j scale_j W_j;  W_{j+1} <- w
+//             beta_j = ||w||; scale_{j+1} = 1/beta_j, or stop at an exact
+//             breakdown beta_j <= tau (|alpha_j| + beta_{j-1}).
+// No reorthogonalisation: the Lanczos approximation of f(A)b stays accurate
+// in finite precision after orthogonality is lost (Greenbaum; Musco, Musco &
+// Sidford 2018), which the parity tests check against the FP64 oracle that
+// reorthogonalises fully.
+//
+// SpMV work split.  A CTA owns kTileRows consecutive rows.  Rows with at
+// most 8*G entries are summed by G-lane groups; longer rows up to kLongDeg
+// by one warp each; rows up to kHeavyDeg by the whole CTA; rows above
+// kHeavyDeg are cut into kChunk-edge chunks, one CTA per chunk, and the last
+// chunk to finish completes the row.  Column indices are streamed with an
+// evict-first hint; the gathered vector stays cache-resident.
+#include <cstdio>
+
+#include "cb_internal.cuh"
+#include "cb_reduce.cuh"
+
+namespace cb {
+
+struct LArgs {
+  const InstDesc *inst;
+  const uint32_t *tile_inst;
+  const HeavyRow *heavy;
+  const uint32_t *chunk_heavy;
+  const uint32_t *fin_inst;
+  const uint32_t *row_ptr;
+  const uint32_t *col;
+  void *V;
+  uint64_t vs;  // vector stride (elements)
+  Scalars sc;
+  RedBufs red;
+  double *cpart;   // per heavy-row chunk partial sums
+  uint32_t *hcnt;  // per heavy row arrival counters
+  double tau;      // breakdown tolerance
+};
+
+// Column indices are read once per step: streaming (evict-first) load.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(p); }
+
+template <typename T>
+__device__ __forceinline__ T ld_vec(const T *p) {
+  return __ldg(p);
+}
+
+// Row epilogue: u = sj*sum - bp*W_{j-1}[row]; store; return W_j[row]*u.
+template <typename T>
+__device__ __forceinline__ T row_epilogue(T sum, uint32_t row, const T *x, const T *xp, T *out,
+                                          T sj, T bp, bool has_prev) {
+  T u = sj * sum;
+  if (has_prev) u -= bp * xp[row];
+  out[row] = u;
+  return x[row] * u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) init_vec_kernel(LArgs a, uint32_t r0, uint32_t r1) {
+  // W_0 = 1 on every realisation's node range.
+  for (uint32_t r = r0; r < r1; ++r) {
+    const InstDesc I = a.inst[r];
+    T *w0 = reinterpret_cast<T *>(a.V) + I.node_base;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I.n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+      w0[i] = T(1);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_t r0, uint32_t r1,
+                                                                uint32_t m) {
+  const uint32_t ms = a.sc.ms;
+  const uint64_t total = (uint64_t)(r1 - r0) * ms;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = r0 + (uint32_t)(q / ms), jj = (uint32_t)(q % ms);
+    const uint64_t o = (uint64_t)r * ms + jj;
+    a.sc.alpha[o] = 0.0;
+    a.sc.beta[o] = 0.0;
+    a.sc.gamma[o] = 0.0;
+    a.sc.scale[o] = jj == 0 ? 1.0 / sqrt((double)a.inst[r].n) : 0.0;
+    if (jj == 0) {
+      a.sc.meff[r] = m;
+      a.sc.status[r] = CB_OK;
+      a.sc.theta[r] = 0.0;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void finish_alpha(const LArgs &a, uint32_t r, uint32_t j, double total) {
+  const uint32_t ms = a.sc.ms;
+  const double alpha = a.sc.scale[r * ms + j] * total;
+  a.sc.alpha[r * ms + j] = alpha;
+  if (!isfinite(alpha)) {
+    a.sc.status[r] = CB_ERR_NONFINITE;
+    a.sc.meff[r] = j;  // stop; this realisation is reported as failed
+  }
+}
+
+// One Lanczos SpMV step over a range of realisations.
+// Blocks [0, n_chunks) are heavy-row chunks starting at chunk_off; blocks
+// [n_chunks, ...) are normal tiles starting at tile_off.
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uint32_t chunk_off,
+                                                        uint32_t n_chunks, uint32_t tile_off) {
+  __shared__ double s_red[32];
+  __shared__ uint32_t s_med[kTileRows];
+  __shared__ uint32_t s_long[kTileRows];
+  __shared__ uint32_t s_nmed, s_nlong;
+  __shared__ int s_last;
+  __shared__ T s_rowsum[32];
+
+  const uint32_t ms = a.sc.ms;
+  const bool is_chunk = blockIdx.x < n_chunks;
+  uint32_t r;
+  uint32_t hid = 0, cidx = 0, tile = 0;
+  if (is_chunk) {
+    cidx = chunk_off + blockIdx.x;
+    hid = a.chunk_heavy[cidx];
+    r = a.heavy[hid].inst;
+  } else {
+    tile = tile_off + (blockIdx.x - n_chunks);
+    r = a.tile_inst[tile];
+  }
+  if (j >= a.sc.meff[r]) return;  // realisation stopped (uniform per CTA)
+
+  const InstDesc &I = a.inst[r];
+  const uint32_t *rp = a.row_ptr + I.rp_base;
+  const uint32_t *col = a.col + I.edge_base;
+  T *Vb = reinterpret_cast<T *>(a.V);
+  const T *x = Vb + (uint64_t)j * a.vs + I.node_base;
+  const bool has_prev = j > 0;
+  const T *xp = has_prev ? Vb + (uint64_t)(j - 1) * a.vs + I.node_base : x;
+  T *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
+  const T sj = (T)a.sc.scale[r * ms + j];
+  const T bp = has_prev ? (T)(a.sc.beta[r * ms + j - 1] * a.sc.scale[r * ms + j - 1]) : T(0);
+
+  if (is_chunk) {
+    // ---- one chunk of a heavy row ----
+    const HeavyRow H = a.heavy[hid];
+    const uint32_t c = cidx - H.chunk_base;
+    const uint32_t e0 = rp[H.row] + c * kChunk;
+    const uint32_t e1 = min(e0 + kChunk, rp[H.row + 1]);
+    T s = T(0);
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kThreads) s += ld_vec(x + ld_stream(col + e));
+    const double part = block_sum_to_double<T>(s, s_red);
+    if (threadIdx.x == 0) {
+      a.cpart[cidx] = part;
+      __threadfence();
+      const uint32_t prev = atomicAdd(&a.hcnt[hid], 1u);
+      s_last = (prev == H.n_chunks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double dot = 0.0;
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (uint32_t q = 0; q < H.n_chunks; ++q) tot += __ldcg(&a.cpart[H.chunk_base + q]);
+      a.hcnt[hid] = 0u;
+      dot = (double)row_epilogue<T>((T)tot, H.row, x, xp, out, sj, bp, has_prev);
+    }
+    const uint32_t slot = I.n_tiles + (hid - I.heavy_base);
+    double total;
+    if (arrive_and_reduce(I.spmv, slot, r, dot, a.red, &total)) finish_alpha<T>(a, r, j, total);
+    return;
+  }
+
+  // ---- normal tile ----
+  const uint32_t row0 = (tile - I.tile_base) * kTileRows;
+  const uint32_t row1 = min(row0 + kTileRows, I.n);
+  if (threadIdx.x == 0) { s_nmed = 0; s_nlong = 0; }
+  __syncthreads();
+
+  T acc = T(0);
+  const uint32_t lane_g = threadIdx.x % G;
+  const uint32_t grp = threadIdx.x / G;
+  constexpr uint32_t kGroups = kThreads / G;
+  constexpr uint32_t kShort = 8 * G;
+  for (uint32_t row = row0 + grp; row < row1; row += kGroups) {
+    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    const uint32_t deg = e1 - e0;
+    if (deg > kShort) {
+      if (lane_g == 0 && deg <= kHeavyDeg) {
+        if (deg <= kLongDeg) s_med[atomicAdd(&s_nmed, 1u)] = row;
+        else s_long[atomicAdd(&s_nlong, 1u)] = row;
+      }
+      continue;
+    }
+    T s = T(0);
+#pragma unroll 4
+    for (uint32_t e = e0 + lane_g; e < e1; e += G) s += ld_vec(x + ld_stream(col + e));
+    s = group_sum<G, T>(s);
+    if (lane_g == 0) acc += row_epilogue<T>(s, row, x, xp, out, sj, bp, has_prev);
+  }
+  __syncthreads();
+
+  // medium rows: one warp per row
+  {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nmed = s_nmed;
+    for (uint32_t q = warp; q < nmed; q += kThreads / 32) {
+      const uint32_t row = s_med[q];
+      const uint32_t e0 = rp[row], e1 = rp[row + 1];
+      T s = T(0);
+#pragma unroll 4
+      for (uint32_t e = e0 + lane; e < e1; e += 32) s += ld_vec(x + ld_stream(col + e));
+      s = warp_sum<T>(s);
+      if (lane == 0) acc += row_epilogue<T>(s, row, x, xp, out, sj, bp, has_prev);
+    }
+  }
+
+  // long rows: the whole CTA per row (uniform loop bound)
+  const uint32_t nlong = s_nlong;
+  for (uint32_t q = 0; q < nlong; ++q) {
+    const uint32_t row = s_long[q];
+    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    T s = T(0);
+#pragma unroll 4
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kThreads) s += ld_vec(x + ld_stream(col + e));
+    s = warp_sum<T>(s);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_rowsum[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T tot = T(0);
+      for (int w = 0; w < kThreads / 32; ++w) tot += s_rowsum[w];
+      acc += row_epilogue<T>(tot, row, x, xp, out, sj, bp, has_prev);
+    }
+    __syncthreads();
+  }
+
+  const double part = block_sum_to_double<T>(acc, s_red);
+  double total;
+  if (arrive_and_reduce(I.spmv, tile - I.tile_base, r, part, a.red, &total))
+    finish_alpha<T>(a, r, j, total);
+}
+
+// w = W_{j+1} - alpha_j scale_j W_j, in place; beta_j = ||w||.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j, uint32_t fin_off) {
+  __shared__ double s_red[32];
+  const uint32_t t = fin_off + blockIdx.x;
+  const uint32_t r = a.fin_inst[t];
+  if (j >= a.sc.meff[r]) return;
+  const InstDesc &I = a.inst[r];
+  const uint32_t ms = a.sc.ms;
+  T *Vb = reinterpret_cast<T *>(a.V);
+  const T *x = Vb + (uint64_t)j * a.vs + I.node_base;
+  T *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
+  const T coef = (T)(a.sc.alpha[r * ms + j] * a.sc.scale[r * ms + j]);
+  const uint32_t i0 = (t - I.fin_base) * kFinRows;
+  const uint32_t i1 = min(i0 + kFinRows, I.n);
+  T acc = T(0);
+  for (uint32_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+    const T w = out[i] - coef * x[i];
+    out[i] = w;
+    acc += w * w;
+  }
+  const double part = block_sum_to_double<T>(acc, s_red);
+  double total;
+  if (arrive_and_reduce(I.fin, t - I.fin_base, r, part, a.red, &total)) {
+    const double beta = sqrt(total);
+    const double alpha = a.sc.alpha[r * ms + j];
+    const double bprev = j > 0 ? a.sc.beta[r * ms + j - 1] : 0.0;
+    a.sc.beta[r * ms + j] = beta;
+    if (!isfinite(beta)) {
+      a.sc.status[r] = CB_ERR_NONFINITE;
+      a.sc.meff[r] = j + 1;
+    } else if (beta <= a.tau * (fabs(alpha) + bprev) || beta == 0.0) {
+      a.sc.meff[r] = j + 1;  // exact breakdown: K_{j+1}(A,1) is invariant
+    } else {
+      a.sc.scale[r * ms + j + 1] = 1.0 / beta;
+    }
+  }
+}
+
+template <typename T, int G>
+static void launch_spmv(const LArgs &a, uint32_t j, uint32_t chunk_off, uint32_t n_chunks,
+                        uint32_t tile_off, uint32_t n_tiles, cudaStream_t s) {
+  const uint32_t grid = n_chunks + n_tiles;
+  if (grid) spmv_kernel<T, G><<<grid, kThreads, 0, s>>>(a, j, chunk_off, n_chunks, tile_off);
+}
+
+template <typename T>
+static void launch_spmv_lanes(int lanes, const LArgs &a, uint32_t j, uint32_t co, uint32_t nc,
+                              uint32_t to, uint32_t nt, cudaStream_t s) {
+  switch (lanes) {
+    case 1: launch_spmv<T, 1>(a, j, co, nc, to, nt, s); break;
+    case 2: launch_spmv<T, 2>(a, j, co, nc, to, nt, s); break;
+    case 4: launch_spmv<T, 4>(a, j, co, nc, to, nt, s); break;
+    case 8: launch_spmv<T, 8>(a, j, co, nc, to, nt, s); break;
+    case 16: launch_spmv<T, 16>(a, j, co, nc, to, nt, s); break;
+    default: launch_spmv<T, 32>(a, j, co, nc, to, nt, s); break;
+  }
+}
+
+template <typename T>
+static int run_t(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t s) {
+  Workspace &W = h->ws;
+  LArgs a;
+  a.inst = h->d_inst;
+  a.tile_inst = h->d_tile_inst;
+  a.heavy = h->d_heavy;
+  a.chunk_heavy = h->d_chunk_heavy;
+  a.fin_inst = h->d_fin_inst;
+  a.row_ptr = h->row_ptr;
+  a.col = h->col;
+  a.V = W.V;
+  a.vs = W.vec_stride;
+  a.sc = W.sc;
+  a.red = RedBufs{W.part, W.gpart, W.gcnt, W.icnt};
+  a.cpart = W.cpart;
+  a.hcnt = W.hcnt;
+  a.tau = sizeof(T) == 4 ? 1e-5 : 1e-12;
+
+  const InstDesc &A0 = h->inst[r0], &A1 = h->inst[r1 - 1];
+  const uint32_t chunk_off = A0.chunk_base;
+  const uint32_t n_chunks = A1.chunk_base + A1.n_chunks - chunk_off;
+  const uint32_t tile_off = A0.tile_base;
+  const uint32_t n_tiles = A1.tile_base + A1.n_tiles - tile_off;
+  const uint32_t fin_off = A0.fin_base;
+  const uint32_t n_fin = A1.fin_base + A1.n_fin - fin_off;
+
+  uint32_t nmax = 0;
+  for (uint32_t r = r0; r < r1; ++r) nmax = h->inst[r].n > nmax ? h->inst[r].n : nmax;
+  const uint32_t init_grid = (nmax + kThreads * 8 - 1) / (kThreads * 8);
+  int tok = prof_begin(CB_K_INIT, s);
+  init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1);
+  const uint64_t nsc = (uint64_t)(r1 - r0) * W.sc.ms;
+  init_scalars_kernel<<<(uint32_t)((nsc + kThreads - 1) / kThreads), kThreads, 0, s>>>(a, r0, r1, m);
+  prof_end(tok, s);
+  for (uint32_t j = 0; j < m; ++j) {
+    tok = prof_begin(CB_K_SPMV, s);
+    launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);
+    prof_end(tok, s);
+    tok = prof_begin(CB_K_FINALIZE, s);
+    if (n_fin) finalize_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off);
+    prof_end(tok, s);
+  }
+  return cuda_error(cudaGetLastError(), "lanczos launch");
+}
+
+int lanczos_run(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, int prec, cudaStream_t s) {
+  return prec == CB_FP64 ? run_t<double>(h, r0, r1, m, s) : run_t<float>(h, r0, r1, m, s);
+}
+
+}  // namespace cb

@@ -1,0 +1,218 @@
+// Top-k selection of the summed scores ("the largest 20 EBTC values").
+//
+// The paper sorts all n scores (Introsort, O(n log n)).  Only the k largest
+// are needed, so this selects them by most-significant-digit radix select
+// and sorts just those k:
+//
+//  * each score maps to an order-preserving 64-bit key (NaN lowest, -0 = +0)
+//    and the key is extended by the complemented node index, so the 96-bit
+//    composite keys are distinct and larger composite = larger score, ties
+//    to the smaller index;
+//  * pass L (L = 0..11) histograms byte L of the composite key over the
+//    elements whose bytes 0..L-1 equal the prefix found so far; the last CTA
+//    to finish picks the byte where the count from the top reaches the
+//    number still needed, and stops the passes as soon as the whole bucket
+//    is needed;
+//  * one pass collects the k elements at or above the prefix, one CTA sorts
+//    them (bitonic) and writes indices and values.
+//
+// Every pass is launched unconditionally and returns at once when the
+// selection is complete, so the sequence needs no host round trip.
+#include "cb_internal.cuh"
+
+namespace cb {
+
+namespace {
+
+struct TopkState {
+  unsigned long long phi;  // prefix of the 64-bit score key (unfixed bits zero)
+  uint32_t plo;            // prefix of the complemented index
+  uint32_t level;          // bytes fixed so far (0..12)
+  uint32_t krem;           // elements still needed inside the prefix bucket
+  uint32_t done;
+  uint32_t arrive;
+  uint32_t ncol;
+  uint32_t hist[256];
+};
+
+struct Cand {
+  unsigned long long key;
+  uint32_t idx;
+  uint32_t pad;
+};
+
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  if (v != v) return 0ull;  // NaN ranks below every number
+  if (v == 0.0) v = 0.0;    // -0.0 -> +0.0
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ unsigned long long mask_hi(uint32_t L) {
+  return L == 0 ? 0ull : (L >= 8 ? ~0ull : (~0ull << (64 - 8 * L)));
+}
+__device__ __forceinline__ uint32_t mask_lo(uint32_t L) {
+  return L <= 8 ? 0u : (L >= 12 ? ~0u : (~0u << (32 - 8 * (L - 8))));
+}
+__device__ __forceinline__ uint32_t digit(unsigned long long hi, uint32_t lo, uint32_t L) {
+  return L < 8 ? (uint32_t)((hi >> (56 - 8 * L)) & 255ull) : ((lo >> (24 - 8 * (L - 8))) & 255u);
+}
+
+__global__ void topk_init(TopkState *st, uint32_t k) {
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) st->hist[d] = 0;
+  if (threadIdx.x == 0) {
+    st->phi = 0ull;
+    st->plo = 0u;
+    st->level = 0u;
+    st->krem = k;
+    st->done = 0u;
+    st->arrive = 0u;
+    st->ncol = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(256) topk_pass(const double *__restrict__ S, uint32_t n,
+                                                 TopkState *st, uint32_t L) {
+  __shared__ uint32_t sh[256];
+  __shared__ int s_last;
+  if (st->done) return;
+  const unsigned long long phi = st->phi, mh = mask_hi(L);
+  const uint32_t plo = st->plo, ml = mask_lo(L);
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long key = order_key(__ldg(S + i));
+    const uint32_t lo = ~i;
+    if ((key & mh) == phi && (lo & ml) == plo) atomicAdd(&sh[digit(key, lo, L)], 1u);
+  }
+  __syncthreads();
+  if (sh[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], sh[threadIdx.x]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&st->arrive, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    const uint32_t krem = st->krem;
+    uint32_t cum = 0, dstar = 0, hstar = 0;
+    for (int d = 255; d >= 0; --d) {
+      const uint32_t hd = __ldcg(&st->hist[d]);
+      if (cum + hd >= krem) {
+        dstar = (uint32_t)d;
+        hstar = hd;
+        break;
+      }
+      cum += hd;
+    }
+    if (L < 8) st->phi = phi | ((unsigned long long)dstar << (56 - 8 * L));
+    else st->plo = plo | (dstar << (24 - 8 * (L - 8)));
+    const uint32_t left = krem - cum;
+    st->krem = left;
+    st->level = L + 1;
+    if (hstar == left || L + 1 >= 12) st->done = 1u;
+    st->arrive = 0u;
+  }
+  __syncthreads();
+  st->hist[threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) topk_collect(const double *__restrict__ S, uint32_t n,
+                                                    TopkState *st, Cand *buf, uint32_t k) {
+  const uint32_t L = st->level;
+  const unsigned long long mh = mask_hi(L), phi = st->phi;
+  const uint32_t ml = mask_lo(L), plo = st->plo;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long key = order_key(__ldg(S + i));
+    const uint32_t lo = ~i;
+    const unsigned long long kh = key & mh;
+    if (kh > phi || (kh == phi && (lo & ml) >= plo)) {
+      const uint32_t pos = atomicAdd(&st->ncol, 1u);
+      if (pos < k) buf[pos] = Cand{key, i, 0u};
+    }
+  }
+}
+
+// (key desc, idx asc) ordering: a goes before b
+__device__ __forceinline__ bool before(unsigned long long ka, uint32_t ia, unsigned long long kb,
+                                       uint32_t ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
+__global__ void __launch_bounds__(1024) topk_sort(const double *__restrict__ S, const Cand *buf,
+                                                  uint32_t k, uint32_t P, uint32_t *idx,
+                                                  double *val) {
+  extern __shared__ unsigned char s_raw[];
+  unsigned long long *sk = reinterpret_cast<unsigned long long *>(s_raw);
+  uint32_t *si = reinterpret_cast<uint32_t *>(sk + P);
+  for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) {
+    if (q < k) { sk[q] = buf[q].key; si[q] = buf[q].idx; }
+    else { sk[q] = 0ull; si[q] = 0xffffffffu; }
+  }
+  __syncthreads();
+  for (uint32_t size = 2; size <= P; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) {
+        const uint32_t p = q ^ stride;
+        if (p > q) {
+          const bool desc = (q & size) == 0;  // first half of each block in final order
+          const bool swap = desc ? before(sk[p], si[p], sk[q], si[q])
+                                 : before(sk[q], si[q], sk[p], si[p]);
+          if (swap) {
+            const unsigned long long tk = sk[q]; sk[q] = sk[p]; sk[p] = tk;
+            const uint32_t ti = si[q]; si[q] = si[p]; si[p] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t q = threadIdx.x; q < k; q += blockDim.x) {
+    idx[q] = si[q];
+    val[q] = S[si[q]];
+  }
+}
+
+}  // namespace
+
+int topk_launch(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
+                void *scratch, cudaStream_t s) {
+  TopkState *st = reinterpret_cast<TopkState *>(scratch);
+  Cand *buf = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) +
+                                       ((sizeof(TopkState) + 255) / 256) * 256);
+  uint32_t grid = (n + 256 * 8 - 1) / (256 * 8);
+  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid == 0) grid = 1;
+  const int tok = prof_begin(CB_K_TOPK, s);
+  topk_init<<<1, 256, 0, s>>>(st, k);
+  for (uint32_t L = 0; L < 12; ++L) topk_pass<<<grid, 256, 0, s>>>(S, n, st, L);
+  topk_collect<<<grid, 256, 0, s>>>(S, n, st, buf, k);
+  uint32_t P = 1;
+  while (P < k) P <<= 1;
+  const size_t shm = (size_t)P * (sizeof(unsigned long long) + sizeof(uint32_t));
+  topk_sort<<<1, 1024, shm, s>>>(S, buf, k, P, idx, val);
+  prof_end(tok, s);
+  return cuda_error(cudaGetLastError(), "topk launch");
+}
+
+size_t topk_scratch_bytes(uint32_t k) {
+  return ((sizeof(TopkState) + 255) / 256) * 256 + (size_t)k * sizeof(Cand);
+}
+
+}  // namespace cb
+
+CB_API int cb_topk(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
+                   void *stream) {
+  using namespace cb;
+  if (!S || !idx || !val) return set_error(CB_ERR_ARG, "cb_topk: null pointer");
+  if (n == 0 || k == 0 || k > n || k > CB_MAX_TOPK)
+    return set_error(CB_ERR_ARG, "cb_topk: need 1 <= k <= min(n, CB_MAX_TOPK)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, topk_scratch_bytes(k), s);
+  if (e != cudaSuccess) return cuda_error(e, "cb_topk: cudaMallocAsync");
+  int rc = topk_launch(S, n, k, idx, val, scratch, s);
+  e = cudaFreeAsync(scratch, s);
+  if (rc != CB_OK) return rc;
+  return cuda_error(e, "cb_topk: cudaFreeAsync");
+}

@@ -1,0 +1,211 @@
+"""CUDA path vs the FP64 oracle, element by element (needs a GB300).
+
+Every case runs through the C ABI (via the ctypes binding) on seeded
+synthetic graphs shaped like the paper's workloads, at sizes the oracle
+finishes in seconds, spanning several SpMV tiles, reduction groups and a
+ragged tail, plus the degenerate cases of the method.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.communicability as oc
+from paper_1409_5000_gb300 import synth
+from tests import parity, pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp32": 0, "fp64": 1}
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1409_5000_gb300 import binding
+
+    binding.lib()  # raises if libcb.so is missing: no fallback
+    return binding
+
+
+def _single(B, g, m, prec):
+    with B.GraphSet([g]) as gs:
+        ls, y, rep = B.communicability(gs, 0, m, PREC[prec], report=True)
+        torch.cuda.synchronize()
+        return float(ls.item()), y.cpu().numpy(), rep
+
+
+class _G:
+    def __init__(self, n, rp, col):
+        self.n, self.row_ptr, self.col = n, rp, col
+
+
+CLOSED = [(name, mk) for name, mk in pins.CLOSED]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CLOSED, ids=[c[0] for c in CLOSED])
+def test_closed_forms(B, case, prec):
+    name, mk = case
+    (n, rp, col), ref, dim = mk()
+    theta, y, rep = _single(B, _G(n, rp, col), 20, prec)
+    s = np.exp(theta) * y
+    tol = parity.TOL_FP64 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(s - ref) / ref) <= tol, (name, np.max(np.abs(s - ref) / ref))
+    if prec == "fp64":
+        assert rep.m_eff == dim
+
+
+def test_single_isolated_node(B):
+    g = synth.from_edges(1, np.zeros((0, 2), np.uint32))
+    for prec in ("fp64", "fp32"):
+        theta, y, rep = _single(B, g, 10, prec)
+        assert rep.m_eff == 1 and abs(math.exp(theta) * y[0] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_er_ensemble_small(B, prec):
+    """10 x ER(500, p=0.016) + 15-node sparse target, m = 20, top-15."""
+    ens = synth.er_ensemble_small()
+    m, k = ens.meta["m"], ens.meta["k"]
+    gs_o = [(g.n, g.row_ptr, g.col) for g in ens.graphs]
+    theta_o, S_o = oc.ensemble_scores(gs_o, m)
+    with B.GraphSet(ens.graphs) as gs:
+        ls, S, rep = B.ensemble_scores(gs, m, PREC[prec], report=True)
+        idx, val = B.topk(S, k)
+        torch.cuda.synchronize()
+        e = parity.assert_scores(ls.item(), S.cpu().numpy(), theta_o, S_o, prec)
+        tol = parity.TOL_FP64 if prec == "fp64" else parity.TOL_FP32
+        parity.assert_topk(idx.cpu().numpy(), val.cpu().numpy(), S_o, k, tol)
+        assert all(r.m_eff == m and r.status == 0 for r in rep)
+    # each realisation alone through the plain per-graph call
+    with B.GraphSet(ens.graphs) as gs:
+        for r in (0, 9):
+            ls, y = B.communicability(gs, r, m, PREC[prec])
+            th_o, y_o, _ = oc.krylov_expv(*gs_o[r], m)
+            parity.assert_scores(ls.item(), y.cpu().numpy(), th_o, y_o, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uneven_ensemble(B, prec):
+    """8 ER realisations, n ~ U[2e3, 4e4], dbar 20, 30-node target, m = 25:
+    many tiles, several reduction groups, ragged tails, padding (eq. 5)."""
+    ens = synth.er_ensemble_uneven(n_inst=8, n_lo=2_000, n_hi=40_000, config=303)
+    m = ens.meta["m"]
+    gs_o = [(g.n, g.row_ptr, g.col) for g in ens.graphs]
+    theta_o, S_o = oc.ensemble_scores(gs_o, m)
+    with B.GraphSet(ens.graphs) as gs:
+        ls, S = B.ensemble_scores(gs, m, PREC[prec], n_out=ens.n_max + 37)
+        S = S.cpu().numpy()
+        assert np.all(S[ens.n_max:] == 0.0)
+        parity.assert_scores(ls.item(), S[: ens.n_max], theta_o, S_o, prec)
+        idx, val = B.topk(torch.from_numpy(S).cuda(), 30)
+        tol = parity.TOL_FP64 if prec == "fp64" else parity.TOL_FP32
+        parity.assert_topk(idx.cpu().numpy(), val.cpu().numpy(), S_o[: ens.n_max], 30, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["er", "ba", "ws"])
+def test_single_background_clique(B, kind, prec):
+    """n = 1e5 ER / BA / WS + planted 12-clique, m = 30 (BA rows reach the
+    warp and whole-CTA tiers)."""
+    ens = synth.single_clique_100k(kind)
+    g = ens.graphs[0]
+    m = ens.meta["m"]
+    th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, m)
+    theta, y, rep = _single(B, g, m, prec)
+    parity.assert_scores(theta, y, th_o, y_o, prec)
+    tol = parity.TOL_FP64 if prec == "fp64" else parity.TOL_FP32
+    with B.GraphSet([g]) as gs:
+        ls, yy = B.communicability(gs, 0, m, PREC[prec])
+        idx, val = B.topk(yy, 12)
+        parity.assert_topk(idx.cpu().numpy(), val.cpu().numpy(), y_o, 12, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_heavy_rows(B, prec):
+    """A hub of degree ~20000 (split across CTAs), rows of degree 1024-8192
+    (whole-CTA tier) and ordinary ER rows."""
+    n = 30_000
+    rng = np.random.default_rng(11)
+    hub = [(0, j) for j in range(1, 20_001)]
+    mid = [(1, int(j)) for j in rng.choice(np.arange(2, n), 3000, replace=False)]
+    mid += [(2, int(j)) for j in rng.choice(np.arange(3, n), 1500, replace=False)]
+    g0 = synth.er(n, 6.0 / n, 5)
+    src = np.repeat(np.arange(n), np.diff(g0.row_ptr.astype(np.int64)))
+    base = [(int(a), int(b)) for a, b in zip(src, g0.col) if a < b]
+    g = synth.from_edges(n, base + hub + mid)
+    assert g.degrees().max() > 8192
+    th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 30)
+    theta, y, _ = _single(B, g, 30, prec)
+    parity.assert_scores(theta, y, th_o, y_o, prec)
+
+
+def test_empty_and_complete_breakdown(B):
+    g = synth.from_edges(5000, np.zeros((0, 2), np.uint32))
+    theta, y, rep = _single(B, g, 30, "fp32")
+    assert rep.m_eff == 1 and np.allclose(np.exp(theta) * y, 1.0, rtol=1e-7)
+    g = synth.from_edges(40, np.array(pins.complete(40)))
+    theta, y, rep = _single(B, g, 30, "fp32")
+    assert rep.m_eff == 1 and np.allclose(np.exp(theta) * y, math.exp(39), rtol=1e-6)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (7, 7), (1000, 1), (100_000, 64), (1_234_567, 20),
+                                 (50_000, 4096)])
+def test_topk_bit_exact(B, n, k):
+    rng = np.random.default_rng(n + k)
+    S = rng.integers(0, 50, size=n).astype(np.float64) * 0.25  # many exact ties
+    S[rng.integers(0, n, size=max(1, n // 100))] = -0.0
+    S[rng.integers(0, n, size=max(1, n // 100))] = np.nan
+    if n > 10:
+        S[3] = np.inf
+        S[5] = -np.inf
+    idx, val = B.topk(torch.from_numpy(S).cuda(), k)
+    ref_idx, ref_val = oc.topk(S, k)
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), ref_idx)
+    assert np.array_equal(val.cpu().numpy(), ref_val, equal_nan=True)
+
+
+def test_topk_distinct_values(B):
+    rng = np.random.default_rng(1)
+    S = np.exp(rng.normal(size=3_000_000) * 3)
+    idx, val = B.topk(torch.from_numpy(S).cuda(), 100)
+    ref_idx, ref_val = oc.topk(S, 100)
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), ref_idx)
+    assert np.array_equal(val.cpu().numpy(), ref_val)
+
+
+def test_deterministic(B):
+    ens = synth.er_ensemble_uneven(n_inst=6, n_lo=5_000, n_hi=60_000, config=304)
+    with B.GraphSet(ens.graphs) as gs:
+        a = B.ensemble_scores(gs, 25, 0)[1].cpu().numpy()
+        b = B.ensemble_scores(gs, 25, 0)[1].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_max_depth(B):
+    g = synth.er(3000, 8.0 / 3000, 9)
+    th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 128)
+    theta, y, rep = _single(B, g, 128, "fp64")
+    parity.assert_scores(theta, y, th_o, y_o, "fp64")
+
+
+def test_argument_errors(B):
+    g = synth.er(100, 0.05, 1)
+    with B.GraphSet([g]) as gs:
+        with pytest.raises(B.CBError):
+            B.communicability(gs, 1, 10)  # realisation out of range
+        with pytest.raises(B.CBError):
+            B.communicability(gs, 0, 0)
+        with pytest.raises(B.CBError):
+            B.communicability(gs, 0, B.CB_MAX_M + 1)
+        with pytest.raises(B.CBError):
+            B.ensemble_scores(gs, 10, n_out=50)
+    S = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.CBError):
+        B.topk(S, 11)
+    bad = _G(3, np.array([0, 1, 1, 1], np.uint32), np.array([2], np.uint32))  # not symmetric
+    with pytest.raises(B.CBError):
+        B.GraphSet([bad], validate=True)
