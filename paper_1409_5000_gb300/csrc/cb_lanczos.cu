@@ -121,13 +121,15 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uint32_t chunk_off,
                                                         uint32_t n_chunks, uint32_t tile_off) {
   __shared__ double s_red[32];
-  __shared__ uint32_t s_med[kTileRows];
-  __shared__ uint32_t s_long[kTileRows];
+  __shared__ uint32_t s_rp[kTileRows + 1];
+  __shared__ uint16_t s_med[kTileRows], s_long[kTileRows];
+  __shared__ uint32_t s_wcnt[kThreads / 32][2];
   __shared__ uint32_t s_nmed, s_nlong;
   __shared__ int s_last;
   __shared__ T s_rowsum[32];
 
   const uint32_t ms = a.sc.ms;
+  static_assert(kTileRows == kThreads, "one tile row per thread in the row classification");
   const bool is_chunk = blockIdx.x < n_chunks;
   uint32_t r;
   uint32_t hid = 0, cidx = 0, tile = 0;
@@ -185,8 +187,9 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
 
   // ---- normal tile ----
   const uint32_t row0 = (tile - I.tile_base) * kTileRows;
-  const uint32_t row1 = min(row0 + kTileRows, I.n);
-  if (threadIdx.x == 0) { s_nmed = 0; s_nlong = 0; }
+  const uint32_t nrows = min((uint32_t)kTileRows, I.n - row0);
+  // the tile's row offsets, staged once (coalesced)
+  for (uint32_t q = threadIdx.x; q <= nrows; q += kThreads) s_rp[q] = rp[row0 + q];
   __syncthreads();
 
   T acc = T(0);
@@ -194,44 +197,70 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
   const uint32_t grp = threadIdx.x / G;
   constexpr uint32_t kGroups = kThreads / G;
   constexpr uint32_t kShort = 8 * G;
-  for (uint32_t row = row0 + grp; row < row1; row += kGroups) {
-    const uint32_t e0 = rp[row], e1 = rp[row + 1];
-    const uint32_t deg = e1 - e0;
-    if (deg > kShort) {
-      if (lane_g == 0 && deg <= kHeavyDeg) {
-        if (deg <= kLongDeg) s_med[atomicAdd(&s_nmed, 1u)] = row;
-        else s_long[atomicAdd(&s_nlong, 1u)] = row;
-      }
-      continue;
-    }
+  // Short rows: G lanes per row.  The trip count depends only on the tile,
+  // so every lane of a warp runs every iteration and the full-mask group
+  // shuffles are always converged.
+  for (uint32_t base = 0; base < nrows; base += kGroups) {
+    const uint32_t lr = base + grp;
+    const bool valid = lr < nrows;
+    uint32_t e0 = 0, e1 = 0;
+    if (valid) { e0 = s_rp[lr]; e1 = s_rp[lr + 1]; }
+    const bool is_short = valid && (e1 - e0) <= kShort;
     T s = T(0);
+    if (is_short) {
 #pragma unroll 4
-    for (uint32_t e = e0 + lane_g; e < e1; e += G) s += ld_vec(x + ld_stream(col + e));
+      for (uint32_t e = e0 + lane_g; e < e1; e += G) s += ld_vec(x + ld_stream(col + e));
+    }
     s = group_sum<G, T>(s);
-    if (lane_g == 0) acc += row_epilogue<T>(s, row, x, xp, out, sj, bp, has_prev);
+    if (is_short && lane_g == 0) acc += row_epilogue<T>(s, row0 + lr, x, xp, out, sj, bp, has_prev);
+  }
+
+  // Medium (kShort < deg <= kLongDeg) and long (kLongDeg < deg <= kHeavyDeg)
+  // rows: lists in row order, built with one ballot per warp (thread q
+  // classifies row q of the tile), so the processing order is fixed.
+  {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lr = threadIdx.x;  // kTileRows == kThreads
+    uint32_t deg = 0;
+    if (lr < nrows) deg = s_rp[lr + 1] - s_rp[lr];
+    const bool med = deg > kShort && deg <= kLongDeg;
+    const bool lng = deg > kLongDeg && deg <= kHeavyDeg;
+    const uint32_t bm = __ballot_sync(0xffffffffu, med), bl = __ballot_sync(0xffffffffu, lng);
+    if (lane == 0) { s_wcnt[warp][0] = __popc(bm); s_wcnt[warp][1] = __popc(bl); }
+    __syncthreads();
+    uint32_t om = 0, ol = 0, nm = 0, nl = 0;
+    for (uint32_t w = 0; w < kThreads / 32; ++w) {
+      if (w < warp) { om += s_wcnt[w][0]; ol += s_wcnt[w][1]; }
+      nm += s_wcnt[w][0];
+      nl += s_wcnt[w][1];
+    }
+    const uint32_t below = (1u << lane) - 1u;
+    if (med) s_med[om + __popc(bm & below)] = lr;
+    if (lng) s_long[ol + __popc(bl & below)] = lr;
+    if (threadIdx.x == 0) { s_nmed = nm; s_nlong = nl; }
   }
   __syncthreads();
 
-  // medium rows: one warp per row
+  // medium rows: warp w takes list entries w, w+8, ...
   {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nmed = s_nmed;
     for (uint32_t q = warp; q < nmed; q += kThreads / 32) {
-      const uint32_t row = s_med[q];
-      const uint32_t e0 = rp[row], e1 = rp[row + 1];
+      const uint32_t lr = s_med[q];
+      const uint32_t e0 = s_rp[lr], e1 = s_rp[lr + 1];
       T s = T(0);
 #pragma unroll 4
       for (uint32_t e = e0 + lane; e < e1; e += 32) s += ld_vec(x + ld_stream(col + e));
       s = warp_sum<T>(s);
-      if (lane == 0) acc += row_epilogue<T>(s, row, x, xp, out, sj, bp, has_prev);
+      if (lane == 0) acc += row_epilogue<T>(s, row0 + lr, x, xp, out, sj, bp, has_prev);
     }
   }
 
-  // long rows: the whole CTA per row (uniform loop bound)
+  // long rows: the whole CTA per row, in row order
   const uint32_t nlong = s_nlong;
   for (uint32_t q = 0; q < nlong; ++q) {
-    const uint32_t row = s_long[q];
-    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    const uint32_t lr = s_long[q];
+    const uint32_t e0 = s_rp[lr], e1 = s_rp[lr + 1];
     T s = T(0);
 #pragma unroll 4
     for (uint32_t e = e0 + threadIdx.x; e < e1; e += kThreads) s += ld_vec(x + ld_stream(col + e));
@@ -242,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
     if (threadIdx.x == 0) {
       T tot = T(0);
       for (int w = 0; w < kThreads / 32; ++w) tot += s_rowsum[w];
-      acc += row_epilogue<T>(tot, row, x, xp, out, sj, bp, has_prev);
+      acc += row_epilogue<T>(tot, row0 + lr, x, xp, out, sj, bp, has_prev);
     }
     __syncthreads();
   }

@@ -4,10 +4,14 @@ Scores are compared as exp(theta) * y without forming the exponential:
 the CUDA result is rescaled by exp(theta_gpu - theta_oracle).
 
 Bars (stated as numbers, see the design notes for their derivation):
-* FP64 mode: every score within 1e-10 relative.
 * FP32 mode: every score in the ranking head (score >= 1e-3 of the
   largest) within 1e-4 relative, and the whole vector within 1e-4 in the
   2-norm; the largest relative error over all nodes is reported too.
+* FP64 mode: the same structure at 1e-10.  Scores far below the maximum
+  carry only the absolute accuracy of the m-step approximation (about
+  eps * max score), so no per-score bound holds there; where the
+  approximation has converged (``assert_scores_all``) every score is
+  checked.
 * top-k indices: bit-exact wherever the gap between the k-th and the
   (k+1)-th oracle score exceeds 10x the score tolerance; otherwise the
   selected sets may differ only inside the tied block.
@@ -38,11 +42,15 @@ def errors(theta_g, y_g, theta_o, y_o):
 
 def assert_scores(theta_g, y_g, theta_o, y_o, prec):
     e = errors(theta_g, y_g, theta_o, y_o)
-    if prec == "fp64":
-        assert e["max_rel"] <= TOL_FP64, e
-    else:
-        assert e["head_rel"] <= TOL_FP32, e
-        assert e["norm_rel"] <= TOL_FP32, e
+    tol = TOL_FP64 if prec == "fp64" else TOL_FP32
+    assert e["head_rel"] <= tol, e
+    assert e["norm_rel"] <= tol, e
+    return e
+
+
+def assert_scores_all(theta_g, y_g, theta_o, y_o, tol):
+    e = errors(theta_g, y_g, theta_o, y_o)
+    assert e["max_rel"] <= tol, e
     return e
 
 

@@ -143,6 +143,16 @@ def test_heavy_rows(B, prec):
     parity.assert_scores(theta, y, th_o, y_o, prec)
 
 
+@pytest.mark.parametrize("kind", ["er", "ws"])
+def test_converged_every_score_fp64(B, kind):
+    """Once m is large enough for the spectral width, the m-step result is
+    e^A 1 itself, and every score (not only the head) is within 1e-10."""
+    g = synth.er(20_000, 8.0 / 20_000, 3) if kind == "er" else synth.ws(20_000, 10, 0.1, 3)
+    th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 70)
+    theta, y, _ = _single(B, g, 70, "fp64")
+    parity.assert_scores_all(theta, y, th_o, y_o, parity.TOL_FP64)
+
+
 def test_empty_and_complete_breakdown(B):
     g = synth.from_edges(5000, np.zeros((0, 2), np.uint32))
     theta, y, rep = _single(B, g, 30, "fp32")
@@ -195,8 +205,10 @@ def test_max_depth(B):
 def test_argument_errors(B):
     g = synth.er(100, 0.05, 1)
     with B.GraphSet([g]) as gs:
-        with pytest.raises(B.CBError):
-            B.communicability(gs, 1, 10)  # realisation out of range
+        y = torch.empty(100, dtype=torch.float64, device="cuda")
+        ls = torch.empty(1, dtype=torch.float64, device="cuda")
+        with pytest.raises(B.CBError):  # realisation out of range
+            B.cb_communicability(gs.h, 1, 10, 0, y.data_ptr(), ls.data_ptr(), None, 0)
         with pytest.raises(B.CBError):
             B.communicability(gs, 0, 0)
         with pytest.raises(B.CBError):
