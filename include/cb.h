@@ -157,6 +157,28 @@ int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out, double
 int cb_topk(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val, void *stream);
 
 /*
+ * cb_topk_noalloc -- the same selection as cb_topk, without any device
+ * allocation.  (The paper has no counterpart: this is a library service.)
+ * For callers that cannot allocate device memory: an application that has
+ * reserved the whole GPU for its own memory pool and rejects further
+ * cudaMalloc / cudaMallocAsync calls, a plug-in whose host forbids CUDA
+ * allocation, or a latency-critical loop where an allocation might stall.
+ *   Arguments, order and tie rule as cb_topk.  k <= CB_MAX_TOPK (4096);
+ *   a larger k is rejected with CB_ERR_ARG and a message naming the limit.
+ *   Scratch: one fixed array of about 65 KB in device memory per GPU that
+ *   loads the library, held until the process exits.  The first call on a
+ *   device looks up that array's device address (cudaGetSymbolAddress), so
+ *   make the first call on each device before any stream capture.
+ *   Every call on a device shares the one array: calls whose work overlaps
+ *   on the GPU (different streams, no ordering between them) race and may
+ *   return wrong results.  Calls ordered on one stream are safe; each call
+ *   resets the scratch state it needs before using it.
+ *   Asynchronous; calls no allocating routine.
+ */
+int cb_topk_noalloc(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
+                    void *stream);
+
+/*
  * Kernel timing for measurement tools.  While enabled, every launch of the
  * kernel families below is bracketed by a CUDA event pair recorded on the
  * stream it is launched on; cb_profile_read() synchronises those events and

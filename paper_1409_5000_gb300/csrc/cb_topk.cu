@@ -216,3 +216,70 @@ CB_API int cb_topk(const double *S, uint32_t n, uint32_t k, uint32_t *idx, doubl
   if (rc != CB_OK) return rc;
   return cuda_error(e, "cb_topk: cudaFreeAsync");
 }
+
+// ---------------------------------------------------------------------------
+// Top-k without allocation.
+//
+// cb_topk takes its scratch from the stream-ordered allocator.  Some callers
+// cannot allocate device memory at all: a host application that has
+// reserved the whole GPU for its own pool and rejects any further cudaMalloc
+// / cudaMallocAsync, a plug-in whose host forbids CUDA allocation calls, or a
+// latency-critical loop where an allocation could stall on the device.  This
+// variant uses a fixed file-scope device array instead, sized for the
+// largest k the library accepts (CB_MAX_TOPK), about 65 KB per device.  It
+// runs the same kernels as cb_topk.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace cb {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes =
+    ((sizeof(TopkState) + 255) / 256) * 256 + (size_t)CB_MAX_TOPK * sizeof(Cand);
+
+// Shared by every cb_topk_noalloc call on a device; resident until exit.
+__device__ __align__(256) unsigned char g_topk_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in, so the address is looked up once per device
+// (with that device current) and cached.
+int noalloc_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cb_topk_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(CB_ERR_ARG, "cb_topk_noalloc: device index beyond the supported range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_topk_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cb_topk_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CB_OK;
+}
+
+}  // namespace
+}  // namespace cb
+
+CB_API int cb_topk_noalloc(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
+                           void *stream) {
+  using namespace cb;
+  if (!S || !idx || !val) return set_error(CB_ERR_ARG, "cb_topk_noalloc: null pointer");
+  if (n == 0 || k == 0 || k > n)
+    return set_error(CB_ERR_ARG, "cb_topk_noalloc: need 1 <= k <= n");
+  if (k > CB_MAX_TOPK || topk_scratch_bytes(k) > kNoAllocScratchBytes)
+    return set_error(CB_ERR_ARG,
+                     "cb_topk_noalloc: k exceeds the fixed scratch capacity (CB_MAX_TOPK = 4096)");
+  void *scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != CB_OK) return rc;
+  // topk_launch's first kernel resets every counter and histogram in the
+  // scratch, so the previous call's contents need no clearing here.
+  return topk_launch(S, n, k, idx, val, scratch, reinterpret_cast<cudaStream_t>(stream));
+}
