@@ -51,6 +51,12 @@ def workload(name):
         ens = synth.er_ensemble_uneven()
         desc = dict(workload="er-ensemble-256-uneven-n20k-400k-d20-m25", n_inst=256,
                     n_range=[20_000, 400_000], dbar=20, target="tree30+15", m=25, k=30)
+    elif name == "ensemble40":
+        # the first 40 realisations' recipe of the default workload: the small
+        # case for ncu captures (cols ~0.6 GB, still larger than L2)
+        ens = synth.er_ensemble_uneven(n_inst=40)
+        desc = dict(workload="er-ensemble-40-uneven-n20k-400k-d20-m25", n_inst=40,
+                    n_range=[20_000, 400_000], dbar=20, target="tree30+15", m=25, k=30)
     elif name == "large":
         ens = synth.ba_clique_large()
         desc = dict(workload="ba-1e7-m8-clique20-m40", n_inst=1, n=10_000_000, ba_m=8,
@@ -187,7 +193,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "large", "small"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "small"])
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the e2e, plain-FP64 and CPU-baseline legs")
     args = ap.parse_args()
