@@ -192,9 +192,36 @@ int cb_topk_noalloc(const double *S, uint32_t n, uint32_t k, uint32_t *idx, doub
 #define CB_K_COMBINE 3  /* basis combine / ensemble sum */
 #define CB_K_TOPK 4     /* top-k selection (all its passes) */
 #define CB_K_INIT 5     /* basis / scalar initialisation */
-#define CB_K_COUNT 6
+#define CB_K_BACKWARD 6 /* adjoint kernels (tridiagonal, node, edge) */
+#define CB_K_COUNT 7
 int cb_profile_enable(int on);
 int cb_profile_read(int kernel, double *total_ms, uint64_t *launches);
+
+/*
+ * cb_scores_backward -- edge gradient of the summed top-k score.  This is an
+ * extension: the paper has no gradient.  It differentiates eq. 5 restricted
+ * to a fixed node set S (normally the recovered top-k):
+ *   L = sum_r sum_{i in S, i < n_r} EBTC_r(i) = sum_r w_r^T e^{A_r} 1,
+ *   dL/da_ij = G_ij + G_ji,  G = int_0^1 e^{sA} w 1^T e^{(1-s)A} ds,
+ * for the undirected weight a_ij = a_ji of every existing edge (the
+ * Frechet derivative of e^A, at unit weights).  It is evaluated in m-step
+ * Krylov form from two Lanczos bases (from w and from 1).
+ *   h, m, prec  handle, Krylov depth 1 <= m <= 64, CB_FP32 or CB_FP64.
+ *   topk_idx    device, uint32[k], DISTINCT node indices of S (1 <= k <=
+ *               CB_MAX_TOPK).  Realisation r uses those < n_r; a realisation
+ *               without any contributes 0.
+ *   grad        device, float[sum_r nnz_r], written in CSR entry order of the
+ *               realisations concatenated in handle order.  The entries
+ *               (i,j) and (j,i) of one edge get the same value.
+ *   log_scale   device, double[1], written:
+ *               dL/da_e = exp(*log_scale) * grad[e].
+ * Asynchronous.  It overwrites the handle's forward workspace, so it must
+ * not run concurrently with other calls on the same handle.  The device
+ * memory it uses grows by one more Krylov basis and two node-major
+ * n x m arrays.
+ */
+int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx, uint32_t k,
+                       float *grad, double *log_scale, void *stream);
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *cb_last_error(void);

@@ -69,6 +69,8 @@ def lib():
         L.cb_last_error.argtypes = []
         L.cb_version.restype = u32
         L.cb_version.argtypes = []
+        L.cb_scores_backward.restype = i32
+        L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
         L.cb_profile_enable.restype = i32
         L.cb_profile_enable.argtypes = [i32]
         L.cb_profile_read.restype = i32
@@ -143,7 +145,14 @@ def cb_topk(S_ptr, n, k, idx_ptr, val_ptr, stream):
                          ctypes.c_void_p(val_ptr), ctypes.c_void_p(stream)))
 
 
-CB_K_SPMV, CB_K_FINALIZE, CB_K_TRIDIAG, CB_K_COMBINE, CB_K_TOPK, CB_K_INIT = range(6)
+CB_K_SPMV, CB_K_FINALIZE, CB_K_TRIDIAG, CB_K_COMBINE, CB_K_TOPK, CB_K_INIT, CB_K_BACKWARD = range(7)
+CB_MAX_M_ADJOINT = 64
+
+
+def cb_scores_backward(h, m, prec, topk_idx_ptr, k, grad_ptr, log_scale_ptr, stream):
+    _check(lib().cb_scores_backward(ctypes.c_void_p(h), m, prec, ctypes.c_void_p(topk_idx_ptr), k,
+                                    ctypes.c_void_p(grad_ptr), ctypes.c_void_p(log_scale_ptr),
+                                    ctypes.c_void_p(stream)))
 
 
 def cb_profile_enable(on):
@@ -268,3 +277,61 @@ def topk(S, k: int, out=None, stream=None):
         idx, val = out
     cb_topk(S.data_ptr(), S.numel(), k, idx.data_ptr(), val.data_ptr(), _stream_handle(stream))
     return idx, val
+
+
+def scores_backward(gs: GraphSet, m: int, nodes, prec: int = CB_FP32, stream=None):
+    """(log_scale, grad) with d/da_e sum_r sum_{i in nodes} EBTC_r(i) =
+    exp(log_scale) * grad[e], grad float32 over all CSR entries of the
+    handle (realisations concatenated)."""
+    import torch
+
+    nodes = torch.as_tensor(nodes, dtype=torch.int32, device="cuda").contiguous()
+    grad = torch.empty(sum(gs.nnz), dtype=torch.float32, device="cuda")
+    ls = torch.empty(1, dtype=torch.float64, device="cuda")
+    cb_scores_backward(gs.h, m, prec, nodes.data_ptr(), nodes.numel(), grad.data_ptr(),
+                       ls.data_ptr(), _stream_handle(stream))
+    return ls, grad
+
+
+def _summed_topk_function():
+    import torch
+
+    class SummedTopkScore(torch.autograd.Function):
+        """Loss = sum_r sum_{i in nodes} EBTC_r(i), scaled by exp(-log_scale),
+        as a function of the (unit) edge weights of the handle's pattern.
+
+        forward(edge_weight, gs, m, nodes, prec) -> scaled loss (float64 0-dim)
+        backward gives d loss / d edge_weight from cb_scores_backward (the
+        edge-sensitivity map of the recovered sub-graph).  The store is
+        pattern-only, so edge_weight must be all ones.
+        """
+
+        @staticmethod
+        def forward(ctx, edge_weight, gs, m, nodes, prec=CB_FP32):
+            if edge_weight.numel() != sum(gs.nnz):
+                raise ValueError("edge_weight must have one entry per CSR entry of the handle")
+            ls, S = ensemble_scores(gs, m, prec)
+            nodes_t = torch.as_tensor(nodes, dtype=torch.int64, device=S.device)
+            ctx.gs, ctx.m, ctx.nodes, ctx.prec = gs, m, nodes, prec
+            ctx.save_for_backward(ls)
+            return S[nodes_t].sum()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (ls_fwd,) = ctx.saved_tensors
+            ls_bw, grad = scores_backward(ctx.gs, ctx.m, ctx.nodes, ctx.prec)
+            scale = torch.exp(ls_bw - ls_fwd).to(torch.float32)
+            return grad * scale * grad_out.to(torch.float32), None, None, None, None
+
+    return SummedTopkScore
+
+
+_FN = None
+
+
+def summed_topk_score(edge_weight, gs: GraphSet, m: int, nodes, prec: int = CB_FP32):
+    """Autograd entry: scaled sum of the summed scores of `nodes` (see above)."""
+    global _FN
+    if _FN is None:
+        _FN = _summed_topk_function()
+    return _FN.apply(edge_weight, gs, m, nodes, prec)

@@ -1,0 +1,286 @@
+// Adjoint: edge gradient of the summed top-k total communicability.
+//
+// The paper has no gradient; this differentiates its score.  With w the
+// indicator of a fixed node set S (the recovered top-k of eq. 5), the loss is
+//     L = sum_r sum_{i in S, i < n_r} (e^{A_r} 1)_i = sum_r w_r^T e^{A_r} 1,
+// and for the undirected weight a_ij = a_ji of an existing edge of A_r
+//     dL/da_ij = G_ij + G_ji,   G = int_0^1 e^{sA} w 1^T e^{(1-s)A} ds
+// (the Frechet derivative of e^A, contracted with w and 1).
+//
+// Krylov form.  With Lanczos bases V_w (from w) and V_1 (from 1) and their
+// tridiagonals T_w, T_1, e^{sA} w ~ ||w|| V_w e^{s T_w} e1 and
+// e^{(1-s)A} 1 ~ sqrt(n) V_1 e^{(1-s) T_1} e1, so G ~ V_w M V_1^T with
+//     M = ||w|| sqrt(n) int_0^1 (e^{s T_w} e1)(e^{(1-s) T_1} e1)^T ds.
+// M is the upper-right block of exp([[T_w, e1 e1^T], [0, T_1]]) (Van Loan's
+// block formula).  The resolvent of that block-triangular matrix has
+// upper-right block R_w(z) e1 e1^T R_1(z), so the contour rule of the
+// forward step (cb_contour.cuh) gives, with the shift theta,
+//     M = ||w|| sqrt(n) 2 Re sum_k w_k x_k y_k^T,
+//     x_k = (z_k I - (T_w - theta))^{-1} e1,  y_k = (z_k I - (T_1 - theta))^{-1} e1:
+// 24 complex tridiagonal solves and 12 rank-1 terms, no eigendecomposition.
+//
+// Then P = V_w M and U = V_1 are written node-major (m contiguous values per
+// node) and every CSR entry (i, j) gets g = P_i . U_j + P_j . U_i: FP32 (or
+// FP64) values, FP64 accumulation.  Realisations share one shift theta* =
+// max_r theta_r; dL/da_e = exp(theta*) * grad[e].
+#include "cb_contour.cuh"
+
+namespace cb {
+
+constexpr uint32_t kMaxAdjM = 64;  // adjoint depth limit (shared-memory staging)
+
+void free_backwork(BackWork &B) {
+  cudaFree(B.P);
+  cudaFree(B.U);
+  cudaFree(B.blob);
+  B = BackWork{};
+}
+
+static int ensure_backwork(cb_graph *h, uint32_t m, int prec, cudaStream_t s) {
+  BackWork &B = h->bw;
+  if (B.P && B.prec == prec && B.m == m) return CB_OK;
+  free_backwork(B);
+  const uint32_t mpad = (m + 3) / 4 * 4;
+  const size_t esz = prec == CB_FP64 ? sizeof(double) : sizeof(float);
+  const size_t vb = h->total_nodes_padded * mpad * esz + 16;
+  cudaError_t e = cudaMalloc(&B.P, vb);
+  if (e == cudaSuccess) e = cudaMalloc(&B.U, vb);
+  const uint32_t N = h->n_inst;
+  const size_t bytes = ((size_t)N * m * m + N) * sizeof(double) + (size_t)N * sizeof(uint32_t) + 64;
+  if (e == cudaSuccess) e = cudaMalloc(&B.blob, bytes);
+  if (e != cudaSuccess) {
+    free_backwork(B);
+    return cuda_error(e, "adjoint workspace");
+  }
+  B.K = reinterpret_cast<double *>(B.blob);
+  B.theta = B.K + (size_t)N * m * m;
+  B.cnt = reinterpret_cast<uint32_t *>(B.theta + N);
+  B.prec = prec;
+  B.m = m;
+  B.mpad = mpad;
+  return cuda_error(cudaMemsetAsync(B.blob, 0, bytes, s), "adjoint workspace clear");
+}
+
+// One warp per realisation: theta_r and the coefficient matrix K_r = M_r.
+__global__ void __launch_bounds__(32) bw_tridiag_kernel(Scalars s1, Scalars sw,
+                                                        const InstDesc *inst, double *K,
+                                                        uint32_t kdim, double *theta_out,
+                                                        uint32_t *cnt_out) {
+  using namespace contour;
+  __shared__ double s_a1[kMaxAdjM], s_b1[kMaxAdjM], s_aw[kMaxAdjM], s_bw[kMaxAdjM];
+  __shared__ cplx s_x[kHalf][kMaxAdjM], s_y[kHalf][kMaxAdjM];
+  __shared__ double s_th[2];
+  const uint32_t r = blockIdx.x, lane = threadIdx.x;
+  const int M1 = (int)s1.meff[r], Mw = (int)sw.meff[r];
+  const bool ok = M1 > 0 && Mw > 0 && s1.status[r] == CB_OK && sw.status[r] == CB_OK;
+  if (!ok) {
+    if (lane == 0) {
+      theta_out[r] = -1e308;
+      cnt_out[r] = 0;
+    }
+    return;
+  }
+  for (int i = lane; i < M1; i += 32) {
+    s_a1[i] = s1.alpha[r * s1.ms + i];
+    s_b1[i] = s1.beta[r * s1.ms + i];
+  }
+  for (int i = lane; i < Mw; i += 32) {
+    s_aw[i] = sw.alpha[r * sw.ms + i];
+    s_bw[i] = sw.beta[r * sw.ms + i];
+  }
+  __syncwarp();
+  if (lane == 0) s_th[0] = lambda_max(s_a1, s_b1, M1);
+  if (lane == 1) s_th[1] = lambda_max(s_aw, s_bw, Mw);
+  __syncwarp();
+  const double theta = fmax(s_th[0], s_th[1]);
+  if (lane < kHalf) {
+    cplx z, w;
+    node((int)lane, &z, &w);
+    cplx cp[kMaxAdjM], x[kMaxAdjM];
+    thomas_e1(s_aw, s_bw, Mw, theta, z, cp, x);
+    for (int i = 0; i < Mw; ++i) s_x[lane][i] = cmul(w, x[i]);
+    thomas_e1(s_a1, s_b1, M1, theta, z, cp, x);
+    for (int i = 0; i < M1; ++i) s_y[lane][i] = x[i];
+  }
+  __syncwarp();
+  // ||w|| = 1 / scale_w[0], sqrt(n) = 1 / scale_1[0]
+  const double c = 1.0 / (sw.scale[r * sw.ms] * s1.scale[r * s1.ms]);
+  double *Kr = K + (size_t)r * kdim * kdim;
+  for (int q = lane; q < Mw * M1; q += 32) {
+    const int a = q / M1, b = q % M1;
+    double acc = 0.0;
+    for (int k = 0; k < kHalf; ++k) {
+      const cplx xa = s_x[k][a], yb = s_y[k][b];
+      acc += xa.re * yb.re - xa.im * yb.im;
+    }
+    Kr[a * kdim + b] = 2.0 * c * acc;
+  }
+  if (lane == 0) {
+    theta_out[r] = theta;
+    const double sw0 = sw.scale[r * sw.ms];
+    cnt_out[r] = (uint32_t)llrint(1.0 / (sw0 * sw0));
+  }
+}
+
+// Node-major P = exp(theta_r - theta*) V_w K_r and U = V_1 (scales applied).
+// One CTA per finalize tile (kFinRows nodes of one realisation), 4 warps;
+// each warp stages 32 nodes' basis values in shared memory and writes the
+// node-major rows with lanes over the row index (coalesced).
+template <typename T>
+__global__ void __launch_bounds__(128) bw_node_kernel(const T *V1, const T *Vw, uint64_t vs,
+                                                      Scalars s1, Scalars sw,
+                                                      const InstDesc *inst, const uint32_t *fin_inst,
+                                                      uint32_t n_inst, const double *K,
+                                                      uint32_t kdim, const double *theta_in,
+                                                      uint32_t mpad, T *P, T *U,
+                                                      double *log_scale) {
+  extern __shared__ unsigned char s_raw[];
+  T *sK = reinterpret_cast<T *>(s_raw);              // kdim * kdim
+  T *sV = sK + kdim * kdim;                          // 4 warps x kdim x 32 (V_w values)
+  T *sW = sV + 4 * kdim * 32;                        // 4 warps x kdim x 32 (V_1 values)
+  __shared__ double s_tmax;
+  const uint32_t t = blockIdx.x;
+  const uint32_t r = fin_inst[t];
+  const InstDesc I = inst[r];
+  if (threadIdx.x == 0) {
+    double tm = -1e308;
+    for (uint32_t q = 0; q < n_inst; ++q) tm = fmax(tm, theta_in[q]);
+    s_tmax = tm;
+    if (t == 0) *log_scale = tm > -1e307 ? tm : 0.0;
+  }
+  __syncthreads();
+  const double th = theta_in[r];
+  const bool active = th > -1e307;
+  const int M1 = active ? (int)s1.meff[r] : 0, Mw = active ? (int)sw.meff[r] : 0;
+  const double f = active ? exp(th - s_tmax) : 0.0;
+  for (uint32_t q = threadIdx.x; q < (uint32_t)(Mw * M1); q += blockDim.x) {
+    const uint32_t a = q / M1, b = q % M1;
+    sK[a * kdim + b] = (T)(f * K[(size_t)r * kdim * kdim + a * kdim + b]);
+  }
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T *myV = sV + warp * kdim * 32, *myW = sW + warp * kdim * 32;
+  const uint32_t i0 = (t - I.fin_base) * kFinRows, i1 = min(i0 + kFinRows, I.n);
+  for (uint32_t base = i0 + warp * 32; base < i1; base += 4 * 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < i1;
+    for (int a = 0; a < Mw; ++a)
+      myV[a * 32 + lane] = valid ? (T)(sw.scale[r * sw.ms + a]) * Vw[(uint64_t)a * vs + I.node_base + i] : T(0);
+    for (int b = 0; b < M1; ++b)
+      myW[b * 32 + lane] = valid ? (T)(s1.scale[r * s1.ms + b]) * V1[(uint64_t)b * vs + I.node_base + i] : T(0);
+    __syncwarp();
+    const uint32_t nn = min(32u, i1 - base);
+    for (uint32_t q = 0; q < nn; ++q) {
+      const uint64_t row = (I.node_base + base + q) * (uint64_t)mpad;
+      for (uint32_t b = lane; b < mpad; b += 32) {
+        T p = T(0), u = T(0);
+        if ((int)b < M1) {
+          for (int a = 0; a < Mw; ++a) p += myV[a * 32 + q] * sK[a * kdim + b];
+          u = myW[b * 32 + q];
+        }
+        P[row + b] = p;
+        U[row + b] = u;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// dot of 4 consecutive values of a with 4 of b (16- or 32-byte aligned)
+__device__ __forceinline__ float dot4(const float *a, const float *b) {
+  const float4 x = *reinterpret_cast<const float4 *>(a), y = *reinterpret_cast<const float4 *>(b);
+  return x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+}
+__device__ __forceinline__ double dot4(const double *a, const double *b) {
+  const double2 x0 = *reinterpret_cast<const double2 *>(a);
+  const double2 x1 = *reinterpret_cast<const double2 *>(a + 2);
+  const double2 y0 = *reinterpret_cast<const double2 *>(b);
+  const double2 y1 = *reinterpret_cast<const double2 *>(b + 2);
+  return x0.x * y0.x + x0.y * y0.y + x1.x * y1.x + x1.y * y1.y;
+}
+
+// g_e = P_i . U_j + P_j . U_i for every CSR entry e = (i, j) of one SpMV tile.
+template <typename T>
+__global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, uint32_t mpad,
+                                                      const InstDesc *inst,
+                                                      const uint32_t *tile_inst,
+                                                      const uint32_t *row_ptr, const uint32_t *col,
+                                                      const double *theta_in, float *grad) {
+  __shared__ uint32_t s_rp[kTileRows + 1];
+  const uint32_t t = blockIdx.x;
+  const uint32_t r = tile_inst[t];
+  const InstDesc I = inst[r];
+  const uint32_t *rp = row_ptr + I.rp_base;
+  const uint32_t *cl = col + I.edge_base;
+  const uint32_t row0 = (t - I.tile_base) * kTileRows;
+  const uint32_t nrows = min((uint32_t)kTileRows, I.n - row0);
+  for (uint32_t q = threadIdx.x; q <= nrows; q += blockDim.x) s_rp[q] = rp[row0 + q];
+  __syncthreads();
+  const uint32_t e0 = s_rp[0], e1 = s_rp[nrows];
+  const bool active = theta_in[r] > -1e307;
+  const uint32_t nv = mpad / 4;
+  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    double g = 0.0;
+    if (active) {
+      uint32_t lo = 0, hi = nrows;  // last lr with s_rp[lr] <= e
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_rp[mid] <= e) lo = mid; else hi = mid;
+      }
+      const uint64_t i = I.node_base + row0 + lo;
+      const uint64_t j = I.node_base + __ldg(cl + e);
+      const T *Pi = P + i * mpad, *Ui = U + i * mpad, *Pj = P + j * mpad, *Uj = U + j * mpad;
+      for (uint32_t c = 0; c < nv; ++c)  // FP64 accumulation of 8-term partial dots
+        g += (double)(dot4(Pi + 4 * c, Uj + 4 * c) + dot4(Pj + 4 * c, Ui + 4 * c));
+    }
+    grad[I.edge_base + e] = (float)g;
+  }
+}
+
+template <typename T>
+static int backward_t(cb_graph *h, uint32_t m, const uint32_t *idx, uint32_t k, float *grad,
+                      double *log_scale, cudaStream_t s) {
+  BackWork &B = h->bw;
+  const uint32_t N = h->n_inst;
+  const int tok = prof_begin(CB_K_BACKWARD, s);
+  bw_tridiag_kernel<<<N, 32, 0, s>>>(h->ws.sc, h->ws2.sc, h->d_inst, B.K, m, B.theta, B.cnt);
+  const size_t shm = (size_t)(m * m + 8 * m * 32) * sizeof(T);
+  auto nk = bw_node_kernel<T>;
+  if (shm > 48 * 1024) cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  nk<<<h->total_fin, 128, shm, s>>>((const T *)h->ws.V, (const T *)h->ws2.V, h->ws.vec_stride,
+                                    h->ws.sc, h->ws2.sc, h->d_inst, h->d_fin_inst, N, B.K, m,
+                                    B.theta, B.mpad, (T *)B.P, (T *)B.U, log_scale);
+  bw_edge_kernel<T><<<h->total_tiles, 256, 0, s>>>((const T *)B.P, (const T *)B.U, B.mpad,
+                                                   h->d_inst, h->d_tile_inst, h->row_ptr, h->col,
+                                                   B.theta, grad);
+  prof_end(tok, s);
+  (void)idx;
+  (void)k;
+  return cuda_error(cudaGetLastError(), "adjoint launch");
+}
+
+}  // namespace cb
+
+using namespace cb;
+
+CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx,
+                              uint32_t k, float *grad, double *log_scale, void *stream) {
+  if (!h || !topk_idx || !grad || !log_scale)
+    return set_error(CB_ERR_ARG, "cb_scores_backward: null argument");
+  if (m < 1 || m > kMaxAdjM)
+    return set_error(CB_ERR_ARG, "cb_scores_backward: need 1 <= m <= 64");
+  if (k < 1 || k > CB_MAX_TOPK)
+    return set_error(CB_ERR_ARG, "cb_scores_backward: need 1 <= k <= CB_MAX_TOPK");
+  if (prec != CB_FP32 && prec != CB_FP64)
+    return set_error(CB_ERR_ARG, "cb_scores_backward: bad precision");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = ensure_workspace(h, h->ws, m, prec, s);
+  if (rc == CB_OK) rc = ensure_workspace(h, h->ws2, m, prec, s);
+  if (rc == CB_OK) rc = ensure_backwork(h, m, prec, s);
+  if (rc == CB_OK) rc = lanczos_run(h, h->ws, 0, h->n_inst, m, prec, s);
+  if (rc == CB_OK) rc = lanczos_run(h, h->ws2, 0, h->n_inst, m, prec, s, topk_idx, k);
+  if (rc == CB_OK)
+    rc = prec == CB_FP64 ? backward_t<double>(h, m, topk_idx, k, grad, log_scale, s)
+                         : backward_t<float>(h, m, topk_idx, k, grad, log_scale, s);
+  return rc;
+}

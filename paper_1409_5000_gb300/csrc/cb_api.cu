@@ -94,8 +94,7 @@ static cudaError_t dalloc(P **p, size_t count) {
   return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P) + 16);
 }
 
-static void free_workspace(cb_graph *h) {
-  Workspace &W = h->ws;
+void free_workspace(Workspace &W) {
   if (W.V) cudaFree(W.V);
   if (W.blob) cudaFree(W.blob);
   W = Workspace{};
@@ -119,10 +118,9 @@ static void free_graph_arrays(cb_graph *h) {
 }
 
 // Workspace for depth m in precision prec; reused when large enough.
-static int ensure_workspace(cb_graph *h, uint32_t m, int prec, cudaStream_t s) {
-  Workspace &W = h->ws;
+int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream_t s) {
   if (W.V && W.prec == prec && W.m >= m) return CB_OK;
-  free_workspace(h);
+  free_workspace(W);
   const size_t esz = prec == CB_FP64 ? sizeof(double) : sizeof(float);
   W.vec_stride = h->total_nodes_padded;
   const size_t vbytes = (size_t)(m + 1) * W.vec_stride * esz;
@@ -143,7 +141,7 @@ static int ensure_workspace(cb_graph *h, uint32_t m, int prec, cudaStream_t s) {
   e = cudaMalloc(&W.blob, bytes);
   if (e != cudaSuccess) {
     W.blob = nullptr;
-    free_workspace(h);
+    free_workspace(W);
     return cuda_error(e, "workspace: scalars");
   }
   double *d = reinterpret_cast<double *>(W.blob);
@@ -168,7 +166,7 @@ static int ensure_workspace(cb_graph *h, uint32_t m, int prec, cudaStream_t s) {
   e = cudaMemsetAsync(W.blob, 0, bytes, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    free_workspace(h);
+    free_workspace(W);
     return cuda_error(e, "workspace: clear");
   }
   return CB_OK;
@@ -418,7 +416,9 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
 CB_API int cb_graph_free(cb_graph *h) {
   if (!h) return set_error(CB_ERR_ARG, "cb_graph_free: null handle");
   cudaError_t e = cudaDeviceSynchronize();
-  free_workspace(h);
+  free_workspace(h->ws);
+  free_workspace(h->ws2);
+  free_backwork(h->bw);
   free_graph_arrays(h);
   delete h;
   return cuda_error(e, "cb_graph_free");
@@ -455,8 +455,8 @@ CB_API int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, 
   if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_communicability: need 1 <= m <= CB_MAX_M");
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_communicability: bad precision");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int rc = ensure_workspace(h, m, prec, s);
-  if (rc == CB_OK) rc = lanczos_run(h, inst, inst + 1, m, prec, s);
+  int rc = ensure_workspace(h, h->ws, m, prec, s);
+  if (rc == CB_OK) rc = lanczos_run(h, h->ws, inst, inst + 1, m, prec, s);
   if (rc == CB_OK) rc = tridiag_run(h, inst, inst + 1, prec, s);
   if (rc == CB_OK) rc = combine_single(h, inst, prec, y_scaled, log_scale, s);
   if (rc == CB_OK && rep) rc = fill_report(h, inst, inst + 1, rep, s);
@@ -470,8 +470,8 @@ CB_API int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out,
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_ensemble_scores: bad precision");
   if (n_out < h->n_max) return set_error(CB_ERR_ARG, "cb_ensemble_scores: n_out < largest n");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int rc = ensure_workspace(h, m, prec, s);
-  if (rc == CB_OK) rc = lanczos_run(h, 0, h->n_inst, m, prec, s);
+  int rc = ensure_workspace(h, h->ws, m, prec, s);
+  if (rc == CB_OK) rc = lanczos_run(h, h->ws, 0, h->n_inst, m, prec, s);
   if (rc == CB_OK) rc = tridiag_run(h, 0, h->n_inst, prec, s);
   if (rc == CB_OK) rc = combine_ensemble(h, prec, n_out, S, log_scale, s);
   if (rc == CB_OK && rep) rc = fill_report(h, 0, h->n_inst, rep, s);

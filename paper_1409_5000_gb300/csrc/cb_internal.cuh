@@ -80,6 +80,18 @@ struct Workspace {
   void *blob = nullptr;    // single allocation backing sc/part/gpart/cnt
 };
 
+// Buffers of the adjoint (cb_scores_backward).
+struct BackWork {
+  int prec = -1;
+  uint32_t m = 0, mpad = 0;  // node-major row length (m rounded up to 4)
+  void *P = nullptr;         // node-major P = V_w K   [total_nodes_padded x mpad]
+  void *U = nullptr;         // node-major U = V_1     [total_nodes_padded x mpad]
+  double *K = nullptr;       // per realisation coefficient matrix [n_inst x ms x ms]
+  double *theta = nullptr;   // per realisation shift
+  uint32_t *cnt = nullptr;   // per realisation |top-k within [0, n_r)|
+  void *blob = nullptr;
+};
+
 }  // namespace cb
 
 struct cb_graph {
@@ -101,7 +113,9 @@ struct cb_graph {
   cb::HeavyRow *d_heavy = nullptr;
   uint32_t *d_chunk_heavy = nullptr;     // heavy-row index of each chunk
   uint32_t *d_fin_inst = nullptr;        // instance of each finalize tile
-  cb::Workspace ws;
+  cb::Workspace ws;   // Krylov basis from 1 (forward)
+  cb::Workspace ws2;  // Krylov basis from the top-k indicator (adjoint)
+  cb::BackWork bw;    // adjoint buffers
 };
 
 namespace cb {
@@ -113,8 +127,16 @@ int cuda_error(cudaError_t e, const char *what);
 int prof_begin(int kernel, cudaStream_t s);
 void prof_end(int token, cudaStream_t s);
 
-// kernel launchers (cb_lanczos.cu).  Range of realisations [r0, r1).
-int lanczos_run(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, int prec, cudaStream_t s);
+// workspace for depth m in precision prec (cb_api.cu)
+int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream_t s);
+void free_workspace(Workspace &W);
+void free_backwork(BackWork &B);  // cb_adjoint.cu
+
+// kernel launchers (cb_lanczos.cu).  Range of realisations [r0, r1).  The
+// start vector is 1, or, with start_idx, the indicator of the k distinct
+// node indices start_idx[0..k) (device array) restricted to [0, n_r).
+int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
+                cudaStream_t s, const uint32_t *start_idx = nullptr, uint32_t k = 0);
 // tridiagonal exp (cb_tridiag.cu)
 int tridiag_run(cb_graph *h, uint32_t r0, uint32_t r1, int prec, cudaStream_t s);
 // combine (cb_combine.cu)

@@ -72,19 +72,34 @@ __device__ __forceinline__ T row_epilogue(T sum, uint32_t row, const T *x, const
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) init_vec_kernel(LArgs a, uint32_t r0, uint32_t r1) {
-  // W_0 = 1 on every realisation's node range.
+__global__ void __launch_bounds__(kThreads) init_vec_kernel(LArgs a, uint32_t r0, uint32_t r1,
+                                                            T fill) {
+  // W_0 = fill (1 for the start vector 1, 0 before an indicator is set).
   for (uint32_t r = r0; r < r1; ++r) {
     const InstDesc I = a.inst[r];
     T *w0 = reinterpret_cast<T *>(a.V) + I.node_base;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I.n;
          i += (uint64_t)gridDim.x * blockDim.x)
-      w0[i] = T(1);
+      w0[i] = fill;
+  }
+}
+
+// W_0[idx[q]] = 1 for the start indices inside each realisation's range.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) init_indicator_kernel(LArgs a, uint32_t r0,
+                                                                  const uint32_t *idx, uint32_t k) {
+  const uint32_t r = r0 + blockIdx.x;
+  const InstDesc I = a.inst[r];
+  T *w0 = reinterpret_cast<T *>(a.V) + I.node_base;
+  for (uint32_t q = threadIdx.x; q < k; q += blockDim.x) {
+    const uint32_t i = idx[q];
+    if (i < I.n) w0[i] = T(1);
   }
 }
 
 __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_t r0, uint32_t r1,
-                                                                uint32_t m) {
+                                                                uint32_t m, const uint32_t *idx,
+                                                                uint32_t k) {
   const uint32_t ms = a.sc.ms;
   const uint64_t total = (uint64_t)(r1 - r0) * ms;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -94,9 +109,14 @@ __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_
     a.sc.alpha[o] = 0.0;
     a.sc.beta[o] = 0.0;
     a.sc.gamma[o] = 0.0;
-    a.sc.scale[o] = jj == 0 ? 1.0 / sqrt((double)a.inst[r].n) : 0.0;
+    uint32_t cnt = a.inst[r].n;  // ||start||^2
+    if (idx && jj == 0) {
+      cnt = 0;
+      for (uint32_t q = 0; q < k; ++q) cnt += (idx[q] < a.inst[r].n);
+    }
+    a.sc.scale[o] = (jj == 0 && cnt) ? 1.0 / sqrt((double)cnt) : 0.0;
     if (jj == 0) {
-      a.sc.meff[r] = m;
+      a.sc.meff[r] = cnt ? m : 0u;  // no start vector: nothing to do
       a.sc.status[r] = CB_OK;
       a.sc.theta[r] = 0.0;
     }
@@ -342,8 +362,8 @@ static void launch_spmv_lanes(int lanes, const LArgs &a, uint32_t j, uint32_t co
 }
 
 template <typename T>
-static int run_t(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t s) {
-  Workspace &W = h->ws;
+static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t s,
+                 const uint32_t *start_idx, uint32_t k) {
   LArgs a;
   a.inst = h->d_inst;
   a.tile_inst = h->d_tile_inst;
@@ -372,9 +392,12 @@ static int run_t(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t
   for (uint32_t r = r0; r < r1; ++r) nmax = h->inst[r].n > nmax ? h->inst[r].n : nmax;
   const uint32_t init_grid = (nmax + kThreads * 8 - 1) / (kThreads * 8);
   int tok = prof_begin(CB_K_INIT, s);
-  init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1);
+  init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1,
+                                                                    start_idx ? T(0) : T(1));
+  if (start_idx) init_indicator_kernel<T><<<r1 - r0, kThreads, 0, s>>>(a, r0, start_idx, k);
   const uint64_t nsc = (uint64_t)(r1 - r0) * W.sc.ms;
-  init_scalars_kernel<<<(uint32_t)((nsc + kThreads - 1) / kThreads), kThreads, 0, s>>>(a, r0, r1, m);
+  init_scalars_kernel<<<(uint32_t)((nsc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      a, r0, r1, m, start_idx, k);
   prof_end(tok, s);
   for (uint32_t j = 0; j < m; ++j) {
     tok = prof_begin(CB_K_SPMV, s);
@@ -387,8 +410,10 @@ static int run_t(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t
   return cuda_error(cudaGetLastError(), "lanczos launch");
 }
 
-int lanczos_run(cb_graph *h, uint32_t r0, uint32_t r1, uint32_t m, int prec, cudaStream_t s) {
-  return prec == CB_FP64 ? run_t<double>(h, r0, r1, m, s) : run_t<float>(h, r0, r1, m, s);
+int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
+                cudaStream_t s, const uint32_t *start_idx, uint32_t k) {
+  return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k)
+                         : run_t<float>(h, W, r0, r1, m, s, start_idx, k);
 }
 
 }  // namespace cb
