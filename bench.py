@@ -61,6 +61,11 @@ def workload(name):
         ens = synth.ba_clique_large()
         desc = dict(workload="ba-1e7-m8-clique20-m40", n_inst=1, n=10_000_000, ba_m=8,
                     target="clique20", m=40, k=20)
+    elif name == "grad":
+        ens = synth.er_ensemble_grad()
+        desc = dict(workload="er-ensemble-64x1e5-d16-m30-fwd+bwd", n_inst=64, n=100_000, dbar=16,
+                    target="tree25+10", m=30, k=25,
+                    step="ensemble scores + top-k + edge gradient of the top-k score")
     elif name == "small":
         ens = synth.er_ensemble_small()
         desc = dict(workload="er-ensemble-10x500-p0.016-m20", n_inst=10, n=500, p=0.016,
@@ -193,7 +198,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "small"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "small", "grad"])
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the e2e, plain-FP64 and CPU-baseline legs")
     args = ap.parse_args()
@@ -232,9 +237,17 @@ def main():
     idx = torch.empty(k, dtype=torch.int32, device=dev)
     val = torch.empty(k, dtype=torch.float64, device=dev)
 
+    with_grad = args.workload == "grad"
+    if with_grad:
+        grad = torch.empty(sum(gs.nnz), dtype=torch.float32, device=dev)
+        gls = torch.empty(1, dtype=torch.float64, device=dev)
+
     def step():
         B.ensemble_scores(gs, m, B.CB_FP32, out=(S, ls))
         B.topk(S, k, out=(idx, val))
+        if with_grad:  # the recovered top-k (still on the device) is the node set
+            B.cb_scores_backward(gs.h, m, B.CB_FP32, idx.data_ptr(), k, grad.data_ptr(),
+                                 gls.data_ptr(), stream.cuda_stream)
 
     for _ in range(args.warmup):
         step()
@@ -270,7 +283,8 @@ def main():
     torch.cuda.synchronize()
     fam = {}
     for name, kid in [("spmv", B.CB_K_SPMV), ("finalize", B.CB_K_FINALIZE), ("tridiag", B.CB_K_TRIDIAG),
-                      ("combine", B.CB_K_COMBINE), ("topk", B.CB_K_TOPK), ("init", B.CB_K_INIT)]:
+                      ("combine", B.CB_K_COMBINE), ("topk", B.CB_K_TOPK), ("init", B.CB_K_INIT),
+                      ("backward", B.CB_K_BACKWARD)]:
         t, c = B.cb_profile_read(kid)
         fam[name] = (t, c)
     B.cb_profile_enable(0)
@@ -285,8 +299,12 @@ def main():
                 "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
                 "kernel_shares": {kname: round(t / tot, 4) for kname, (t, _) in fam.items()}}
     launches_per_step = 2 + 2 * m + 1 + 1 + 15
+    if with_grad:  # two more Lanczos runs (one with the indicator kernel) + 3 adjoint kernels
+        launches_per_step += (2 + 2 * m) + (3 + 2 * m) + 3
 
     extra = {}
+    if with_grad:
+        extra["backward_share"] = round(fam["backward"][0] / tot, 4)
     ls1 = torch.empty(1, dtype=torch.float64, device=dev)
     if rank == 0 and not args.skip_extra:
         # plain per-graph FP64 path: one cb_communicability call per realisation

@@ -409,6 +409,14 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     delete h;
     return cuda_error(e, "cb_graph_upload: copy");
   }
+  std::vector<const uint32_t *> rpv(n_inst);
+  for (uint32_t r = 0; r < n_inst; ++r) rpv[r] = rp_of(r);
+  int rc = build_blocked(h, rpv, s);
+  if (rc != CB_OK) {
+    free_graph_arrays(h);
+    delete h;
+    return rc;
+  }
   *out = h;
   return CB_OK;
 }
@@ -419,6 +427,7 @@ CB_API int cb_graph_free(cb_graph *h) {
   free_workspace(h->ws);
   free_workspace(h->ws2);
   free_backwork(h->bw);
+  free_blocked(h);
   free_graph_arrays(h);
   delete h;
   return cuda_error(e, "cb_graph_free");

@@ -1,0 +1,250 @@
+// Builder of the column-blocked adjacency format used by the FP32 SpMV.
+//
+// On GB300 a random 4-byte gather from L2 costs one 32-byte sector request
+// (about one per clock per SM), while a shared-memory gather is ~6x cheaper.
+// The format lets the SpMV stage a block of kBCol entries of v_j in shared
+// memory and gather only from there:
+//   * rows are tiled by kBTileRows; thread i of a tile owns the
+//     kBRowsPerThread consecutive rows starting at kBRowsPerThread * i;
+//   * a tile's edges are grouped by column block b = col >> kBColBits into
+//     one segment per (tile, b); inside a segment, thread i's edges (its
+//     rows in order, each row's columns in order) form one contiguous
+//     stream, streams in thread order;
+//   * each stream element stores the local column (u16, col & (kBCol-1))
+//     and the row slot of the owning thread (u8, 0..kBRowsPerThread-1);
+//   * per segment: kBThreads + 1 stream offsets (u32) and a u64 start.
+// Rows with more than kBLongDeg entries stay out of the streams; the SpMV
+// sums them from the CSR with whole-CTA global gathers.  Built on the device
+// from the CSR (one count pass, a host prefix over segment lengths, one
+// fill pass), once per upload.
+#include <algorithm>
+#include <cstdlib>
+
+#include "cb_internal.cuh"
+
+namespace cb {
+
+namespace {
+
+// Exclusive prefix sum over the kBThreads threads of the CTA; returns the
+// thread's offset and writes the CTA total to *total (all threads).
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sh /*[32]*/, uint32_t *total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    sh[lane] = w;  // inclusive prefix of warp totals
+  }
+  __syncthreads();
+  const uint32_t before = (warp ? sh[warp - 1] : 0u) + x - v;
+  *total = sh[31];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
+                                                           const uint32_t *btile_inst,
+                                                           const uint64_t *bseg_base,
+                                                           const uint32_t *row_ptr,
+                                                           const uint32_t *col, uint32_t *boff,
+                                                           uint32_t *seglen) {
+  __shared__ uint32_t sh[32];
+  const uint32_t t = blockIdx.x;
+  const InstDesc I = inst[btile_inst[t]];
+  const uint32_t *rp = row_ptr + I.rp_base;
+  const uint32_t *cl = col + I.edge_base;
+  const uint32_t row0 = (t - I.btile_base) * kBTileRows;
+  uint32_t len[kBMaxBlocks];
+  for (uint32_t b = 0; b < kBMaxBlocks; ++b) len[b] = 0;
+  for (int k = 0; k < kBRowsPerThread; ++k) {
+    const uint32_t row = row0 + kBRowsPerThread * threadIdx.x + k;
+    if (row >= I.n) break;
+    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    if (e1 - e0 > kBLongDeg) continue;
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t b = cl[e] >> kBColBits;
+      if (b < I.nb) len[b]++;  // columns >= n are invalid input: skipped
+    }
+  }
+  for (uint32_t b = 0; b < I.nb; ++b) {
+    uint32_t total;
+    const uint32_t off = block_exclusive_scan(len[b], sh, &total);
+    const uint64_t seg = bseg_base[t] + b;
+    boff[seg * (kBThreads + 1) + threadIdx.x] = off;
+    if (threadIdx.x == 0) {
+      boff[seg * (kBThreads + 1) + kBThreads] = total;
+      seglen[seg] = total;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
+                                                          const uint32_t *btile_inst,
+                                                          const uint64_t *bseg_base,
+                                                          const uint64_t *bseg_start,
+                                                          const uint32_t *boff,
+                                                          const uint32_t *row_ptr,
+                                                          const uint32_t *col, uint16_t *bcol,
+                                                          uint8_t *bslot) {
+  const uint32_t t = blockIdx.x;
+  const InstDesc I = inst[btile_inst[t]];
+  const uint32_t *rp = row_ptr + I.rp_base;
+  const uint32_t *cl = col + I.edge_base;
+  const uint32_t row0 = (t - I.btile_base) * kBTileRows;
+  uint64_t cur[kBMaxBlocks];
+  for (uint32_t b = 0; b < I.nb; ++b) {
+    const uint64_t seg = bseg_base[t] + b;
+    cur[b] = bseg_start[seg] + boff[seg * (kBThreads + 1) + threadIdx.x];
+  }
+  for (int k = 0; k < kBRowsPerThread; ++k) {
+    const uint32_t row = row0 + kBRowsPerThread * threadIdx.x + k;
+    if (row >= I.n) break;
+    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    if (e1 - e0 > kBLongDeg) continue;
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t c = cl[e];
+      const uint32_t b = c >> kBColBits;
+      if (b >= I.nb) continue;
+      bcol[cur[b]] = (uint16_t)(c & (kBCol - 1));
+      bslot[cur[b]] = (uint8_t)k;
+      cur[b]++;
+    }
+  }
+}
+
+template <typename P>
+cudaError_t dalloc(P **p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P) + 64);
+}
+
+}  // namespace
+
+void free_blocked(cb_graph *h) {
+  cudaFree(h->d_btile_inst);
+  cudaFree(h->d_bseg_base);
+  cudaFree(h->d_bseg_start);
+  cudaFree(h->d_boff);
+  cudaFree(h->d_bcol);
+  cudaFree(h->d_bslot);
+  cudaFree(h->d_blong_ptr);
+  cudaFree(h->d_blong_rows);
+  h->d_btile_inst = nullptr;
+  h->d_bseg_base = h->d_bseg_start = nullptr;
+  h->d_boff = nullptr;
+  h->d_bcol = nullptr;
+  h->d_bslot = nullptr;
+  h->d_blong_ptr = h->d_blong_rows = nullptr;
+  h->total_btiles = 0;
+  h->total_bseg = 0;
+}
+
+int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s) {
+  if (std::getenv("CB_NO_BLOCKED")) return CB_OK;
+  // which realisations, their tiles, segments and reduction plans
+  uint32_t nbt = 0, slot = 0, group = 0;
+  uint64_t nseg = 0;
+  std::vector<uint32_t> btile_inst;
+  std::vector<uint64_t> bseg_base;
+  std::vector<uint32_t> long_ptr(1, 0), long_rows;
+  for (uint32_t r = 0; r < h->n_inst; ++r) {
+    InstDesc &I = h->inst[r];
+    I.blocked = I.n <= kBMaxBlocks * kBCol ? 1u : 0u;
+    I.nb = I.blocked ? (I.n + kBCol - 1) / kBCol : 0u;
+    I.btile_base = nbt;
+    I.n_btiles = I.blocked ? (I.n + kBTileRows - 1) / kBTileRows : 0u;
+    I.bspmv = RedPlan{slot, I.n_btiles, group, (I.n_btiles + kGroup - 1) / kGroup};
+    slot += I.bspmv.n_slots;
+    group += I.bspmv.n_groups;
+    const uint32_t *rp = rp_host[r];
+    for (uint32_t q = 0; q < I.n_btiles; ++q) {
+      btile_inst.push_back(r);
+      bseg_base.push_back(nseg);
+      nseg += I.nb;
+      const uint32_t row0 = q * kBTileRows, row1 = std::min<uint32_t>(row0 + kBTileRows, I.n);
+      for (uint32_t row = row0; row < row1; ++row)
+        if (rp[row + 1] - rp[row] > kBLongDeg) long_rows.push_back(row - row0);
+      long_ptr.push_back((uint32_t)long_rows.size());
+    }
+    nbt += I.n_btiles;
+  }
+  h->total_btiles = nbt;
+  h->total_bseg = nseg;
+  h->total_slots = std::max(h->total_slots, slot);
+  h->total_groups = std::max(h->total_groups, group);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  if (nbt) {
+    uint32_t *seglen = nullptr;
+    chk(dalloc(&h->d_btile_inst, nbt));
+    chk(dalloc(&h->d_bseg_base, nbt));
+    chk(dalloc(&h->d_bseg_start, nseg));
+    chk(dalloc(&h->d_boff, nseg * (kBThreads + 1)));
+    chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
+    chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
+    chk(dalloc(&seglen, nseg));
+    if (e != cudaSuccess) {
+      cudaFree(seglen);
+      free_blocked(h);
+      return cuda_error(e, "blocked format: allocate");
+    }
+    chk(cudaMemcpyAsync(h->d_btile_inst, btile_inst.data(), nbt * 4, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(h->d_bseg_base, bseg_base.data(), nbt * 8, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(h->d_blong_ptr, long_ptr.data(), long_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!long_rows.empty())
+      chk(cudaMemcpyAsync(h->d_blong_rows, long_rows.data(), long_rows.size() * 4,
+                          cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
+                        cudaMemcpyHostToDevice, s));
+    bcount_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr,
+                                            h->col, h->d_boff, seglen);
+    chk(cudaGetLastError());
+    std::vector<uint32_t> len(nseg);
+    chk(cudaMemcpyAsync(len.data(), seglen, nseg * 4, cudaMemcpyDeviceToHost, s));
+    chk(cudaStreamSynchronize(s));
+    cudaFree(seglen);
+    std::vector<uint64_t> start(nseg);
+    uint64_t tot = 0;
+    for (uint64_t q = 0; q < nseg; ++q) {
+      start[q] = tot;
+      tot += len[q];
+    }
+    // 16 spare elements: the SpMV reads whole 16-byte / 8-byte vectors
+    chk(dalloc(&h->d_bcol, tot + 16));
+    chk(dalloc(&h->d_bslot, tot + 16));
+    if (e == cudaSuccess) {
+      chk(cudaMemsetAsync(h->d_bcol, 0, (tot + 16) * 2, s));
+      chk(cudaMemsetAsync(h->d_bslot, 0, tot + 16, s));
+      chk(cudaMemcpyAsync(h->d_bseg_start, start.data(), nseg * 8, cudaMemcpyHostToDevice, s));
+      bfill_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base,
+                                             h->d_bseg_start, h->d_boff, h->row_ptr, h->col,
+                                             h->d_bcol, h->d_bslot);
+      chk(cudaGetLastError());
+      chk(cudaStreamSynchronize(s));
+    }
+  } else {
+    chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
+                        cudaMemcpyHostToDevice, s));
+    chk(cudaStreamSynchronize(s));
+  }
+  if (e != cudaSuccess) {
+    free_blocked(h);
+    return cuda_error(e, "blocked format: build");
+  }
+  return CB_OK;
+}
+
+}  // namespace cb

@@ -25,6 +25,18 @@ constexpr uint32_t kChunk = 4096;    // edges per heavy-row chunk
 constexpr uint32_t kLongDeg = 1024;  // rows above this (<= kHeavyDeg) use the whole CTA
 constexpr int kNodeAlign = 32;       // per-instance node offset alignment (elements)
 
+// Column-blocked SpMV (FP32): a CTA of kBThreads owns kBTileRows rows,
+// kBRowsPerThread consecutive rows per thread; the columns are cut into
+// blocks of kBCol that are staged in shared memory, so every gather of v_j
+// is a shared-memory load.
+constexpr int kBThreads = 1024;
+constexpr int kBRowsPerThread = 16;
+constexpr int kBTileRows = kBThreads * kBRowsPerThread;  // 16384
+constexpr uint32_t kBColBits = 14;
+constexpr uint32_t kBCol = 1u << kBColBits;              // 16384 floats = 64 KB per buffer
+constexpr uint32_t kBMaxBlocks = 32;                     // blocked when n <= 32 * kBCol
+constexpr uint32_t kBLongDeg = 512;                      // longer rows: whole-CTA global gathers
+
 // Two-level deterministic reduction plan of one instance for one kernel kind:
 // one partial per slot, slots grouped by kGroup; the last CTA to arrive in a
 // group sums the group, the last group of the instance sums the groups.
@@ -45,6 +57,9 @@ struct InstDesc {
   uint32_t fin_base, n_fin;       // finalize tiles (kFinRows nodes each)
   RedPlan spmv;                   // slots: n_tiles normal tiles, then n_heavy rows
   RedPlan fin;                    // slots: n_fin tiles
+  uint32_t blocked, nb;           // column-blocked FP32 SpMV? number of column blocks
+  uint32_t btile_base, n_btiles;  // blocked tiles (kBTileRows rows each)
+  RedPlan bspmv;                  // slots: n_btiles
 };
 
 struct HeavyRow {
@@ -113,6 +128,17 @@ struct cb_graph {
   cb::HeavyRow *d_heavy = nullptr;
   uint32_t *d_chunk_heavy = nullptr;     // heavy-row index of each chunk
   uint32_t *d_fin_inst = nullptr;        // instance of each finalize tile
+  // column-blocked format (FP32 SpMV), for realisations with blocked = 1
+  uint32_t total_btiles = 0;
+  uint64_t total_bseg = 0;               // (tile, column block) segments
+  uint32_t *d_btile_inst = nullptr;      // realisation of each blocked tile
+  uint64_t *d_bseg_base = nullptr;       // first segment of each blocked tile
+  uint64_t *d_bseg_start = nullptr;      // first stream element of each segment
+  uint32_t *d_boff = nullptr;            // per segment: kBThreads + 1 stream offsets
+  uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per stream element
+  uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning thread per element
+  uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
+  uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
   cb::Workspace ws;   // Krylov basis from 1 (forward)
   cb::Workspace ws2;  // Krylov basis from the top-k indicator (adjoint)
   cb::BackWork bw;    // adjoint buffers
@@ -126,6 +152,10 @@ int cuda_error(cudaError_t e, const char *what);
 // optional per-launch event timing (cb_api.cu); no-ops unless enabled
 int prof_begin(int kernel, cudaStream_t s);
 void prof_end(int token, cudaStream_t s);
+
+// column-blocked format builder (cb_blocked.cu); host row_ptr views per realisation
+int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s);
+void free_blocked(cb_graph *h);
 
 // workspace for depth m in precision prec (cb_api.cu)
 int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream_t s);

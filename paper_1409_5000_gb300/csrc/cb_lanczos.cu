@@ -51,6 +51,14 @@ struct LArgs {
   double *cpart;   // per heavy-row chunk partial sums
   uint32_t *hcnt;  // per heavy row arrival counters
   double tau;      // breakdown tolerance
+  // column-blocked format (FP32 path)
+  const uint32_t *btile_inst;
+  const uint64_t *bseg_base, *bseg_start;
+  const uint32_t *boff;
+  const uint16_t *bcol;
+  const uint8_t *bslot;
+  const uint32_t *blong_ptr, *blong_rows;
+  uint32_t skip_blocked;  // the tiled-CSR kernel leaves blocked realisations alone
 };
 
 // Column indices are read once per step: streaming (evict-first) load.
@@ -162,6 +170,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
     r = a.tile_inst[tile];
   }
   if (j >= a.sc.meff[r]) return;  // realisation stopped (uniform per CTA)
+  if (a.skip_blocked && a.inst[r].blocked) return;  // the column-blocked kernel owns it
 
   const InstDesc &I = a.inst[r];
   const uint32_t *rp = a.row_ptr + I.rp_base;
@@ -302,6 +311,146 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
     finish_alpha<T>(a, r, j, total);
 }
 
+// ---------------------------------------------------------------------------
+// Column-blocked SpMV step (FP32).  Same arithmetic as spmv_kernel
+// (u = scale_j A W_j - beta_{j-1} scale_{j-1} W_{j-1}, alpha_j partial), but
+// every gather of W_j is a shared-memory load: the CTA walks the column
+// blocks of its tile, double-buffering each block of W_j into shared memory
+// with cp.async while the previous block is consumed.  Thread i owns rows
+// kBRowsPerThread*i .. +15 of the tile and accumulates them in shared memory
+// (slot-major, so the accumulator traffic is conflict-free); every row has a
+// single writer, so the result is deterministic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage x[b*kBCol, min((b+1)*kBCol, n)) into dst (x is 128-byte aligned).
+__device__ __forceinline__ void stage_block(float *dst, const float *x, uint32_t n, uint32_t b) {
+  const uint32_t lo = b * kBCol;
+  const uint32_t len = min(kBCol, n - lo);
+  const uint32_t n4 = len >> 2;
+  for (uint32_t q = threadIdx.x; q < n4; q += kBThreads) cp_async16(dst + 4 * q, x + lo + 4 * q);
+  for (uint32_t q = 4 * n4 + threadIdx.x; q < len; q += kBThreads) cp_async4(dst + q, x + lo + q);
+}
+
+constexpr size_t kBSmemBytes = (2 * kBCol + kBRowsPerThread * kBThreads) * sizeof(float);
+
+__global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j,
+                                                             uint32_t btile_off) {
+  extern __shared__ float4 s_dyn4[];
+  float *xs = reinterpret_cast<float *>(s_dyn4);  // two column blocks of W_j
+  float *sacc = xs + 2 * kBCol;                   // [slot][thread] row sums
+  __shared__ uint32_t s_long[kBTileRows / 32];    // bitmap of long rows
+  __shared__ double s_red[32];
+  __shared__ float s_rowsum[32];
+  const uint32_t t = btile_off + blockIdx.x;
+  const uint32_t r = a.btile_inst[t];
+  if (j >= a.sc.meff[r]) return;
+  const InstDesc &I = a.inst[r];
+  const uint32_t ms = a.sc.ms;
+  float *Vb = reinterpret_cast<float *>(a.V);
+  const float *x = Vb + (uint64_t)j * a.vs + I.node_base;
+  const bool has_prev = j > 0;
+  const float *xp = has_prev ? Vb + (uint64_t)(j - 1) * a.vs + I.node_base : x;
+  float *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
+  const float sj = (float)a.sc.scale[r * ms + j];
+  const float bp = has_prev ? (float)(a.sc.beta[r * ms + j - 1] * a.sc.scale[r * ms + j - 1]) : 0.f;
+  const uint32_t row0 = (t - I.btile_base) * kBTileRows;
+  const uint32_t tid = threadIdx.x;
+
+  for (uint32_t q = tid; q < kBRowsPerThread * kBThreads; q += kBThreads) sacc[q] = 0.f;
+  for (uint32_t q = tid; q < kBTileRows / 32; q += kBThreads) s_long[q] = 0u;
+  __syncthreads();
+  const uint32_t lp0 = a.blong_ptr[t], lp1 = a.blong_ptr[t + 1];
+  for (uint32_t q = lp0 + tid; q < lp1; q += kBThreads) {
+    const uint32_t lr = a.blong_rows[q];
+    atomicOr(&s_long[lr >> 5], 1u << (lr & 31));
+  }
+
+  const uint32_t nb = I.nb;
+  const uint64_t sbase = a.bseg_base[t];
+  stage_block(xs, x, I.n, 0);
+  cp_async_commit();
+  for (uint32_t b = 0; b < nb; ++b) {
+    if (b + 1 < nb) {
+      stage_block(xs + ((b + 1) & 1) * kBCol, x, I.n, b + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float *cur = xs + (b & 1) * kBCol;
+    const uint64_t seg = sbase + b;
+    const uint64_t s0 = a.bseg_start[seg];
+    const uint64_t start = s0 + a.boff[seg * (kBThreads + 1) + tid];
+    const uint64_t end = s0 + a.boff[seg * (kBThreads + 1) + tid + 1];
+    const uint64_t a0 = start & ~7ull;
+    const uint32_t nch = end > start ? (uint32_t)((end - a0 + 7) >> 3) : 0u;
+    const uint32_t maxch = __reduce_max_sync(0xffffffffu, nch);
+    for (uint32_t ch = 0; ch < maxch; ++ch) {
+      if (ch < nch) {
+        const uint64_t e0 = a0 + 8ull * ch;
+        const uint4 cv = __ldcs(reinterpret_cast<const uint4 *>(a.bcol + e0));
+        const uint2 sv = __ldcs(reinterpret_cast<const uint2 *>(a.bslot + e0));
+        const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint64_t e = e0 + q;
+          if (e >= start && e < end) {
+            const uint32_t c = (cw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+            const uint32_t k = ((q < 4 ? sv.x : sv.y) >> (8 * (q & 3))) & 0xffu;
+            sacc[k * kBThreads + tid] += cur[c];
+          }
+        }
+      }
+    }
+    __syncthreads();  // the buffer of block b is refilled at iteration b + 1
+  }
+
+  float acc = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < kBRowsPerThread; ++k) {
+    const uint32_t lr = kBRowsPerThread * tid + k;
+    const uint32_t row = row0 + lr;
+    if (row < I.n && !((s_long[lr >> 5] >> (lr & 31)) & 1u))
+      acc += row_epilogue<float>(sacc[k * kBThreads + tid], row, x, xp, out, sj, bp, has_prev);
+  }
+  // long rows: whole CTA per row from the CSR, in row order
+  const uint32_t *rp = a.row_ptr + I.rp_base;
+  const uint32_t *col = a.col + I.edge_base;
+  for (uint32_t q = lp0; q < lp1; ++q) {
+    const uint32_t row = row0 + a.blong_rows[q];
+    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    float sum = 0.f;
+    for (uint32_t e = e0 + tid; e < e1; e += kBThreads) sum += __ldg(x + ld_stream(col + e));
+    sum = warp_sum<float>(sum);
+    if ((tid & 31) == 0) s_rowsum[tid >> 5] = sum;
+    __syncthreads();
+    if (tid == 0) {
+      float tot = 0.f;
+      for (int w = 0; w < kBThreads / 32; ++w) tot += s_rowsum[w];
+      acc += row_epilogue<float>(tot, row, x, xp, out, sj, bp, has_prev);
+    }
+    __syncthreads();
+  }
+  const double part = block_sum_to_double<float>(acc, s_red);
+  double total;
+  if (arrive_and_reduce(I.bspmv, t - I.btile_base, r, part, a.red, &total))
+    finish_alpha<float>(a, r, j, total);
+}
+
 // w = W_{j+1} - alpha_j scale_j W_j, in place; beta_j = ||w||.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j, uint32_t fin_off) {
@@ -379,6 +528,16 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.cpart = W.cpart;
   a.hcnt = W.hcnt;
   a.tau = sizeof(T) == 4 ? 1e-5 : 1e-12;
+  a.btile_inst = h->d_btile_inst;
+  a.bseg_base = h->d_bseg_base;
+  a.bseg_start = h->d_bseg_start;
+  a.boff = h->d_boff;
+  a.bcol = h->d_bcol;
+  a.bslot = h->d_bslot;
+  a.blong_ptr = h->d_blong_ptr;
+  a.blong_rows = h->d_blong_rows;
+  const bool use_blocked = sizeof(T) == 4 && h->total_btiles > 0;
+  a.skip_blocked = use_blocked ? 1u : 0u;
 
   const InstDesc &A0 = h->inst[r0], &A1 = h->inst[r1 - 1];
   const uint32_t chunk_off = A0.chunk_base;
@@ -387,6 +546,16 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   const uint32_t n_tiles = A1.tile_base + A1.n_tiles - tile_off;
   const uint32_t fin_off = A0.fin_base;
   const uint32_t n_fin = A1.fin_base + A1.n_fin - fin_off;
+  const uint32_t btile_off = A0.btile_base;
+  const uint32_t n_btiles = use_blocked ? A1.btile_base + A1.n_btiles - btile_off : 0u;
+  if (n_btiles) {
+    static bool attr_set = false;  // one-time opt-in to > 48 KB of shared memory
+    if (!attr_set) {
+      cudaFuncSetAttribute(bspmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBSmemBytes);
+      attr_set = true;
+    }
+  }
 
   uint32_t nmax = 0;
   for (uint32_t r = r0; r < r1; ++r) nmax = h->inst[r].n > nmax ? h->inst[r].n : nmax;
@@ -402,6 +571,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   for (uint32_t j = 0; j < m; ++j) {
     tok = prof_begin(CB_K_SPMV, s);
     launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);
+    if (n_btiles) bspmv_kernel<<<n_btiles, kBThreads, kBSmemBytes, s>>>(a, j, btile_off);
     prof_end(tok, s);
     tok = prof_begin(CB_K_FINALIZE, s);
     if (n_fin) finalize_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off);

@@ -159,7 +159,8 @@ def test_empty_and_complete_breakdown(B):
     assert rep.m_eff == 1 and np.allclose(np.exp(theta) * y, 1.0, rtol=1e-7)
     g = synth.from_edges(40, np.array(pins.complete(40)))
     theta, y, rep = _single(B, g, 30, "fp32")
-    assert rep.m_eff == 1 and np.allclose(np.exp(theta) * y, math.exp(39), rtol=1e-6)
+    # FP32: theta = alpha_1 = 39 carries ~1e-7 relative error, i.e. ~4e-6 in e^theta
+    assert rep.m_eff == 1 and np.allclose(np.exp(theta) * y, math.exp(39), rtol=parity.TOL_FP32)
 
 
 @pytest.mark.parametrize("n,k", [(1, 1), (7, 7), (1000, 1), (100_000, 64), (1_234_567, 20),
@@ -221,3 +222,28 @@ def test_argument_errors(B):
     bad = _G(3, np.array([0, 1, 1, 1], np.uint32), np.array([2], np.uint32))  # not symmetric
     with pytest.raises(B.CBError):
         B.GraphSet([bad], validate=True)
+
+
+def test_column_blocked_matches_tiled_csr(B, monkeypatch):
+    """The FP32 column-blocked SpMV (shared-memory gathers) and the tiled-CSR
+    SpMV compute the same recurrence: results agree to FP32 rounding, and
+    both agree with the oracle.  n = 70 000 spans 5 column blocks and a
+    ragged last tile; a hub row takes the long-row tier."""
+    n = 70_000
+    g0 = synth.er(n, 12.0 / n, 41)
+    src = np.repeat(np.arange(n), np.diff(g0.row_ptr.astype(np.int64)))
+    base = [(int(a), int(b)) for a, b in zip(src, g0.col) if a < b]
+    hub = [(7, int(j)) for j in range(20_000, 21_000)]
+    g = synth.from_edges(n, base + hub)
+    res = {}
+    for mode in ("blocked", "csr"):
+        if mode == "csr":
+            monkeypatch.setenv("CB_NO_BLOCKED", "1")
+        else:
+            monkeypatch.delenv("CB_NO_BLOCKED", raising=False)
+        res[mode] = _single(B, g, 30, "fp32")
+    (tb, yb, _), (tc, yc, _) = res["blocked"], res["csr"]
+    e = parity.errors(tb, yb, tc, yc)  # head + normwise: the tail is FP32 noise in both
+    assert e["head_rel"] < 1e-5 and e["norm_rel"] < 1e-5, e
+    th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 30)
+    parity.assert_scores(tb, yb, th_o, y_o, "fp32")
