@@ -7,12 +7,17 @@
 //   * rows are tiled by kBTileRows; thread i of a tile owns the
 //     kBRowsPerThread consecutive rows starting at kBRowsPerThread * i;
 //   * a tile's edges are grouped by column block b = col >> kBColBits into
-//     one segment per (tile, b); inside a segment, thread i's edges (its
-//     rows in order, each row's columns in order) form one contiguous
-//     stream, streams in thread order;
-//   * each stream element stores the local column (u16, col & (kBCol-1))
-//     and the row slot of the owning thread (u8, 0..kBRowsPerThread-1);
-//   * per segment: kBThreads + 1 stream offsets (u32) and a u64 start.
+//     one segment per (tile, b); thread i's edges of a segment (its rows in
+//     order, each row's columns in order) form its stream;
+//   * the 32 streams of a warp are interleaved in stripes of 4: element q of
+//     lane l sits at start(segment, warp) + 128 (q / 4) + 4 l + q % 4, and
+//     every stream is padded to the warp's longest, rounded up to a multiple
+//     of 4 (len(segment, warp)).  A lane reads 4 columns (8 bytes) and 4
+//     slots (4 bytes) per stripe; a warp's stripe is 384 contiguous bytes, so
+//     the loads are coalesced and need no per-element range checks;
+//   * each element stores the local column (u16, col & (kBCol-1)) and the row
+//     slot of the owning lane (u8, 0..kBRowsPerThread-1); padding elements
+//     carry slot 0xff and are skipped.
 // Rows with more than kBLongDeg entries stay out of the streams; the SpMV
 // sums them from the CSR with whole-CTA global gathers.  Built on the device
 // from the CSR (one count pass, a host prefix over segment lengths, one
@@ -26,41 +31,11 @@ namespace cb {
 
 namespace {
 
-// Exclusive prefix sum over the kBThreads threads of the CTA; returns the
-// thread's offset and writes the CTA total to *total (all threads).
-__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sh /*[32]*/, uint32_t *total) {
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= (uint32_t)o) x += y;
-  }
-  if (lane == 31) sh[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = sh[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= (uint32_t)o) w += y;
-    }
-    sh[lane] = w;  // inclusive prefix of warp totals
-  }
-  __syncthreads();
-  const uint32_t before = (warp ? sh[warp - 1] : 0u) + x - v;
-  *total = sh[31];
-  __syncthreads();
-  return before;
-}
-
 __global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
                                                            const uint32_t *btile_inst,
                                                            const uint64_t *bseg_base,
                                                            const uint32_t *row_ptr,
-                                                           const uint32_t *col, uint32_t *boff,
-                                                           uint32_t *seglen) {
-  __shared__ uint32_t sh[32];
+                                                           const uint32_t *col, uint32_t *bwlen) {
   const uint32_t t = blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
@@ -79,22 +54,16 @@ __global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
     }
   }
   for (uint32_t b = 0; b < I.nb; ++b) {
-    uint32_t total;
-    const uint32_t off = block_exclusive_scan(len[b], sh, &total);
-    const uint64_t seg = bseg_base[t] + b;
-    boff[seg * (kBThreads + 1) + threadIdx.x] = off;
-    if (threadIdx.x == 0) {
-      boff[seg * (kBThreads + 1) + kBThreads] = total;
-      seglen[seg] = total;
-    }
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, len[b]);
+    if ((threadIdx.x & 31) == 0)
+      bwlen[(bseg_base[t] + b) * 32 + (threadIdx.x >> 5)] = (wmax + 3) & ~3u;
   }
 }
 
 __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
                                                           const uint32_t *btile_inst,
                                                           const uint64_t *bseg_base,
-                                                          const uint64_t *bseg_start,
-                                                          const uint32_t *boff,
+                                                          const uint64_t *bwstart,
                                                           const uint32_t *row_ptr,
                                                           const uint32_t *col, uint16_t *bcol,
                                                           uint8_t *bslot) {
@@ -103,10 +72,11 @@ __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
   const uint32_t *rp = row_ptr + I.rp_base;
   const uint32_t *cl = col + I.edge_base;
   const uint32_t row0 = (t - I.btile_base) * kBTileRows;
-  uint64_t cur[kBMaxBlocks];
+  uint64_t cur[kBMaxBlocks];  // lane's stripe base in each segment
+  uint32_t cnt[kBMaxBlocks];  // elements written so far
   for (uint32_t b = 0; b < I.nb; ++b) {
-    const uint64_t seg = bseg_base[t] + b;
-    cur[b] = bseg_start[seg] + boff[seg * (kBThreads + 1) + threadIdx.x];
+    cur[b] = bwstart[(bseg_base[t] + b) * 32 + (threadIdx.x >> 5)] + 4 * (threadIdx.x & 31);
+    cnt[b] = 0;
   }
   for (int k = 0; k < kBRowsPerThread; ++k) {
     const uint32_t row = row0 + kBRowsPerThread * threadIdx.x + k;
@@ -117,9 +87,10 @@ __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
       const uint32_t c = cl[e];
       const uint32_t b = c >> kBColBits;
       if (b >= I.nb) continue;
-      bcol[cur[b]] = (uint16_t)(c & (kBCol - 1));
-      bslot[cur[b]] = (uint8_t)k;
-      cur[b]++;
+      const uint64_t pos = cur[b] + 128ull * (cnt[b] >> 2) + (cnt[b] & 3);
+      bcol[pos] = (uint16_t)(c & (kBCol - 1));
+      bslot[pos] = (uint8_t)k;
+      cnt[b]++;
     }
   }
 }
@@ -134,15 +105,15 @@ cudaError_t dalloc(P **p, size_t count) {
 void free_blocked(cb_graph *h) {
   cudaFree(h->d_btile_inst);
   cudaFree(h->d_bseg_base);
-  cudaFree(h->d_bseg_start);
-  cudaFree(h->d_boff);
+  cudaFree(h->d_bwstart);
+  cudaFree(h->d_bwlen);
   cudaFree(h->d_bcol);
   cudaFree(h->d_bslot);
   cudaFree(h->d_blong_ptr);
   cudaFree(h->d_blong_rows);
   h->d_btile_inst = nullptr;
-  h->d_bseg_base = h->d_bseg_start = nullptr;
-  h->d_boff = nullptr;
+  h->d_bseg_base = h->d_bwstart = nullptr;
+  h->d_bwlen = nullptr;
   h->d_bcol = nullptr;
   h->d_bslot = nullptr;
   h->d_blong_ptr = h->d_blong_rows = nullptr;
@@ -188,16 +159,14 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     if (e == cudaSuccess) e = x;
   };
   if (nbt) {
-    uint32_t *seglen = nullptr;
+    const uint64_t nw = nseg * 32;
     chk(dalloc(&h->d_btile_inst, nbt));
     chk(dalloc(&h->d_bseg_base, nbt));
-    chk(dalloc(&h->d_bseg_start, nseg));
-    chk(dalloc(&h->d_boff, nseg * (kBThreads + 1)));
+    chk(dalloc(&h->d_bwstart, nw));
+    chk(dalloc(&h->d_bwlen, nw));
     chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
     chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
-    chk(dalloc(&seglen, nseg));
     if (e != cudaSuccess) {
-      cudaFree(seglen);
       free_blocked(h);
       return cuda_error(e, "blocked format: allocate");
     }
@@ -210,28 +179,26 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
                         cudaMemcpyHostToDevice, s));
     bcount_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr,
-                                            h->col, h->d_boff, seglen);
+                                            h->col, h->d_bwlen);
     chk(cudaGetLastError());
-    std::vector<uint32_t> len(nseg);
-    chk(cudaMemcpyAsync(len.data(), seglen, nseg * 4, cudaMemcpyDeviceToHost, s));
+    std::vector<uint32_t> len(nw);
+    chk(cudaMemcpyAsync(len.data(), h->d_bwlen, nw * 4, cudaMemcpyDeviceToHost, s));
     chk(cudaStreamSynchronize(s));
-    cudaFree(seglen);
-    std::vector<uint64_t> start(nseg);
+    std::vector<uint64_t> start(nw);
     uint64_t tot = 0;
-    for (uint64_t q = 0; q < nseg; ++q) {
+    for (uint64_t q = 0; q < nw; ++q) {
       start[q] = tot;
-      tot += len[q];
+      tot += 32ull * len[q];
     }
-    // 16 spare elements: the SpMV reads whole 16-byte / 8-byte vectors
     chk(dalloc(&h->d_bcol, tot + 16));
     chk(dalloc(&h->d_bslot, tot + 16));
     if (e == cudaSuccess) {
       chk(cudaMemsetAsync(h->d_bcol, 0, (tot + 16) * 2, s));
-      chk(cudaMemsetAsync(h->d_bslot, 0, tot + 16, s));
-      chk(cudaMemcpyAsync(h->d_bseg_start, start.data(), nseg * 8, cudaMemcpyHostToDevice, s));
+      chk(cudaMemsetAsync(h->d_bslot, 0xff, tot + 16, s));  // padding: no row slot
+      chk(cudaMemcpyAsync(h->d_bwstart, start.data(), nw * 8, cudaMemcpyHostToDevice, s));
       bfill_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base,
-                                             h->d_bseg_start, h->d_boff, h->row_ptr, h->col,
-                                             h->d_bcol, h->d_bslot);
+                                             h->d_bwstart, h->row_ptr, h->col, h->d_bcol,
+                                             h->d_bslot);
       chk(cudaGetLastError());
       chk(cudaStreamSynchronize(s));
     }

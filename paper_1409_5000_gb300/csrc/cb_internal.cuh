@@ -132,11 +132,11 @@ struct cb_graph {
   uint32_t total_btiles = 0;
   uint64_t total_bseg = 0;               // (tile, column block) segments
   uint32_t *d_btile_inst = nullptr;      // realisation of each blocked tile
-  uint64_t *d_bseg_base = nullptr;       // first segment of each blocked tile
-  uint64_t *d_bseg_start = nullptr;      // first stream element of each segment
-  uint32_t *d_boff = nullptr;            // per segment: kBThreads + 1 stream offsets
-  uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per stream element
-  uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning thread per element
+  uint64_t *d_bseg_base = nullptr;       // first (tile, column block) segment of each tile
+  uint64_t *d_bwstart = nullptr;         // per (segment, warp): first element of its region
+  uint32_t *d_bwlen = nullptr;           // per (segment, warp): longest lane stream
+  uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per element
+  uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane; 0xff = padding
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
   cb::Workspace ws;   // Krylov basis from 1 (forward)

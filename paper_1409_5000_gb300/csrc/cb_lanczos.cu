@@ -53,8 +53,8 @@ struct LArgs {
   double tau;      // breakdown tolerance
   // column-blocked format (FP32 path)
   const uint32_t *btile_inst;
-  const uint64_t *bseg_base, *bseg_start;
-  const uint32_t *boff;
+  const uint64_t *bseg_base, *bwstart;
+  const uint32_t *bwlen;
   const uint16_t *bcol;
   const uint8_t *bslot;
   const uint32_t *blong_ptr, *blong_rows;
@@ -344,6 +344,7 @@ __device__ __forceinline__ void stage_block(float *dst, const float *x, uint32_t
   for (uint32_t q = 4 * n4 + threadIdx.x; q < len; q += kBThreads) cp_async4(dst + q, x + lo + q);
 }
 
+// two column blocks of W_j, then kBRowsPerThread accumulator slots per thread
 constexpr size_t kBSmemBytes = (2 * kBCol + kBRowsPerThread * kBThreads) * sizeof(float);
 
 __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j,
@@ -380,10 +381,20 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
 
   const uint32_t nb = I.nb;
   const uint64_t sbase = a.bseg_base[t];
+  const uint32_t lane = tid & 31, warp = tid >> 5;
+  // this warp's interleaved region of block 0; the next block's is fetched
+  // one block ahead
+  uint64_t wst = a.bwstart[sbase * 32 + warp];
+  uint32_t wl = a.bwlen[sbase * 32 + warp];
   stage_block(xs, x, I.n, 0);
   cp_async_commit();
   for (uint32_t b = 0; b < nb; ++b) {
+    const uint64_t my = wst + 4 * lane;
+    const uint32_t len = wl;
     if (b + 1 < nb) {
+      const uint64_t nseg = sbase + b + 1;
+      wst = a.bwstart[nseg * 32 + warp];
+      wl = a.bwlen[nseg * 32 + warp];
       stage_block(xs + ((b + 1) & 1) * kBCol, x, I.n, b + 1);
       cp_async_commit();
       cp_async_wait<1>();
@@ -392,29 +403,27 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     }
     __syncthreads();
     const float *cur = xs + (b & 1) * kBCol;
-    const uint64_t seg = sbase + b;
-    const uint64_t s0 = a.bseg_start[seg];
-    const uint64_t start = s0 + a.boff[seg * (kBThreads + 1) + tid];
-    const uint64_t end = s0 + a.boff[seg * (kBThreads + 1) + tid + 1];
-    const uint64_t a0 = start & ~7ull;
-    const uint32_t nch = end > start ? (uint32_t)((end - a0 + 7) >> 3) : 0u;
-    const uint32_t maxch = __reduce_max_sync(0xffffffffu, nch);
-    for (uint32_t ch = 0; ch < maxch; ++ch) {
-      if (ch < nch) {
-        const uint64_t e0 = a0 + 8ull * ch;
-        const uint4 cv = __ldcs(reinterpret_cast<const uint4 *>(a.bcol + e0));
-        const uint2 sv = __ldcs(reinterpret_cast<const uint2 *>(a.bslot + e0));
-        const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
+    float *mine = sacc + tid;
+    const uint32_t ns = len >> 2;  // stripes of 4 elements (len is a multiple of 4)
+    for (uint32_t s0 = 0; s0 < ns; s0 += 8) {
+      uint2 cv[8];
+      uint32_t sv[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint64_t e = e0 + q;
-          if (e >= start && e < end) {
-            const uint32_t c = (cw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
-            const uint32_t k = ((q < 4 ? sv.x : sv.y) >> (8 * (q & 3))) & 0xffu;
-            sacc[k * kBThreads + tid] += cur[c];
+      for (int u = 0; u < 8; ++u)  // all of this round's stripe loads in flight at once
+        if (s0 + u < ns) {
+          cv[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * (s0 + u)));
+          sv[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * (s0 + u)));
+        }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < ns) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const uint32_t col = ((e < 2 ? cv[u].x : cv[u].y) >> (16 * (e & 1))) & 0xffffu;
+            const uint32_t k = (sv[u] >> (8 * e)) & 0xffu;
+            if (k < (uint32_t)kBRowsPerThread) mine[k * kBThreads] += cur[col];  // else padding
           }
         }
-      }
     }
     __syncthreads();  // the buffer of block b is refilled at iteration b + 1
   }
@@ -530,8 +539,8 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.tau = sizeof(T) == 4 ? 1e-5 : 1e-12;
   a.btile_inst = h->d_btile_inst;
   a.bseg_base = h->d_bseg_base;
-  a.bseg_start = h->d_bseg_start;
-  a.boff = h->d_boff;
+  a.bwstart = h->d_bwstart;
+  a.bwlen = h->d_bwlen;
   a.bcol = h->d_bcol;
   a.bslot = h->d_bslot;
   a.blong_ptr = h->d_blong_ptr;
