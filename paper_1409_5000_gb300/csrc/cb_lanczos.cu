@@ -382,19 +382,30 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   const uint32_t nb = I.nb;
   const uint64_t sbase = a.bseg_base[t];
   const uint32_t lane = tid & 31, warp = tid >> 5;
-  // this warp's interleaved region of block 0; the next block's is fetched
-  // one block ahead
-  uint64_t wst = a.bwstart[sbase * 32 + warp];
-  uint32_t wl = a.bwlen[sbase * 32 + warp];
+  // Stripe rounds: a warp's stream of block b has ns_b = len_b / 4 stripes,
+  // read 4 stripes (16 elements per lane) per round.  The loads of the next
+  // round -- in the same block or, after the last round, round 0 of the next
+  // block -- are issued before the current round is processed, so the
+  // global-memory latency overlaps the shared-memory work and the barrier.
+  uint64_t my = a.bwstart[sbase * 32 + warp] + 4 * lane;
+  uint32_t ns = a.bwlen[sbase * 32 + warp] >> 2;
+  uint2 cvA[4], cvB[4];
+  uint32_t svA[4], svB[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if ((uint32_t)u < ns) {
+      cvA[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * u));
+      svA[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * u));
+    }
   stage_block(xs, x, I.n, 0);
   cp_async_commit();
   for (uint32_t b = 0; b < nb; ++b) {
-    const uint64_t my = wst + 4 * lane;
-    const uint32_t len = wl;
+    uint64_t my1 = 0;
+    uint32_t ns1 = 0;
     if (b + 1 < nb) {
       const uint64_t nseg = sbase + b + 1;
-      wst = a.bwstart[nseg * 32 + warp];
-      wl = a.bwlen[nseg * 32 + warp];
+      my1 = a.bwstart[nseg * 32 + warp] + 4 * lane;
+      ns1 = a.bwlen[nseg * 32 + warp] >> 2;
       stage_block(xs + ((b + 1) & 1) * kBCol, x, I.n, b + 1);
       cp_async_commit();
       cp_async_wait<1>();
@@ -404,27 +415,46 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     __syncthreads();
     const float *cur = xs + (b & 1) * kBCol;
     float *mine = sacc + tid;
-    const uint32_t ns = len >> 2;  // stripes of 4 elements (len is a multiple of 4)
-    for (uint32_t s0 = 0; s0 < ns; s0 += 8) {
-      uint2 cv[8];
-      uint32_t sv[8];
+    const uint32_t nr = (ns + 3) >> 2;
+    const uint32_t iters = nr ? nr : 1u;  // one pass even when empty: prefetch the next block
+    for (uint32_t r = 0; r < iters; ++r) {
+      // next round's loads
+      if (r + 1 < nr) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u)  // all of this round's stripe loads in flight at once
-        if (s0 + u < ns) {
-          cv[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * (s0 + u)));
-          sv[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * (s0 + u)));
-        }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (s0 + u < ns) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const uint32_t col = ((e < 2 ? cv[u].x : cv[u].y) >> (16 * (e & 1))) & 0xffffu;
-            const uint32_t k = (sv[u] >> (8 * e)) & 0xffu;
-            if (k < (uint32_t)kBRowsPerThread) mine[k * kBThreads] += cur[col];  // else padding
+        for (int u = 0; u < 4; ++u)
+          if (4 * (r + 1) + u < ns) {
+            cvB[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * (4 * (r + 1) + u)));
+            svB[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * (4 * (r + 1) + u)));
           }
-        }
+      } else if (b + 1 < nb) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((uint32_t)u < ns1) {
+            cvB[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my1 + 128ull * u));
+            svB[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my1 + 128ull * u));
+          }
+      }
+      // this round
+      if (r < nr) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (4 * r + u < ns) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const uint32_t col = ((e < 2 ? cvA[u].x : cvA[u].y) >> (16 * (e & 1))) & 0xffffu;
+              const uint32_t k = (svA[u] >> (8 * e)) & 0xffu;
+              if (k < (uint32_t)kBRowsPerThread) mine[k * kBThreads] += cur[col];  // else padding
+            }
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cvA[u] = cvB[u];
+        svA[u] = svB[u];
+      }
     }
+    my = my1;
+    ns = ns1;
     __syncthreads();  // the buffer of block b is refilled at iteration b + 1
   }
 
