@@ -242,6 +242,9 @@ static int backward_t(cb_graph *h, uint32_t m, const uint32_t *idx, uint32_t k, 
                       double *log_scale, cudaStream_t s) {
   BackWork &B = h->bw;
   const uint32_t N = h->n_inst;
+  prefer_shared(bw_tridiag_kernel);
+  prefer_shared(bw_node_kernel<T>);
+  prefer_shared(bw_edge_kernel<T>);
   const int tok = prof_begin(CB_K_BACKWARD, s);
   bw_tridiag_kernel<<<N, 32, 0, s>>>(h->ws.sc, h->ws2.sc, h->d_inst, B.K, m, B.theta, B.cnt);
   const size_t shm = (size_t)(m * m + 8 * m * 32) * sizeof(T);

@@ -76,6 +76,17 @@ static void prof_clear() {
   g_prof.clear();
 }
 
+void prefer_shared_impl(const void *kernel) {
+  static std::mutex mu;
+  static std::vector<const void *> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const void *k : done)
+    if (k == kernel) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  done.push_back(kernel);
+}
+
 static int pick_lanes(double avg_deg) {
   if (const char *env = std::getenv("CB_LANES")) {
     int v = std::atoi(env);

@@ -4,8 +4,9 @@
 // (about one per clock per SM), while a shared-memory gather is ~6x cheaper.
 // The format lets the SpMV stage a block of kBCol entries of v_j in shared
 // memory and gather only from there:
-//   * rows are tiled by kBTileRows; thread i of a tile owns the
-//     kBRowsPerThread consecutive rows starting at kBRowsPerThread * i;
+//   * rows are tiled by kBTileRows; thread i of a tile owns rows
+//     i + kBThreads * k, k = 0..kBRowsPerThread-1 (row slot k), so even a
+//     partly filled tile spreads its rows over all warps;
 //   * a tile's edges are grouped by column block b = col >> kBColBits into
 //     one segment per (tile, b); thread i's edges of a segment (its rows in
 //     order, each row's columns in order) form its stream;
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
   uint32_t len[kBMaxBlocks];
   for (uint32_t b = 0; b < kBMaxBlocks; ++b) len[b] = 0;
   for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t row = row0 + kBRowsPerThread * threadIdx.x + k;
+    const uint32_t row = row0 + threadIdx.x + kBThreads * k;
     if (row >= I.n) break;
     const uint32_t e0 = rp[row], e1 = rp[row + 1];
     if (e1 - e0 > kBLongDeg) continue;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
     cnt[b] = 0;
   }
   for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t row = row0 + kBRowsPerThread * threadIdx.x + k;
+    const uint32_t row = row0 + threadIdx.x + kBThreads * k;
     if (row >= I.n) break;
     const uint32_t e0 = rp[row], e1 = rp[row + 1];
     if (e1 - e0 > kBLongDeg) continue;

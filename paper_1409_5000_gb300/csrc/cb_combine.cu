@@ -1,5 +1,9 @@
 // Combine step: scores from the Krylov basis, and the ensemble sum (eq. 5).
 //
+// Two phases for the ensemble: every realisation's y_r over all its nodes in
+// parallel (combine_y_kernel, bandwidth-bound reads of the basis), then the
+// ordered FP64 sum over realisations per node (combine_sum_kernel).
+//
 //   y_r(i) = beta0 (V_m c)_i = sum_j gamma_{r,j} W_{r,j}(i)        (eq. 4)
 //   S(i)   = sum_r [i < n_r] exp(theta_r - theta*) y_r(i)           (eq. 5)
 //   theta* = max_r theta_r
@@ -12,51 +16,76 @@
 
 namespace cb {
 
-template <typename T>
-__global__ void __launch_bounds__(256) combine_single_kernel(const T *V, uint64_t vs, Scalars sc,
-                                                             const InstDesc *inst, uint32_t r,
-                                                             double *y, double *log_scale) {
-  const InstDesc I = inst[r];
-  const uint32_t ms = sc.ms;
-  const uint32_t M = sc.meff[r];
-  const bool ok = sc.status[r] == CB_OK;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *log_scale = ok ? sc.theta[r] : __longlong_as_double(0x7ff8000000000000ll);
-  if (i >= I.n) return;
-  T acc = T(0);
-  const T *w = V + I.node_base + i;
-  for (uint32_t j = 0; j < M; ++j) acc += (T)sc.gamma[r * ms + j] * w[(uint64_t)j * vs];
-  y[i] = ok ? (double)acc : __longlong_as_double(0x7ff8000000000000ll);
+__global__ void log_scale_kernel(Scalars sc, uint32_t r, double *log_scale) {
+  if (threadIdx.x == 0)
+    *log_scale = sc.status[r] == CB_OK ? sc.theta[r] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
+// y(i) = sum_j gamma_{r,j} W_j(i) over one finalize tile (kFinRows nodes of
+// realisation r), 8 consecutive nodes per thread: the M loads of a thread
+// are independent, so they are all in flight together.  OutT is double for
+// the single-realisation result and T for the ensemble's per-realisation
+// terms (written into basis slot `out_slot`).
+template <typename T, typename OutT>
+__global__ void __launch_bounds__(256) combine_y_kernel(const T *V, uint64_t vs, Scalars sc,
+                                                        const InstDesc *inst,
+                                                        const uint32_t *fin_inst, uint32_t fin_off,
+                                                        OutT *out, bool out_is_basis) {
+  __shared__ T s_g[CB_MAX_M + 1];
+  const uint32_t t = fin_off + blockIdx.x;
+  const uint32_t r = fin_inst[t];
+  const InstDesc I = inst[r];
+  const uint32_t ms = sc.ms;
+  const uint32_t M = sc.status[r] == CB_OK ? sc.meff[r] : 0u;
+  for (uint32_t j = threadIdx.x; j < M; j += blockDim.x) s_g[j] = (T)sc.gamma[r * ms + j];
+  __syncthreads();
+  const uint32_t i0 = (t - I.fin_base) * kFinRows + 8 * threadIdx.x;
+  if (i0 >= I.n) return;
+  const uint32_t cnt = min(8u, I.n - i0);
+  T acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = T(0);
+  const T *w = V + I.node_base + i0;
+  for (uint32_t j = 0; j < M; ++j) {
+    const T g = s_g[j];
+    const T *wj = w + (uint64_t)j * vs;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if ((uint32_t)q < cnt) acc[q] += g * wj[q];
+  }
+  OutT *o = out_is_basis ? out + I.node_base + i0 : out + i0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if ((uint32_t)q < cnt) o[q] = (OutT)acc[q];
+}
+
+// S(i) = sum_r [i < n_r] exp(theta_r - theta*) y_r(i), in realisation order,
+// FP64; y_r was written into basis slot `yslot` by combine_y_kernel.
 template <typename T>
-__global__ void __launch_bounds__(256) combine_ensemble_kernel(const T *V, uint64_t vs,
-                                                               Scalars sc, const InstDesc *inst,
-                                                               uint32_t n_inst, uint32_t n_out,
-                                                               double *S, double *log_scale) {
-  // per-realisation tables staged in shared memory
+__global__ void __launch_bounds__(256) combine_sum_kernel(const T *Y, Scalars sc,
+                                                          const InstDesc *inst, uint32_t n_inst,
+                                                          uint32_t n_out, double *S,
+                                                          double *log_scale) {
   extern __shared__ unsigned char s_raw[];
-  double *s_wt = reinterpret_cast<double *>(s_raw);             // exp(theta_r - theta*)
-  uint64_t *s_base = reinterpret_cast<uint64_t *>(s_wt + n_inst); // node_base
-  uint32_t *s_n = reinterpret_cast<uint32_t *>(s_base + n_inst);  // n_r
-  uint32_t *s_m = s_n + n_inst;                                   // m_eff
+  double *s_wt = reinterpret_cast<double *>(s_raw);                // exp(theta_r - theta*)
+  uint64_t *s_base = reinterpret_cast<uint64_t *>(s_wt + n_inst);  // node_base
+  uint32_t *s_n = reinterpret_cast<uint32_t *>(s_base + n_inst);   // n_r
   __shared__ double s_max[8];
   __shared__ int s_badw[8];
-  double t = -1e308;
+  double tm = -1e308;
   int bad = 0;
   for (uint32_t r = threadIdx.x; r < n_inst; r += blockDim.x) {
-    t = fmax(t, sc.theta[r]);
+    tm = fmax(tm, sc.theta[r]);
     bad |= (sc.status[r] != CB_OK);
     s_base[r] = inst[r].node_base;
     s_n[r] = inst[r].n;
-    s_m[r] = sc.meff[r];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
-  if ((threadIdx.x & 31) == 0) { s_max[threadIdx.x >> 5] = t; s_badw[threadIdx.x >> 5] = bad; }
+  if ((threadIdx.x & 31) == 0) { s_max[threadIdx.x >> 5] = tm; s_badw[threadIdx.x >> 5] = bad; }
   __syncthreads();
   double tmax = s_max[0];
   int any_bad = s_badw[0];
@@ -67,53 +96,60 @@ __global__ void __launch_bounds__(256) combine_ensemble_kernel(const T *V, uint6
   const double qnan = __longlong_as_double(0x7ff8000000000000ll);
   if (i == 0) *log_scale = any_bad ? qnan : tmax;
   if (i >= n_out) return;
-  const uint32_t ms = sc.ms;
   double sum = 0.0;
-  for (uint32_t r = 0; r < n_inst; ++r) {
-    if (i >= s_n[r]) continue;
-    const uint32_t M = s_m[r];
-    const T *w = V + s_base[r] + i;
-    const double *g = sc.gamma + (uint64_t)r * ms;
-    T acc = T(0);
-    for (uint32_t j = 0; j < M; ++j) acc += (T)__ldg(g + j) * w[(uint64_t)j * vs];
-    sum += s_wt[r] * (double)acc;
-  }
+  for (uint32_t r = 0; r < n_inst; ++r)
+    if (i < s_n[r]) sum += s_wt[r] * (double)Y[s_base[r] + i];
   S[i] = any_bad ? qnan : sum;
 }
 
 int combine_single(cb_graph *h, uint32_t r, int prec, double *y, double *log_scale,
                    cudaStream_t s) {
-  const uint32_t n = h->inst[r].n;
-  const uint32_t grid = (n + 255) / 256;
+  const InstDesc &I = h->inst[r];
+  prefer_shared(combine_y_kernel<double, double>);
+  prefer_shared(combine_y_kernel<float, double>);
+  prefer_shared(log_scale_kernel);
   const int tok = prof_begin(CB_K_COMBINE, s);
-  if (prec == CB_FP64)
-    combine_single_kernel<double><<<grid, 256, 0, s>>>((const double *)h->ws.V, h->ws.vec_stride,
-                                                       h->ws.sc, h->d_inst, r, y, log_scale);
-  else
-    combine_single_kernel<float><<<grid, 256, 0, s>>>((const float *)h->ws.V, h->ws.vec_stride,
-                                                      h->ws.sc, h->d_inst, r, y, log_scale);
+  if (I.n_fin) {
+    if (prec == CB_FP64)
+      combine_y_kernel<double, double><<<I.n_fin, 256, 0, s>>>(
+          (const double *)h->ws.V, h->ws.vec_stride, h->ws.sc, h->d_inst, h->d_fin_inst,
+          I.fin_base, y, false);
+    else
+      combine_y_kernel<float, double><<<I.n_fin, 256, 0, s>>>(
+          (const float *)h->ws.V, h->ws.vec_stride, h->ws.sc, h->d_inst, h->d_fin_inst,
+          I.fin_base, y, false);
+  }
+  log_scale_kernel<<<1, 32, 0, s>>>(h->ws.sc, r, log_scale);
   prof_end(tok, s);
   return cuda_error(cudaGetLastError(), "combine launch");
 }
 
 int combine_ensemble(cb_graph *h, int prec, uint32_t n_out, double *S, double *log_scale,
                      cudaStream_t s) {
-  const uint32_t grid = (n_out + 255) / 256;
-  const size_t shm = (sizeof(double) + sizeof(uint64_t) + 2 * sizeof(uint32_t)) * h->n_inst;
+  const size_t shm = (sizeof(double) + sizeof(uint64_t) + sizeof(uint32_t)) * h->n_inst;
   if (shm > 200 * 1024) return set_error(CB_ERR_ARG, "too many realisations for one combine");
+  const uint32_t grid = (n_out + 255) / 256;
+  prefer_shared(combine_y_kernel<double, double>);
+  prefer_shared(combine_y_kernel<float, float>);
+  prefer_shared(combine_sum_kernel<double>);
+  prefer_shared(combine_sum_kernel<float>);
   const int tok = prof_begin(CB_K_COMBINE, s);
+  // per-realisation terms go into the last basis slot, which the combine never reads
+  const uint64_t yoff = (uint64_t)h->ws.m * h->ws.vec_stride;
   if (prec == CB_FP64) {
-    auto k = combine_ensemble_kernel<double>;
-    if (shm > 48 * 1024)
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k<<<grid, 256, shm, s>>>((const double *)h->ws.V, h->ws.vec_stride, h->ws.sc, h->d_inst,
-                             h->n_inst, n_out, S, log_scale);
+    double *Y = (double *)h->ws.V + yoff;
+    combine_y_kernel<double, double><<<h->total_fin, 256, 0, s>>>(
+        (const double *)h->ws.V, h->ws.vec_stride, h->ws.sc, h->d_inst, h->d_fin_inst, 0, Y, true);
+    auto k = combine_sum_kernel<double>;
+    if (shm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k<<<grid, 256, shm, s>>>(Y, h->ws.sc, h->d_inst, h->n_inst, n_out, S, log_scale);
   } else {
-    auto k = combine_ensemble_kernel<float>;
-    if (shm > 48 * 1024)
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k<<<grid, 256, shm, s>>>((const float *)h->ws.V, h->ws.vec_stride, h->ws.sc, h->d_inst,
-                             h->n_inst, n_out, S, log_scale);
+    float *Y = (float *)h->ws.V + yoff;
+    combine_y_kernel<float, float><<<h->total_fin, 256, 0, s>>>(
+        (const float *)h->ws.V, h->ws.vec_stride, h->ws.sc, h->d_inst, h->d_fin_inst, 0, Y, true);
+    auto k = combine_sum_kernel<float>;
+    if (shm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k<<<grid, 256, shm, s>>>(Y, h->ws.sc, h->d_inst, h->n_inst, n_out, S, log_scale);
   }
   prof_end(tok, s);
   return cuda_error(cudaGetLastError(), "combine launch");

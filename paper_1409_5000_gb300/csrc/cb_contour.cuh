@@ -37,57 +37,84 @@ __device__ __forceinline__ cplx cinv(cplx a) {
   return {a.re * d, -a.im * d};
 }
 
-__device__ inline bool laguerre_terms(const double *al, const double *be, int M, double x,
-                                      double *G, double *H) {
-  double r = x - al[0], rd = 1.0, rdd = 0.0;  // r_1 and its x-derivatives
-  if (!(r > 0.0)) return false;
-  double g = rd / r;
-  double h = g * g - rdd / r;
+// f'/f and (f'/f)^2 - f''/f of f(x) = det(xI - T) via the ratios
+// r_k = p_k / p_{k-1} of the leading principal minors and their derivatives
+// (one reciprocal per k).  Returns false if some r_k <= 0, i.e. x is not
+// above every eigenvalue of every leading block.  R is float or double.
+template <typename R>
+__device__ inline bool laguerre_terms(const double *al, const double *be, int M, R x, R *G,
+                                      R *H) {
+  R r = x - (R)al[0], rd = R(1), rdd = R(0);
+  if (!(r > R(0))) return false;
+  R ir = R(1) / r;
+  R g = rd * ir;
+  R h = g * g - rdd * ir;
   for (int k = 1; k < M; ++k) {
-    const double b2 = be[k - 1] * be[k - 1];
-    const double ir = 1.0 / r;
-    const double q = b2 * ir;
-    const double nr = (x - al[k]) - q;
-    const double nrd = 1.0 + q * ir * rd;
-    const double nrdd = b2 * ir * ir * (rdd - 2.0 * rd * rd * ir);
+    const R b2 = (R)be[k - 1] * (R)be[k - 1];
+    const R q = b2 * ir;
+    const R nr = (x - (R)al[k]) - q;
+    const R nrd = R(1) + q * ir * rd;
+    const R nrdd = q * ir * (rdd - R(2) * rd * rd * ir);
     r = nr;
     rd = nrd;
     rdd = nrdd;
-    if (!(r > 0.0)) return false;
-    const double gk = rd / r;
+    if (!(r > R(0))) return false;
+    ir = R(1) / r;
+    const R gk = rd * ir;
     g += gk;
-    h += gk * gk - rdd / r;
+    h += gk * gk - rdd * ir;
   }
   *G = g;
   *H = h;
   return true;
 }
 
-// Largest eigenvalue of tridiag(be, al, be) (be[0..M-2] used).
+// One Laguerre step from x (above the largest root); false when x is not
+// above the spectrum or the step is not finite.
+template <typename R>
+__device__ inline bool laguerre_step(const double *al, const double *be, int M, R x, R *step) {
+  R G, H;
+  if (!laguerre_terms<R>(al, be, M, x, &G, &H)) return false;
+  const R disc = (R)(M - 1) * ((R)M * H - G * G);
+  const R den = G + sqrt(disc > R(0) ? disc : R(0));
+  if (!(den > R(0))) return false;
+  *step = (R)M / den;
+  return true;
+}
+
+// Largest eigenvalue of tridiag(be, al, be) (be[0..M-2] used).  Laguerre's
+// iteration from above the Gershgorin bound runs in FP32 until its step is
+// below 1e-6 relative (FP64 arithmetic is scarce on GB300), then two FP64
+// steps polish the result: the convergence is cubic, so the FP32 estimate
+// turns into an FP64-accurate one.  theta only has to lie within rounding
+// of lambda_max for the contour rule to keep its accuracy.
 __device__ inline double lambda_max(const double *al, const double *be, int M) {
   if (M == 1) return al[0];
-  double x = -1e300;
+  double x0 = -1e300;
   for (int i = 0; i < M; ++i) {
     const double lo = i > 0 ? fabs(be[i - 1]) : 0.0;
     const double hi = i < M - 1 ? fabs(be[i]) : 0.0;
-    x = fmax(x, al[i] + lo + hi);
+    x0 = fmax(x0, al[i] + lo + hi);
   }
-  x += 1e-6 * (fabs(x) + 1.0);  // strictly above the spectrum
-  for (int it = 0; it < 64; ++it) {
-    double G, H;
-    if (!laguerre_terms(al, be, M, x, &G, &H)) break;
-    const double disc = fmax((M - 1.0) * (M * H - G * G), 0.0);
-    const double den = G + sqrt(disc);
-    if (!(den > 0.0)) break;
-    const double step = M / den;
-    const double nx = x - step;
-    double G2, H2;
-    if (!laguerre_terms(al, be, M, nx, &G2, &H2)) {
-      x = nx;  // rounding put nx at the root: within one step of it
-      break;
+  x0 += 1e-3 * (fabs(x0) + 1.0);  // strictly above the spectrum, also in FP32
+  float xf = (float)x0;
+  if ((double)xf < x0) xf = nextafterf(xf, 3.0e38f);
+  float st;
+  if (laguerre_step<float>(al, be, M, xf, &st)) {
+    for (int it = 0; it < 40; ++it) {
+      const float nx = xf - st;
+      float st2;
+      if (!laguerre_step<float>(al, be, M, nx, &st2)) break;  // nx not above: keep xf
+      xf = nx;
+      st = st2;
+      if (st <= 1e-6f * (fabsf(xf) + 1.0f)) break;
     }
-    x = nx;
-    if (step <= 1e-15 * fabs(x) + 1e-300) break;
+  }
+  double x = xf;
+  for (int it = 0; it < 2; ++it) {  // FP64 polish (a failed step leaves x above the root)
+    double sd;
+    if (!laguerre_step<double>(al, be, M, x, &sd)) break;
+    x -= sd;
   }
   return x;
 }

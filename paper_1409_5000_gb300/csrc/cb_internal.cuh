@@ -26,7 +26,7 @@ constexpr uint32_t kLongDeg = 1024;  // rows above this (<= kHeavyDeg) use the w
 constexpr int kNodeAlign = 32;       // per-instance node offset alignment (elements)
 
 // Column-blocked SpMV (FP32): a CTA of kBThreads owns kBTileRows rows,
-// kBRowsPerThread consecutive rows per thread; the columns are cut into
+// kBRowsPerThread rows per thread (strided by kBThreads); the columns are cut into
 // blocks of kBCol that are staged in shared memory, so every gather of v_j
 // is a shared-memory load.
 constexpr int kBThreads = 1024;
@@ -148,6 +148,15 @@ namespace cb {
 // error plumbing (cb_api.cu)
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);
+
+// One-time hint that a kernel should run with the shared-memory-heavy L1 /
+// shared split that the column-blocked SpMV needs, so that consecutive
+// launches of the library's kernels do not reconfigure the SM (cb_api.cu).
+void prefer_shared_impl(const void *kernel);
+template <typename K>
+inline void prefer_shared(K *kernel) {
+  prefer_shared_impl(reinterpret_cast<const void *>(kernel));
+}
 
 // optional per-launch event timing (cb_api.cu); no-ops unless enabled
 int prof_begin(int kernel, cudaStream_t s);

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
 // every gather of W_j is a shared-memory load: the CTA walks the column
 // blocks of its tile, double-buffering each block of W_j into shared memory
 // with cp.async while the previous block is consumed.  Thread i owns rows
-// kBRowsPerThread*i .. +15 of the tile and accumulates them in shared memory
+// i + kBThreads k (k = 0..15) of the tile and accumulates them in shared memory
 // (slot-major, so the accumulator traffic is conflict-free); every row has a
 // single writer, so the result is deterministic.
 // ---------------------------------------------------------------------------
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   float acc = 0.f;
 #pragma unroll 4
   for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t lr = kBRowsPerThread * tid + k;
+    const uint32_t lr = tid + kBThreads * k;  // row slot k of this thread
     const uint32_t row = row0 + lr;
     if (row < I.n && !((s_long[lr >> 5] >> (lr & 31)) & 1u))
       acc += row_epilogue<float>(sacc[k * kBThreads + tid], row, x, xp, out, sj, bp, has_prev);
@@ -490,9 +490,40 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     finish_alpha<float>(a, r, j, total);
 }
 
-// w = W_{j+1} - alpha_j scale_j W_j, in place; beta_j = ||w||.
+// w = W_{j+1} - alpha_j scale_j W_j, in place; beta_j = ||w||.  Each thread
+// owns 8 consecutive nodes of the tile (16- or 32-byte aligned vectors).
+template <typename T>
+struct Vec8;
+template <>
+struct Vec8<float> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[8]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  static __device__ __forceinline__ void store(float *p, const float (&v)[8]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <>
+struct Vec8<double> {
+  static __device__ __forceinline__ void load(const double *p, double (&v)[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 a = *reinterpret_cast<const double2 *>(p + 2 * q);
+      v[2 * q] = a.x;
+      v[2 * q + 1] = a.y;
+    }
+  }
+  static __device__ __forceinline__ void store(double *p, const double (&v)[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) *reinterpret_cast<double2 *>(p + 2 * q) = make_double2(v[2 * q], v[2 * q + 1]);
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j, uint32_t fin_off) {
+  static_assert(kFinRows == 8 * kThreads, "8 nodes per thread");
   __shared__ double s_red[32];
   const uint32_t t = fin_off + blockIdx.x;
   const uint32_t r = a.fin_inst[t];
@@ -503,13 +534,24 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j,
   const T *x = Vb + (uint64_t)j * a.vs + I.node_base;
   T *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
   const T coef = (T)(a.sc.alpha[r * ms + j] * a.sc.scale[r * ms + j]);
-  const uint32_t i0 = (t - I.fin_base) * kFinRows;
-  const uint32_t i1 = min(i0 + kFinRows, I.n);
+  const uint32_t i0 = (t - I.fin_base) * kFinRows + 8 * threadIdx.x;
   T acc = T(0);
-  for (uint32_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
-    const T w = out[i] - coef * x[i];
-    out[i] = w;
-    acc += w * w;
+  if (i0 + 8 <= I.n) {
+    T u[8], v[8];
+    Vec8<T>::load(out + i0, u);
+    Vec8<T>::load(x + i0, v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      u[q] -= coef * v[q];
+      acc += u[q] * u[q];
+    }
+    Vec8<T>::store(out + i0, u);
+  } else {
+    for (uint32_t i = i0; i < I.n; ++i) {
+      const T w = out[i] - coef * x[i];
+      out[i] = w;
+      acc += w * w;
+    }
   }
   const double part = block_sum_to_double<T>(acc, s_red);
   double total;
@@ -587,11 +629,15 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   const uint32_t n_fin = A1.fin_base + A1.n_fin - fin_off;
   const uint32_t btile_off = A0.btile_base;
   const uint32_t n_btiles = use_blocked ? A1.btile_base + A1.n_btiles - btile_off : 0u;
+  bool any_csr = !use_blocked;  // does the tiled-CSR kernel have work in the range?
+  for (uint32_t r = r0; r < r1 && !any_csr; ++r) any_csr = !h->inst[r].blocked;
   if (n_btiles) {
     static bool attr_set = false;  // one-time opt-in to > 48 KB of shared memory
     if (!attr_set) {
       cudaFuncSetAttribute(bspmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kBSmemBytes);
+      cudaFuncSetAttribute(bspmv_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
       attr_set = true;
     }
   }
@@ -599,6 +645,10 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   uint32_t nmax = 0;
   for (uint32_t r = r0; r < r1; ++r) nmax = h->inst[r].n > nmax ? h->inst[r].n : nmax;
   const uint32_t init_grid = (nmax + kThreads * 8 - 1) / (kThreads * 8);
+  prefer_shared(init_vec_kernel<T>);
+  prefer_shared(init_indicator_kernel<T>);
+  prefer_shared(init_scalars_kernel);
+  prefer_shared(finalize_kernel<T>);
   int tok = prof_begin(CB_K_INIT, s);
   init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1,
                                                                     start_idx ? T(0) : T(1));
@@ -609,7 +659,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   prof_end(tok, s);
   for (uint32_t j = 0; j < m; ++j) {
     tok = prof_begin(CB_K_SPMV, s);
-    launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);
+    if (any_csr) launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);
     if (n_btiles) bspmv_kernel<<<n_btiles, kBThreads, kBSmemBytes, s>>>(a, j, btile_off);
     prof_end(tok, s);
     tok = prof_begin(CB_K_FINALIZE, s);

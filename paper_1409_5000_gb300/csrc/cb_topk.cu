@@ -183,6 +183,10 @@ int topk_launch(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *
   uint32_t grid = (n + 256 * 8 - 1) / (256 * 8);
   if (grid > 152 * 8) grid = 152 * 8;
   if (grid == 0) grid = 1;
+  prefer_shared(topk_init);
+  prefer_shared(topk_pass);
+  prefer_shared(topk_collect);
+  prefer_shared(topk_sort);
   const int tok = prof_begin(CB_K_TOPK, s);
   topk_init<<<1, 256, 0, s>>>(st, k);
   for (uint32_t L = 0; L < 12; ++L) topk_pass<<<grid, 256, 0, s>>>(S, n, st, L);
