@@ -84,11 +84,13 @@ typedef struct {
  *              Host array.
  *   row_ptr[r] uint32[n[r]+1] row offsets (row_ptr[r][0] = 0).  Host
  *              pointers unless CB_DEVICE_PTRS is set.
- *   col[r]     uint32[nnz[r]] column indices, each row sorted or unsorted.
- *              Host pointers unless CB_DEVICE_PTRS is set.
- *   flags      CB_VALIDATE: check that row_ptr is monotone, cols are in
- *              range, there are no self-loops and the pattern is symmetric
- *              (host arrays only; O(nnz log) host time).
+ *   col[r]     uint32[nnz[r]] column indices, each row sorted ascending
+ *              without duplicates.  Host pointers unless CB_DEVICE_PTRS is set.
+ *   flags      CB_VALIDATE: check that row_ptr is monotone, rows are sorted
+ *              without duplicates, cols are in range, there are no
+ *              self-loops and the pattern is symmetric (host arrays only;
+ *              O(nnz * degree) host time).  Without it, unsorted rows are
+ *              still detected on the device (CB_ERR_ARG).
  *   stream     used for the copies.  The call synchronises `stream` before
  *              returning, so the input arrays may be freed afterwards.
  *   out        receives the handle.

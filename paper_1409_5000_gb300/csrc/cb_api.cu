@@ -76,6 +76,21 @@ static void prof_clear() {
   g_prof.clear();
 }
 
+void parallel_for(uint32_t n, const std::function<void(uint32_t)> &fn) {
+  unsigned hw = std::thread::hardware_concurrency();
+  const uint32_t nt = std::min<uint32_t>(n, hw ? std::min(hw, 32u) : 1u);
+  if (nt <= 1) {
+    for (uint32_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (uint32_t t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (uint32_t i = t; i < n; i += nt) fn(i);
+    });
+  for (auto &x : th) x.join();
+}
+
 void prefer_shared_impl(const void *kernel) {
   static std::mutex mu;
   static std::vector<const void *> done;
@@ -197,6 +212,10 @@ static int validate_host(uint32_t n, uint64_t nnz, const uint32_t *rp, const uin
     }
     for (uint32_t e = rp[i]; e < rp[i + 1]; ++e) {
       const uint32_t c = col[e];
+      if (e > rp[i] && c <= col[e - 1]) {
+        snprintf(buf, sizeof buf, "realisation %u: row %u not sorted ascending (or duplicate)", r, i);
+        return set_error(CB_ERR_ARG, buf);
+      }
       if (c >= n || c == i) {
         snprintf(buf, sizeof buf, "realisation %u: bad column %u in row %u", r, c, i);
         return set_error(CB_ERR_ARG, buf);
@@ -325,20 +344,24 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     delete h;
     return set_error(CB_ERR_ARG, "cb_graph_upload: input too large");
   }
-  // heavy rows (degree > kHeavyDeg), in realisation and row order
+  // heavy rows (degree > kHeavyDeg), in realisation and row order; the row
+  // scans run in parallel over realisations
+  std::vector<std::vector<uint32_t>> heavy_rows(n_inst);
+  parallel_for(n_inst, [&](uint32_t r) {
+    const uint32_t *rp = rp_of(r);
+    for (uint32_t i = 0; i < h->inst[r].n; ++i)
+      if (rp[i + 1] - rp[i] > kHeavyDeg) heavy_rows[r].push_back(i);
+  });
   uint32_t chunk_off = 0;
   for (uint32_t r = 0; r < n_inst; ++r) {
     InstDesc &I = h->inst[r];
     const uint32_t *rp = rp_of(r);
     I.heavy_base = (uint32_t)h->heavy.size();
     I.chunk_base = chunk_off;
-    for (uint32_t i = 0; i < I.n; ++i) {
-      const uint32_t deg = rp[i + 1] - rp[i];
-      if (deg > kHeavyDeg) {
-        const uint32_t nc = (deg + kChunk - 1) / kChunk;
-        h->heavy.push_back(HeavyRow{r, i, chunk_off, nc});
-        chunk_off += nc;
-      }
+    for (uint32_t i : heavy_rows[r]) {
+      const uint32_t nc = (rp[i + 1] - rp[i] + kChunk - 1) / kChunk;
+      h->heavy.push_back(HeavyRow{r, i, chunk_off, nc});
+      chunk_off += nc;
     }
     I.n_heavy = (uint32_t)h->heavy.size() - I.heavy_base;
     I.n_chunks = chunk_off - I.chunk_base;

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
                                                            const uint32_t *btile_inst,
                                                            const uint64_t *bseg_base,
                                                            const uint32_t *row_ptr,
-                                                           const uint32_t *col, uint32_t *bwlen) {
+                                                           const uint32_t *col, uint32_t *bwlen,
+                                                           uint32_t *unsorted) {
   const uint32_t t = blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
     for (uint32_t e = e0; e < e1; ++e) {
       const uint32_t b = cl[e] >> kBColBits;
       if (b < I.nb) len[b]++;  // columns >= n are invalid input: skipped
+      if (e > e0 && cl[e] < cl[e - 1]) *unsorted = 1u;  // the fill needs sorted rows
     }
   }
   for (uint32_t b = 0; b < I.nb; ++b) {
@@ -61,6 +63,9 @@ __global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
   }
 }
 
+// Fill the streams one column block at a time: each row keeps a cursor into
+// its (column-sorted) CSR row, so block b's edges of a row are the ones
+// under the cursor, and all writes of block b land in this warp's region.
 __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
                                                           const uint32_t *btile_inst,
                                                           const uint64_t *bseg_base,
@@ -73,25 +78,37 @@ __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
   const uint32_t *rp = row_ptr + I.rp_base;
   const uint32_t *cl = col + I.edge_base;
   const uint32_t row0 = (t - I.btile_base) * kBTileRows;
-  uint64_t cur[kBMaxBlocks];  // lane's stripe base in each segment
-  uint32_t cnt[kBMaxBlocks];  // elements written so far
-  for (uint32_t b = 0; b < I.nb; ++b) {
-    cur[b] = bwstart[(bseg_base[t] + b) * 32 + (threadIdx.x >> 5)] + 4 * (threadIdx.x & 31);
-    cnt[b] = 0;
-  }
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t cur[kBRowsPerThread], end[kBRowsPerThread];
+#pragma unroll
   for (int k = 0; k < kBRowsPerThread; ++k) {
     const uint32_t row = row0 + threadIdx.x + kBThreads * k;
-    if (row >= I.n) break;
-    const uint32_t e0 = rp[row], e1 = rp[row + 1];
-    if (e1 - e0 > kBLongDeg) continue;
-    for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t c = cl[e];
-      const uint32_t b = c >> kBColBits;
-      if (b >= I.nb) continue;
-      const uint64_t pos = cur[b] + 128ull * (cnt[b] >> 2) + (cnt[b] & 3);
-      bcol[pos] = (uint16_t)(c & (kBCol - 1));
-      bslot[pos] = (uint8_t)k;
-      cnt[b]++;
+    cur[k] = end[k] = 0;
+    if (row < I.n) {
+      const uint32_t e0 = rp[row], e1 = rp[row + 1];
+      if (e1 - e0 <= kBLongDeg) {
+        cur[k] = e0;
+        end[k] = e1;
+      }
+    }
+  }
+  for (uint32_t b = 0; b < I.nb; ++b) {
+    const uint64_t base = bwstart[(bseg_base[t] + b) * 32 + warp] + 4 * lane;
+    uint32_t q = 0;
+#pragma unroll
+    for (int k = 0; k < kBRowsPerThread; ++k) {
+      while (cur[k] < end[k]) {
+        const uint32_t c = cl[cur[k]];
+        const uint32_t cb = c >> kBColBits;
+        if (cb > b) break;  // the row's next edges belong to a later block
+        if (cb == b) {
+          const uint64_t pos = base + 128ull * (q >> 2) + (q & 3);
+          bcol[pos] = (uint16_t)(c & (kBCol - 1));
+          bslot[pos] = (uint8_t)k;
+          ++q;
+        }
+        ++cur[k];
+      }
     }
   }
 }
@@ -130,6 +147,24 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
   std::vector<uint32_t> btile_inst;
   std::vector<uint64_t> bseg_base;
   std::vector<uint32_t> long_ptr(1, 0), long_rows;
+  // long rows per tile, scanned in parallel over realisations
+  std::vector<std::vector<uint32_t>> lrows(h->n_inst), lcount(h->n_inst);
+  parallel_for(h->n_inst, [&](uint32_t r) {
+    const InstDesc &I = h->inst[r];
+    if (I.n > kBMaxBlocks * kBCol) return;
+    const uint32_t *rp = rp_host[r];
+    const uint32_t ntile = (I.n + kBTileRows - 1) / kBTileRows;
+    for (uint32_t q = 0; q < ntile; ++q) {
+      const uint32_t row0 = q * kBTileRows, row1 = std::min<uint32_t>(row0 + kBTileRows, I.n);
+      uint32_t c = 0;
+      for (uint32_t row = row0; row < row1; ++row)
+        if (rp[row + 1] - rp[row] > kBLongDeg) {
+          lrows[r].push_back(row - row0);
+          ++c;
+        }
+      lcount[r].push_back(c);
+    }
+  });
   for (uint32_t r = 0; r < h->n_inst; ++r) {
     InstDesc &I = h->inst[r];
     I.blocked = I.n <= kBMaxBlocks * kBCol ? 1u : 0u;
@@ -139,16 +174,13 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     I.bspmv = RedPlan{slot, I.n_btiles, group, (I.n_btiles + kGroup - 1) / kGroup};
     slot += I.bspmv.n_slots;
     group += I.bspmv.n_groups;
-    const uint32_t *rp = rp_host[r];
     for (uint32_t q = 0; q < I.n_btiles; ++q) {
       btile_inst.push_back(r);
       bseg_base.push_back(nseg);
       nseg += I.nb;
-      const uint32_t row0 = q * kBTileRows, row1 = std::min<uint32_t>(row0 + kBTileRows, I.n);
-      for (uint32_t row = row0; row < row1; ++row)
-        if (rp[row + 1] - rp[row] > kBLongDeg) long_rows.push_back(row - row0);
-      long_ptr.push_back((uint32_t)long_rows.size());
+      long_ptr.push_back(long_ptr.back() + lcount[r][q]);
     }
+    long_rows.insert(long_rows.end(), lrows[r].begin(), lrows[r].end());
     nbt += I.n_btiles;
   }
   h->total_btiles = nbt;
@@ -179,12 +211,22 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
                           cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
                         cudaMemcpyHostToDevice, s));
+    uint32_t *d_unsorted = nullptr;
+    chk(dalloc(&d_unsorted, 1));
+    if (e == cudaSuccess) chk(cudaMemsetAsync(d_unsorted, 0, 4, s));
     bcount_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr,
-                                            h->col, h->d_bwlen);
+                                            h->col, h->d_bwlen, d_unsorted);
     chk(cudaGetLastError());
     std::vector<uint32_t> len(nw);
+    uint32_t unsorted = 0;
     chk(cudaMemcpyAsync(len.data(), h->d_bwlen, nw * 4, cudaMemcpyDeviceToHost, s));
+    chk(cudaMemcpyAsync(&unsorted, d_unsorted, 4, cudaMemcpyDeviceToHost, s));
     chk(cudaStreamSynchronize(s));
+    cudaFree(d_unsorted);
+    if (e == cudaSuccess && unsorted) {
+      free_blocked(h);
+      return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
+    }
     std::vector<uint64_t> start(nw);
     uint64_t tot = 0;
     for (uint64_t q = 0; q < nw; ++q) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -145,6 +146,9 @@ struct cb_graph {
 };
 
 namespace cb {
+// fn(i) for i in [0, n) on the host, spread over the hardware threads
+void parallel_for(uint32_t n, const std::function<void(uint32_t)> &fn);
+
 // error plumbing (cb_api.cu)
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);

@@ -247,3 +247,15 @@ def test_column_blocked_matches_tiled_csr(B, monkeypatch):
     assert e["head_rel"] < 1e-5 and e["norm_rel"] < 1e-5, e
     th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 30)
     parity.assert_scores(tb, yb, th_o, y_o, "fp32")
+
+
+def test_unsorted_rows_rejected(B):
+    """The column-blocked format needs each row sorted: an unsorted row is an
+    argument error at upload, not a silent miscount."""
+    g = synth.er(2000, 0.01, 3)
+    col = g.col.copy()
+    rp = g.row_ptr
+    i = int(np.argmax(np.diff(rp.astype(np.int64))))
+    col[rp[i]:rp[i + 1]] = col[rp[i]:rp[i + 1]][::-1].copy()
+    with pytest.raises(B.CBError):
+        B.GraphSet([_G(g.n, rp, col)])
