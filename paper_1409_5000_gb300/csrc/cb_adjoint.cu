@@ -204,6 +204,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, uint32_t mpad,
                                                       const InstDesc *inst,
                                                       const uint32_t *tile_inst,
+                                                      const uint2 *tile_rows,
                                                       const uint32_t *row_ptr, const uint32_t *col,
                                                       const double *theta_in, float *grad) {
   __shared__ uint32_t s_rp[kTileRows + 1];
@@ -212,8 +213,9 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
   const InstDesc I = inst[r];
   const uint32_t *rp = row_ptr + I.rp_base;
   const uint32_t *cl = col + I.edge_base;
-  const uint32_t row0 = (t - I.tile_base) * kTileRows;
-  const uint32_t nrows = min((uint32_t)kTileRows, I.n - row0);
+  const uint2 tr = tile_rows[t];
+  const uint32_t row0 = tr.x;
+  const uint32_t nrows = tr.y - tr.x;
   for (uint32_t q = threadIdx.x; q <= nrows; q += blockDim.x) s_rp[q] = rp[row0 + q];
   __syncthreads();
   const uint32_t e0 = s_rp[0], e1 = s_rp[nrows];
@@ -254,7 +256,8 @@ static int backward_t(cb_graph *h, uint32_t m, const uint32_t *idx, uint32_t k, 
                                     h->ws.sc, h->ws2.sc, h->d_inst, h->d_fin_inst, N, B.K, m,
                                     B.theta, B.mpad, (T *)B.P, (T *)B.U, log_scale);
   bw_edge_kernel<T><<<h->total_tiles, 256, 0, s>>>((const T *)B.P, (const T *)B.U, B.mpad,
-                                                   h->d_inst, h->d_tile_inst, h->row_ptr, h->col,
+                                                   h->d_inst, h->d_tile_inst, h->d_tile_rows,
+                                                   h->row_ptr, h->col,
                                                    B.theta, grad);
   prof_end(tok, s);
   (void)idx;

@@ -5,7 +5,8 @@
 // the static launch tables of the Lanczos kernels:
 //   * every realisation's node range is padded to kNodeAlign elements in the
 //     Krylov vectors, so vector tiles start aligned;
-//   * SpMV tiles of kTileRows rows; rows with more than kHeavyDeg entries are
+//   * SpMV tiles of at most kTileRows rows and about kTileNnz entries; rows
+//     with more than kHeavyDeg entries are
 //     listed as heavy rows and cut into kChunk-edge chunks;
 //   * finalize tiles of kFinRows nodes;
 //   * one reduction plan (slots and groups) per realisation and kernel kind.
@@ -131,6 +132,7 @@ static void free_graph_arrays(cb_graph *h) {
   cudaFree(h->row_ptr);
   cudaFree(h->d_inst);
   cudaFree(h->d_tile_inst);
+  cudaFree(h->d_tile_rows);
   cudaFree(h->d_heavy);
   cudaFree(h->d_chunk_heavy);
   cudaFree(h->d_fin_inst);
@@ -138,6 +140,7 @@ static void free_graph_arrays(cb_graph *h) {
   h->row_ptr = nullptr;
   h->d_inst = nullptr;
   h->d_tile_inst = nullptr;
+  h->d_tile_rows = nullptr;
   h->d_heavy = nullptr;
   h->d_chunk_heavy = nullptr;
   h->d_fin_inst = nullptr;
@@ -332,9 +335,6 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     node_off += ((uint64_t)n[r] + kNodeAlign - 1) / kNodeAlign * kNodeAlign;
     edge_off += nnz[r];
     rp_off += (uint64_t)n[r] + 1;
-    I.tile_base = tile_off;
-    I.n_tiles = (n[r] + kTileRows - 1) / kTileRows;
-    tile_off += I.n_tiles;
     I.fin_base = fin_off;
     I.n_fin = (n[r] + kFinRows - 1) / kFinRows;
     fin_off += I.n_fin;
@@ -346,12 +346,32 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   }
   // heavy rows (degree > kHeavyDeg), in realisation and row order; the row
   // scans run in parallel over realisations
-  std::vector<std::vector<uint32_t>> heavy_rows(n_inst);
+  // SpMV tiles are balanced by entries: a tile closes at kTileRows rows or
+  // before it would exceed kTileNnz entries (heavy rows count as empty here:
+  // their chunks run in CTAs of their own), so hub-heavy regions of a graph
+  // get short tiles and no CTA becomes a straggler.
+  std::vector<std::vector<uint32_t>> heavy_rows(n_inst), tile_starts(n_inst);
   parallel_for(n_inst, [&](uint32_t r) {
     const uint32_t *rp = rp_of(r);
-    for (uint32_t i = 0; i < h->inst[r].n; ++i)
-      if (rp[i + 1] - rp[i] > kHeavyDeg) heavy_rows[r].push_back(i);
+    uint32_t rows = 0, acc = 0;
+    for (uint32_t i = 0; i < h->inst[r].n; ++i) {
+      const uint32_t deg = rp[i + 1] - rp[i];
+      if (deg > kHeavyDeg) heavy_rows[r].push_back(i);
+      const uint32_t w = deg > kHeavyDeg ? 0u : deg;
+      if (rows == 0 || rows == (uint32_t)kTileRows || (acc > 0 && acc + w > kTileNnz)) {
+        tile_starts[r].push_back(i);
+        rows = 0;
+        acc = 0;
+      }
+      ++rows;
+      acc += w;
+    }
   });
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    h->inst[r].tile_base = tile_off;
+    h->inst[r].n_tiles = (uint32_t)tile_starts[r].size();
+    tile_off += h->inst[r].n_tiles;
+  }
   uint32_t chunk_off = 0;
   for (uint32_t r = 0; r < n_inst; ++r) {
     InstDesc &I = h->inst[r];
@@ -397,6 +417,12 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
 
   // per-tile instance tables
   std::vector<uint32_t> tile_inst(std::max<uint32_t>(tile_off, 1)), fin_inst(std::max<uint32_t>(fin_off, 1));
+  std::vector<uint2> tile_rows(std::max<uint32_t>(tile_off, 1));
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    const auto &ts = tile_starts[r];
+    for (size_t q = 0; q < ts.size(); ++q)
+      tile_rows[h->inst[r].tile_base + q] = make_uint2(ts[q], q + 1 < ts.size() ? ts[q + 1] : h->inst[r].n);
+  }
   std::vector<uint32_t> chunk_heavy(std::max<uint32_t>(chunk_off, 1));
   for (uint32_t r = 0; r < n_inst; ++r) {
     const InstDesc &I = h->inst[r];
@@ -414,6 +440,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   chk(dalloc(&h->row_ptr, rp_off));
   chk(dalloc(&h->d_inst, n_inst));
   chk(dalloc(&h->d_tile_inst, tile_inst.size()));
+  chk(dalloc(&h->d_tile_rows, tile_rows.size()));
   chk(dalloc(&h->d_fin_inst, fin_inst.size()));
   chk(dalloc(&h->d_heavy, std::max<size_t>(h->heavy.size(), 1)));
   chk(dalloc(&h->d_chunk_heavy, chunk_heavy.size()));
@@ -430,6 +457,8 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   }
   chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), n_inst * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(h->d_tile_inst, tile_inst.data(), tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(h->d_tile_rows, tile_rows.data(), tile_rows.size() * sizeof(uint2),
+                      cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(h->d_fin_inst, fin_inst.data(), fin_inst.size() * 4, cudaMemcpyHostToDevice, s));
   if (!h->heavy.empty())
     chk(cudaMemcpyAsync(h->d_heavy, h->heavy.data(), h->heavy.size() * sizeof(HeavyRow),

@@ -18,7 +18,8 @@ namespace cb {
 // Layout constants
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;        // threads per CTA in the SpMV / finalize kernels
-constexpr int kTileRows = 256;       // rows per SpMV tile
+constexpr int kTileRows = 256;       // most rows per SpMV tile
+constexpr uint32_t kTileNnz = 6144;  // a tile closes before it exceeds this many entries
 constexpr int kFinRows = 2048;       // nodes per finalize tile (256 threads x 8)
 constexpr int kGroup = 32;           // reduction slots per last-arriver group
 constexpr uint32_t kHeavyDeg = 8192; // rows above this degree are split across CTAs
@@ -52,7 +53,7 @@ struct InstDesc {
   uint64_t rp_base;    // offset of row_ptr[0] in the row_ptr array
   uint32_t n;
   uint32_t nnz_hi;     // unused (nnz < 2^32 per instance); keeps alignment
-  uint32_t tile_base, n_tiles;    // SpMV tiles (kTileRows rows each)
+  uint32_t tile_base, n_tiles;    // SpMV tiles (<= kTileRows rows, ~kTileNnz entries)
   uint32_t heavy_base, n_heavy;   // heavy rows
   uint32_t chunk_base, n_chunks;  // heavy-row chunks
   uint32_t fin_base, n_fin;       // finalize tiles (kFinRows nodes each)
@@ -126,6 +127,7 @@ struct cb_graph {
   uint32_t *row_ptr = nullptr;
   cb::InstDesc *d_inst = nullptr;
   uint32_t *d_tile_inst = nullptr;       // instance of each normal tile
+  uint2 *d_tile_rows = nullptr;          // [first, last) local row of each normal tile
   cb::HeavyRow *d_heavy = nullptr;
   uint32_t *d_chunk_heavy = nullptr;     // heavy-row index of each chunk
   uint32_t *d_fin_inst = nullptr;        // instance of each finalize tile

@@ -23,7 +23,8 @@
 // Sidford 2018), which the parity tests check against the FP64 oracle that
 // reorthogonalises fully.
 //
-// SpMV work split.  A CTA owns kTileRows consecutive rows.  Rows with at
+// SpMV work split.  A CTA owns a tile of consecutive rows (at most kTileRows,
+// closed before kTileNnz entries, so hub regions get short tiles).  Rows with at
 // most 8*G entries are summed by G-lane groups; longer rows up to kLongDeg
 // by one warp each; rows up to kHeavyDeg by the whole CTA; rows above
 // kHeavyDeg are cut into kChunk-edge chunks, one CTA per chunk, and the last
@@ -39,6 +40,7 @@ namespace cb {
 struct LArgs {
   const InstDesc *inst;
   const uint32_t *tile_inst;
+  const uint2 *tile_rows;
   const HeavyRow *heavy;
   const uint32_t *chunk_heavy;
   const uint32_t *fin_inst;
@@ -215,8 +217,9 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
   }
 
   // ---- normal tile ----
-  const uint32_t row0 = (tile - I.tile_base) * kTileRows;
-  const uint32_t nrows = min((uint32_t)kTileRows, I.n - row0);
+  const uint2 tr = a.tile_rows[tile];
+  const uint32_t row0 = tr.x;
+  const uint32_t nrows = tr.y - tr.x;  // <= kTileRows
   // the tile's row offsets, staged once (coalesced)
   for (uint32_t q = threadIdx.x; q <= nrows; q += kThreads) s_rp[q] = rp[row0 + q];
   __syncthreads();
@@ -597,6 +600,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   LArgs a;
   a.inst = h->d_inst;
   a.tile_inst = h->d_tile_inst;
+  a.tile_rows = h->d_tile_rows;
   a.heavy = h->d_heavy;
   a.chunk_heavy = h->d_chunk_heavy;
   a.fin_inst = h->d_fin_inst;
