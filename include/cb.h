@@ -140,6 +140,13 @@ int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, double 
  *   S          device, double[n_out], written.
  *   log_scale  device, double[1], written.
  *   rep        optional host cb_inst_report[N] (forces a synchronise).
+ * The second call with the same (m, prec, n_out, S, log_scale) on a handle
+ * captures the pass into a CUDA graph (on a private stream; nothing runs
+ * there) and later calls replay it on `stream`: one launch per call instead
+ * of 2m + 5.  A handle keeps up to 8 such graphs; growing the workspace
+ * (a larger m, another precision) retires them.  The environment variable
+ * CB_NO_GRAPH (any value) forces direct launches; so do cb_profile_enable(1)
+ * and a non-null rep.  Results are bit-identical either way.
  */
 int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out, double *S,
                        double *log_scale, cb_inst_report *rep, void *stream);

@@ -23,6 +23,8 @@
 // node) and every CSR entry (i, j) gets g = P_i . U_j + P_j . U_i: FP32 (or
 // FP64) values, FP64 accumulation.  Realisations share one shift theta* =
 // max_r theta_r; dL/da_e = exp(theta*) * grad[e].
+#include <cstdlib>
+
 #include "cb_contour.cuh"
 
 namespace cb {
@@ -200,6 +202,11 @@ __device__ __forceinline__ double dot4(const double *a, const double *b) {
 }
 
 // g_e = P_i . U_j + P_j . U_i for every CSR entry e = (i, j) of one SpMV tile.
+// A group of kEdgeLanes lanes shares an edge: lane c takes the 4-value chunks
+// c, c + kEdgeLanes, ... of the four node-major rows, so each row is read as
+// whole 128-byte lines; the FP64 partials are summed across the group with
+// shuffles.
+constexpr uint32_t kEdgeLanes = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, uint32_t mpad,
                                                       const InstDesc *inst,
@@ -221,9 +228,13 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
   const uint32_t e0 = s_rp[0], e1 = s_rp[nrows];
   const bool active = theta_in[r] > -1e307;
   const uint32_t nv = mpad / 4;
-  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+  const uint32_t c0 = threadIdx.x % kEdgeLanes;
+  constexpr uint32_t kGroups = 256 / kEdgeLanes;
+  // the loop bound is uniform across each group, so the shuffles see all lanes
+  for (uint32_t eb = e0; eb < e1; eb += kGroups) {
+    const uint32_t e = eb + threadIdx.x / kEdgeLanes;
     double g = 0.0;
-    if (active) {
+    if (active && e < e1) {
       uint32_t lo = 0, hi = nrows;  // last lr with s_rp[lr] <= e
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -232,10 +243,12 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
       const uint64_t i = I.node_base + row0 + lo;
       const uint64_t j = I.node_base + __ldg(cl + e);
       const T *Pi = P + i * mpad, *Ui = U + i * mpad, *Pj = P + j * mpad, *Uj = U + j * mpad;
-      for (uint32_t c = 0; c < nv; ++c)  // FP64 accumulation of 8-term partial dots
+      for (uint32_t c = c0; c < nv; c += kEdgeLanes)  // FP64 sum of 8-term partial dots
         g += (double)(dot4(Pi + 4 * c, Uj + 4 * c) + dot4(Pj + 4 * c, Ui + 4 * c));
     }
-    grad[I.edge_base + e] = (float)g;
+    for (uint32_t off = kEdgeLanes / 2; off > 0; off >>= 1)
+      g += __shfl_xor_sync(0xffffffffu, g, off, kEdgeLanes);
+    if (c0 == 0 && e < e1) grad[I.edge_base + e] = (float)g;
   }
 }
 
@@ -283,7 +296,19 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
   int rc = ensure_workspace(h, h->ws, m, prec, s);
   if (rc == CB_OK) rc = ensure_workspace(h, h->ws2, m, prec, s);
   if (rc == CB_OK) rc = ensure_backwork(h, m, prec, s);
-  if (rc == CB_OK) rc = lanczos_run(h, h->ws, 0, h->n_inst, m, prec, s);
+  // the basis from 1 is the forward pass's when an ensemble pass at this m
+  // and precision ran last on the handle (same stream order assumed)
+  const bool reuse = rc == CB_OK && h->basis_m == m && h->basis_prec == prec &&
+                     h->basis_gen == h->ws.gen && !std::getenv("CB_NO_REUSE");
+  if (rc == CB_OK && !reuse) {
+    h->basis_m = 0;
+    rc = lanczos_run(h, h->ws, 0, h->n_inst, m, prec, s);
+    if (rc == CB_OK) {
+      h->basis_m = m;
+      h->basis_prec = prec;
+      h->basis_gen = h->ws.gen;
+    }
+  }
   if (rc == CB_OK) rc = lanczos_run(h, h->ws2, 0, h->n_inst, m, prec, s, topk_idx, k);
   if (rc == CB_OK)
     rc = prec == CB_FP64 ? backward_t<double>(h, m, topk_idx, k, grad, log_scale, s)

@@ -95,6 +95,7 @@ struct Workspace {
   uint32_t *hcnt = nullptr;// heavy-row arrival counters
   size_t blob_bytes = 0;
   void *blob = nullptr;    // single allocation backing sc/part/gpart/cnt
+  uint64_t gen = 0;        // allocation generation (process-wide unique)
 };
 
 // Buffers of the adjoint (cb_scores_backward).
@@ -142,6 +143,22 @@ struct cb_graph {
   uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane; 0xff = padding
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
+  // captured ensemble pass (one CUDA graph per m / precision / outputs)
+  struct GraphEntry {
+    uint32_t m;
+    int prec;
+    uint32_t n_out;
+    double *S, *log_scale;
+    uint64_t ws_gen;  // workspace allocation the graph was captured against
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t capture_stream = nullptr;
+  // ws holds the Lanczos basis from 1 of every realisation at this depth and
+  // precision (an ensemble pass or an adjoint ran last); 0 = not valid
+  uint32_t basis_m = 0;
+  int basis_prec = -1;
+  uint64_t basis_gen = 0;
   cb::Workspace ws;   // Krylov basis from 1 (forward)
   cb::Workspace ws2;  // Krylov basis from the top-k indicator (adjoint)
   cb::BackWork bw;    // adjoint buffers

@@ -151,6 +151,28 @@ def test_autograd_function(B):
         assert abs(loss.item() - S[torch.as_tensor(nodes, device="cuda")].sum().item()) <= 1e-12 * abs(loss.item())
 
 
+def test_forward_basis_reuse(B, monkeypatch):
+    """After an ensemble pass at the same m and precision the adjoint reuses
+    its basis from 1; the gradient must be bit-identical to a recomputation,
+    also when a per-realisation call or another depth came in between."""
+    ens = synth.er_ensemble_small()
+    nodes = [int(x) for x in ens.target]
+    with B.GraphSet(ens.graphs) as gs:
+        monkeypatch.setenv("CB_NO_REUSE", "1")
+        ls0, g0 = B.scores_backward(gs, 20, nodes)
+        g0 = g0.cpu().numpy()
+        monkeypatch.delenv("CB_NO_REUSE")
+        for between in (None, "single", "depth"):
+            B.ensemble_scores(gs, 20, 0)
+            if between == "single":
+                B.communicability(gs, 3, 20)
+            elif between == "depth":
+                B.ensemble_scores(gs, 12, 0)
+            ls, g = B.scores_backward(gs, 20, nodes)
+            assert float(ls.item()) == float(ls0.item()), between
+            assert np.array_equal(g.cpu().numpy(), g0), between
+
+
 def test_backward_argument_errors(B):
     g = synth.er(100, 0.05, 1)
     with B.GraphSet([g]) as gs:

@@ -196,6 +196,33 @@ def test_deterministic(B):
     assert np.array_equal(a, b)
 
 
+def test_graph_replay(B, monkeypatch):
+    """Repeated ensemble calls replay a captured CUDA graph: the first call
+    launches directly, the second captures, later ones replay.  All must be
+    bit-identical to direct launches, also after the workspace grows (a
+    per-realisation call at larger m) and for a second output buffer."""
+    ens = synth.er_ensemble_uneven(n_inst=5, n_lo=5_000, n_hi=40_000, config=305)
+    with B.GraphSet(ens.graphs) as gs:
+        monkeypatch.setenv("CB_NO_GRAPH", "1")
+        ref = {m: B.ensemble_scores(gs, m, 0) for m in (12, 30)}
+        ref = {m: (float(l.item()), S.cpu().numpy()) for m, (l, S) in ref.items()}
+        monkeypatch.delenv("CB_NO_GRAPH")
+        n = gs.n_max
+        bufs = [(torch.full((n,), -1.0, dtype=torch.float64, device="cuda"),
+                 torch.zeros(1, dtype=torch.float64, device="cuda")) for _ in range(2)]
+        for rep in range(4):
+            for m in (12, 30):
+                S, ls = bufs[m == 30]
+                S.fill_(float("nan"))
+                B.ensemble_scores(gs, m, 0, out=(S, ls))
+                assert float(ls.item()) == ref[m][0], (rep, m)
+                assert np.array_equal(S.cpu().numpy(), ref[m][1]), (rep, m)
+            if rep == 1:  # regrow the workspace under the captured graphs
+                B.communicability(gs, 0, 60)
+                ref30 = B.ensemble_scores(gs, 30, 0)
+                assert np.array_equal(ref30[1].cpu().numpy(), ref[30][1])
+
+
 def test_max_depth(B):
     g = synth.er(3000, 8.0 / 3000, 9)
     th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 128)
