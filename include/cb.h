@@ -104,8 +104,23 @@ int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
                     const uint32_t *const *row_ptr, const uint32_t *const *col,
                     uint32_t flags, void *stream, cb_graph **out);
 
-/* Release a handle and its device memory (synchronises the device). */
+/* Release a handle and its device memory (synchronises the device).  The
+ * memory goes back to the library's per-device pool (see below), not to the
+ * driver. */
 int cb_graph_free(cb_graph *h);
+
+/*
+ * cb_release_cached_memory -- hand the device memory that the library's
+ * pools keep for reuse back to the driver.  Handles, their workspaces and the
+ * adjoint buffers are allocated from a stream-ordered pool per device that
+ * keeps freed memory, because a cudaFree of multi-GB arrays costs about a
+ * millisecond per GB and a following upload reuses the memory at no cost.
+ * Memory held by live handles is not affected.  Synchronises the current
+ * device.  With the environment variable CB_NO_POOL set (read once, at the
+ * first allocation) the library uses cudaMalloc / cudaFree and this call
+ * does nothing.  The paper has no counterpart; this is a library service.
+ */
+int cb_release_cached_memory(void);
 
 /* Number of realisations / node count of realisation r / largest n. */
 uint32_t cb_graph_num_instances(const cb_graph *h);

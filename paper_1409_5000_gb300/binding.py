@@ -71,6 +71,10 @@ def lib():
         L.cb_version.argtypes = []
         L.cb_scores_backward.restype = i32
         L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
+        L.cb_release_cached_memory.restype = i32
+        L.cb_release_cached_memory.argtypes = []
+        L.cb_topk_noalloc.restype = i32
+        L.cb_topk_noalloc.argtypes = [vp, u32, u32, vp, vp, vp]
         L.cb_profile_enable.restype = i32
         L.cb_profile_enable.argtypes = [i32]
         L.cb_profile_read.restype = i32
@@ -128,6 +132,22 @@ def cb_graph_free(h):
     _check(lib().cb_graph_free(ctypes.c_void_p(h)))
 
 
+def cb_graph_num_instances(h):
+    return int(lib().cb_graph_num_instances(ctypes.c_void_p(h)))
+
+
+def cb_graph_num_nodes(h, r):
+    return int(lib().cb_graph_num_nodes(ctypes.c_void_p(h), r))
+
+
+def cb_graph_max_nodes(h):
+    return int(lib().cb_graph_max_nodes(ctypes.c_void_p(h)))
+
+
+def cb_release_cached_memory():
+    _check(lib().cb_release_cached_memory())
+
+
 def cb_communicability(h, inst, m, prec, y_ptr, log_scale_ptr, report, stream):
     rep = ctypes.c_void_p(ctypes.addressof(report)) if report is not None else None
     _check(lib().cb_communicability(ctypes.c_void_p(h), inst, m, prec, ctypes.c_void_p(y_ptr),
@@ -143,6 +163,11 @@ def cb_ensemble_scores(h, m, prec, n_out, S_ptr, log_scale_ptr, report, stream):
 def cb_topk(S_ptr, n, k, idx_ptr, val_ptr, stream):
     _check(lib().cb_topk(ctypes.c_void_p(S_ptr), n, k, ctypes.c_void_p(idx_ptr),
                          ctypes.c_void_p(val_ptr), ctypes.c_void_p(stream)))
+
+
+def cb_topk_noalloc(S_ptr, n, k, idx_ptr, val_ptr, stream):
+    _check(lib().cb_topk_noalloc(ctypes.c_void_p(S_ptr), n, k, ctypes.c_void_p(idx_ptr),
+                                 ctypes.c_void_p(val_ptr), ctypes.c_void_p(stream)))
 
 
 CB_K_SPMV, CB_K_FINALIZE, CB_K_TRIDIAG, CB_K_COMBINE, CB_K_TOPK, CB_K_INIT, CB_K_BACKWARD = range(7)

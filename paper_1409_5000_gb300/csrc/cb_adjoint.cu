@@ -20,8 +20,8 @@
 // 24 complex tridiagonal solves and 12 rank-1 terms, no eigendecomposition.
 //
 // Then P = V_w M and U = V_1 are written node-major (m contiguous values per
-// node) and every CSR entry (i, j) gets g = P_i . U_j + P_j . U_i: FP32 (or
-// FP64) values, FP64 accumulation.  Realisations share one shift theta* =
+// node) and every CSR entry (i, j) gets g = P_i . U_j + P_j . U_i, computed
+// in the basis precision (FP32 or FP64).  Realisations share one shift theta* =
 // max_r theta_r; dL/da_e = exp(theta*) * grad[e].
 #include <cstdlib>
 
@@ -32,9 +32,9 @@ namespace cb {
 constexpr uint32_t kMaxAdjM = 64;  // adjoint depth limit (shared-memory staging)
 
 void free_backwork(BackWork &B) {
-  cudaFree(B.P);
-  cudaFree(B.U);
-  cudaFree(B.blob);
+  dev_free(B.P);
+  dev_free(B.U);
+  dev_free(B.blob);
   B = BackWork{};
 }
 
@@ -45,11 +45,11 @@ static int ensure_backwork(cb_graph *h, uint32_t m, int prec, cudaStream_t s) {
   const uint32_t mpad = (m + 3) / 4 * 4;
   const size_t esz = prec == CB_FP64 ? sizeof(double) : sizeof(float);
   const size_t vb = h->total_nodes_padded * mpad * esz + 16;
-  cudaError_t e = cudaMalloc(&B.P, vb);
-  if (e == cudaSuccess) e = cudaMalloc(&B.U, vb);
+  cudaError_t e = dev_alloc(&B.P, vb);
+  if (e == cudaSuccess) e = dev_alloc(&B.U, vb);
   const uint32_t N = h->n_inst;
   const size_t bytes = ((size_t)N * m * m + N) * sizeof(double) + (size_t)N * sizeof(uint32_t) + 64;
-  if (e == cudaSuccess) e = cudaMalloc(&B.blob, bytes);
+  if (e == cudaSuccess) e = dev_alloc(&B.blob, bytes);
   if (e != cudaSuccess) {
     free_backwork(B);
     return cuda_error(e, "adjoint workspace");
@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(32) bw_tridiag_kernel(Scalars s1, Scalars sw,
 // Node-major P = exp(theta_r - theta*) V_w K_r and U = V_1 (scales applied).
 // One CTA per finalize tile (kFinRows nodes of one realisation), 4 warps;
 // each warp stages 32 nodes' basis values in shared memory and writes the
-// node-major rows with lanes over the row index (coalesced).
+// node-major rows with lanes over the row index (coalesced).  All per-node
+// arithmetic runs in T: the FP64 scalars are converted once per CTA (FP64
+// instructions are scarce on GB300).
 template <typename T>
 __global__ void __launch_bounds__(128) bw_node_kernel(const T *V1, const T *Vw, uint64_t vs,
                                                       Scalars s1, Scalars sw,
@@ -140,36 +142,40 @@ __global__ void __launch_bounds__(128) bw_node_kernel(const T *V1, const T *Vw, 
   T *sK = reinterpret_cast<T *>(s_raw);              // kdim * kdim
   T *sV = sK + kdim * kdim;                          // 4 warps x kdim x 32 (V_w values)
   T *sW = sV + 4 * kdim * 32;                        // 4 warps x kdim x 32 (V_1 values)
-  __shared__ double s_tmax;
+  __shared__ T s_sc1[kMaxAdjM], s_scw[kMaxAdjM];
+  __shared__ double s_wmax[4];
   const uint32_t t = blockIdx.x;
   const uint32_t r = fin_inst[t];
   const InstDesc I = inst[r];
-  if (threadIdx.x == 0) {
-    double tm = -1e308;
-    for (uint32_t q = 0; q < n_inst; ++q) tm = fmax(tm, theta_in[q]);
-    s_tmax = tm;
-    if (t == 0) *log_scale = tm > -1e307 ? tm : 0.0;
-  }
-  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double tm = -1e308;
+  for (uint32_t q = threadIdx.x; q < n_inst; q += blockDim.x) tm = fmax(tm, theta_in[q]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+  if (lane == 0) s_wmax[warp] = tm;
   const double th = theta_in[r];
   const bool active = th > -1e307;
   const int M1 = active ? (int)s1.meff[r] : 0, Mw = active ? (int)sw.meff[r] : 0;
-  const double f = active ? exp(th - s_tmax) : 0.0;
+  for (int q = threadIdx.x; q < M1; q += blockDim.x) s_sc1[q] = (T)s1.scale[r * s1.ms + q];
+  for (int q = threadIdx.x; q < Mw; q += blockDim.x) s_scw[q] = (T)sw.scale[r * sw.ms + q];
+  __syncthreads();
+  const double tmax = fmax(fmax(s_wmax[0], s_wmax[1]), fmax(s_wmax[2], s_wmax[3]));
+  if (t == 0 && threadIdx.x == 0) *log_scale = tmax > -1e307 ? tmax : 0.0;
+  const double f = active ? exp(th - tmax) : 0.0;
   for (uint32_t q = threadIdx.x; q < (uint32_t)(Mw * M1); q += blockDim.x) {
     const uint32_t a = q / M1, b = q % M1;
     sK[a * kdim + b] = (T)(f * K[(size_t)r * kdim * kdim + a * kdim + b]);
   }
   __syncthreads();
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T *myV = sV + warp * kdim * 32, *myW = sW + warp * kdim * 32;
   const uint32_t i0 = (t - I.fin_base) * kFinRows, i1 = min(i0 + kFinRows, I.n);
   for (uint32_t base = i0 + warp * 32; base < i1; base += 4 * 32) {
     const uint32_t i = base + lane;
     const bool valid = i < i1;
     for (int a = 0; a < Mw; ++a)
-      myV[a * 32 + lane] = valid ? (T)(sw.scale[r * sw.ms + a]) * Vw[(uint64_t)a * vs + I.node_base + i] : T(0);
+      myV[a * 32 + lane] = valid ? s_scw[a] * Vw[(uint64_t)a * vs + I.node_base + i] : T(0);
     for (int b = 0; b < M1; ++b)
-      myW[b * 32 + lane] = valid ? (T)(s1.scale[r * s1.ms + b]) * V1[(uint64_t)b * vs + I.node_base + i] : T(0);
+      myW[b * 32 + lane] = valid ? s_sc1[b] * V1[(uint64_t)b * vs + I.node_base + i] : T(0);
     __syncwarp();
     const uint32_t nn = min(32u, i1 - base);
     for (uint32_t q = 0; q < nn; ++q) {
@@ -204,8 +210,9 @@ __device__ __forceinline__ double dot4(const double *a, const double *b) {
 // g_e = P_i . U_j + P_j . U_i for every CSR entry e = (i, j) of one SpMV tile.
 // A group of kEdgeLanes lanes shares an edge: lane c takes the 4-value chunks
 // c, c + kEdgeLanes, ... of the four node-major rows, so each row is read as
-// whole 128-byte lines; the FP64 partials are summed across the group with
-// shuffles.
+// whole 128-byte lines; the partials are summed across the group with a
+// shuffle tree.  Arithmetic in T (FP32 in CB_FP32 mode): FP64 instructions
+// are scarce on GB300 and would bound this kernel.
 constexpr uint32_t kEdgeLanes = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, uint32_t mpad,
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
   // the loop bound is uniform across each group, so the shuffles see all lanes
   for (uint32_t eb = e0; eb < e1; eb += kGroups) {
     const uint32_t e = eb + threadIdx.x / kEdgeLanes;
-    double g = 0.0;
+    T g = T(0);
     if (active && e < e1) {
       uint32_t lo = 0, hi = nrows;  // last lr with s_rp[lr] <= e
       while (hi - lo > 1) {
@@ -243,8 +250,8 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
       const uint64_t i = I.node_base + row0 + lo;
       const uint64_t j = I.node_base + __ldg(cl + e);
       const T *Pi = P + i * mpad, *Ui = U + i * mpad, *Pj = P + j * mpad, *Uj = U + j * mpad;
-      for (uint32_t c = c0; c < nv; c += kEdgeLanes)  // FP64 sum of 8-term partial dots
-        g += (double)(dot4(Pi + 4 * c, Uj + 4 * c) + dot4(Pj + 4 * c, Ui + 4 * c));
+      for (uint32_t c = c0; c < nv; c += kEdgeLanes)
+        g += dot4(Pi + 4 * c, Uj + 4 * c) + dot4(Pj + 4 * c, Ui + 4 * c);
     }
     for (uint32_t off = kEdgeLanes / 2; off > 0; off >>= 1)
       g += __shfl_xor_sync(0xffffffffu, g, off, kEdgeLanes);

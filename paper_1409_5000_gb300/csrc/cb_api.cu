@@ -117,26 +117,79 @@ static int pick_lanes(double avg_deg) {
   return 32;
 }
 
+static std::mutex g_pool_mu;
+static std::vector<cudaMemPool_t> g_pools;  // per device, created on first use
+
+static bool use_pool() {
+  static const bool on = std::getenv("CB_NO_POOL") == nullptr;
+  return on;
+}
+
+static cudaError_t device_pool(cudaMemPool_t *pool) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;  // never hand memory back on synchronisation
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = p;
+  }
+  *pool = g_pools[dev];
+  return cudaSuccess;
+}
+
+// Pool allocations are ordered on the legacy default stream and completed
+// before returning, so the memory is usable from any stream.
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (!use_pool()) return cudaMalloc(p, bytes);
+  cudaMemPool_t pool;
+  cudaError_t e = device_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) *p = nullptr;
+  return e;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  if (!use_pool()) {
+    cudaFree(p);
+    return;
+  }
+  cudaDeviceSynchronize();  // no kernel may still use it
+  cudaFreeAsync(p, 0);
+}
+
 template <typename P>
 static cudaError_t dalloc(P **p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P) + 16);
+  return dev_alloc_n(p, count);
 }
 
 void free_workspace(Workspace &W) {
-  if (W.V) cudaFree(W.V);
-  if (W.blob) cudaFree(W.blob);
+  dev_free(W.V);
+  dev_free(W.blob);
   W = Workspace{};
 }
 
 static void free_graph_arrays(cb_graph *h) {
-  cudaFree(h->col);
-  cudaFree(h->row_ptr);
-  cudaFree(h->d_inst);
-  cudaFree(h->d_tile_inst);
-  cudaFree(h->d_tile_rows);
-  cudaFree(h->d_heavy);
-  cudaFree(h->d_chunk_heavy);
-  cudaFree(h->d_fin_inst);
+  dev_free(h->col);
+  dev_free(h->row_ptr);
+  dev_free(h->d_inst);
+  dev_free(h->d_tile_inst);
+  dev_free(h->d_tile_rows);
+  dev_free(h->d_heavy);
+  dev_free(h->d_chunk_heavy);
+  dev_free(h->d_fin_inst);
   h->col = nullptr;
   h->row_ptr = nullptr;
   h->d_inst = nullptr;
@@ -154,7 +207,7 @@ int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream
   const size_t esz = prec == CB_FP64 ? sizeof(double) : sizeof(float);
   W.vec_stride = h->total_nodes_padded;
   const size_t vbytes = (size_t)(m + 1) * W.vec_stride * esz;
-  cudaError_t e = cudaMalloc(&W.V, vbytes ? vbytes : 16);
+  cudaError_t e = dev_alloc(&W.V, vbytes ? vbytes : 16);
   if (e != cudaSuccess) {
     W.V = nullptr;
     return cuda_error(e, "workspace: Krylov basis");
@@ -168,7 +221,7 @@ int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream
   const size_t nd = 4 * (size_t)N * ms + N + nslots + ngroups + nchunks;
   const size_t nw = 2 * (size_t)N + ngroups + N + nheavy;
   const size_t bytes = nd * sizeof(double) + nw * sizeof(uint32_t) + 256;
-  e = cudaMalloc(&W.blob, bytes);
+  e = dev_alloc(&W.blob, bytes);
   if (e != cudaSuccess) {
     W.blob = nullptr;
     free_workspace(W);
@@ -243,6 +296,17 @@ static int validate_host(uint32_t n, uint64_t nnz, const uint32_t *rp, const uin
 using namespace cb;
 
 CB_API const char *cb_last_error(void) { return g_err.c_str(); }
+
+CB_API int cb_release_cached_memory(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (cudaMemPool_t p : g_pools)
+    if (p) {
+      const cudaError_t x = cudaMemPoolTrimTo(p, 0);
+      if (e == cudaSuccess) e = x;
+    }
+  return cuda_error(e, "cb_release_cached_memory");
+}
 
 CB_API int cb_profile_enable(int on) {
   prof_clear();

@@ -18,7 +18,8 @@
 //     the loads are coalesced and need no per-element range checks;
 //   * each element stores the local column (u16, col & (kBCol-1)) and the row
 //     slot of the owning lane (u8, 0..kBRowsPerThread-1); padding elements
-//     carry slot 0xff and are skipped.
+//     carry column kBPadCol (a zero word after the staged block) and slot 0,
+//     so they add +0.
 // Rows with more than kBLongDeg entries stay out of the streams; the SpMV
 // sums them from the CSR with whole-CTA global gathers.  Built on the device
 // from the CSR (one count pass, a host prefix over segment lengths, one
@@ -92,43 +93,63 @@ __global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
       }
     }
   }
+  // Elements are collected 4 at a time in registers (the lane's stripe) and
+  // written with one 8-byte and one 4-byte store; unfilled positions of the
+  // last stripe keep the padding values.
+  constexpr uint32_t kPad2 = kBPadCol | (kBPadCol << 16);
   for (uint32_t b = 0; b < I.nb; ++b) {
-    const uint64_t base = bwstart[(bseg_base[t] + b) * 32 + warp] + 4 * lane;
+    const uint64_t start = bwstart[(bseg_base[t] + b) * 32 + warp];
+    uint2 *dc = reinterpret_cast<uint2 *>(bcol + start) + lane;  // stripe s at dc[32 s]
+    uint32_t *dk = reinterpret_cast<uint32_t *>(bslot + start) + lane;
     uint32_t q = 0;
+    uint2 cv = make_uint2(kPad2, kPad2);
+    uint32_t sv = 0;
 #pragma unroll
     for (int k = 0; k < kBRowsPerThread; ++k) {
       while (cur[k] < end[k]) {
-        const uint32_t c = cl[cur[k]];
+        const uint32_t c = __ldg(cl + cur[k]);
         const uint32_t cb = c >> kBColBits;
         if (cb > b) break;  // the row's next edges belong to a later block
         if (cb == b) {
-          const uint64_t pos = base + 128ull * (q >> 2) + (q & 3);
-          bcol[pos] = (uint16_t)(c & (kBCol - 1));
-          bslot[pos] = (uint8_t)k;
+          const uint32_t p = q & 3, sh = 16 * (p & 1);
+          const uint32_t v = c & (kBCol - 1);
+          if (p < 2) cv.x = (cv.x & ~(0xffffu << sh)) | (v << sh);
+          else cv.y = (cv.y & ~(0xffffu << sh)) | (v << sh);
+          sv |= (uint32_t)k << (8 * p);
+          if (p == 3) {
+            dc[32 * (q >> 2)] = cv;
+            dk[32 * (q >> 2)] = sv;
+            cv = make_uint2(kPad2, kPad2);
+            sv = 0;
+          }
           ++q;
         }
         ++cur[k];
       }
+    }
+    if (q & 3) {
+      dc[32 * (q >> 2)] = cv;
+      dk[32 * (q >> 2)] = sv;
     }
   }
 }
 
 template <typename P>
 cudaError_t dalloc(P **p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P) + 64);
+  return dev_alloc_n(p, count);
 }
 
 }  // namespace
 
 void free_blocked(cb_graph *h) {
-  cudaFree(h->d_btile_inst);
-  cudaFree(h->d_bseg_base);
-  cudaFree(h->d_bwstart);
-  cudaFree(h->d_bwlen);
-  cudaFree(h->d_bcol);
-  cudaFree(h->d_bslot);
-  cudaFree(h->d_blong_ptr);
-  cudaFree(h->d_blong_rows);
+  dev_free(h->d_btile_inst);
+  dev_free(h->d_bseg_base);
+  dev_free(h->d_bwstart);
+  dev_free(h->d_bwlen);
+  dev_free(h->d_bcol);
+  dev_free(h->d_bslot);
+  dev_free(h->d_blong_ptr);
+  dev_free(h->d_blong_rows);
   h->d_btile_inst = nullptr;
   h->d_bseg_base = h->d_bwstart = nullptr;
   h->d_bwlen = nullptr;
@@ -222,7 +243,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     chk(cudaMemcpyAsync(len.data(), h->d_bwlen, nw * 4, cudaMemcpyDeviceToHost, s));
     chk(cudaMemcpyAsync(&unsorted, d_unsorted, 4, cudaMemcpyDeviceToHost, s));
     chk(cudaStreamSynchronize(s));
-    cudaFree(d_unsorted);
+    dev_free(d_unsorted);
     if (e == cudaSuccess && unsorted) {
       free_blocked(h);
       return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
@@ -233,11 +254,13 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       start[q] = tot;
       tot += 32ull * len[q];
     }
-    chk(dalloc(&h->d_bcol, tot + 16));
-    chk(dalloc(&h->d_bslot, tot + 16));
+    const uint64_t alloc = tot + 16;
+    chk(dalloc(&h->d_bcol, alloc));
+    chk(dalloc(&h->d_bslot, alloc));
     if (e == cudaSuccess) {
-      chk(cudaMemsetAsync(h->d_bcol, 0, (tot + 16) * 2, s));
-      chk(cudaMemsetAsync(h->d_bslot, 0xff, tot + 16, s));  // padding: no row slot
+      static_assert((kBPadCol >> 8) == (kBPadCol & 0xff), "padding column must be a repeated byte");
+      chk(cudaMemsetAsync(h->d_bcol, (int)(kBPadCol & 0xff), alloc * 2, s));  // padding: zero word
+      chk(cudaMemsetAsync(h->d_bslot, 0, alloc, s));                          // into slot 0
       chk(cudaMemcpyAsync(h->d_bwstart, start.data(), nw * 8, cudaMemcpyHostToDevice, s));
       bfill_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base,
                                              h->d_bwstart, h->row_ptr, h->col, h->d_bcol,

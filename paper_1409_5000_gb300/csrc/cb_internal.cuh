@@ -36,6 +36,11 @@ constexpr int kBRowsPerThread = 16;
 constexpr int kBTileRows = kBThreads * kBRowsPerThread;  // 16384
 constexpr uint32_t kBColBits = 14;
 constexpr uint32_t kBCol = 1u << kBColBits;              // 16384 floats = 64 KB per buffer
+// Padding elements of the edge streams read column kBPadCol, a zero word placed
+// after each staged block, into row slot 0: they add +0 and need no test.
+// (0x4040 is a repeated byte, so the padding is a plain byte memset.)
+constexpr uint32_t kBPadCol = 0x4040;
+constexpr uint32_t kBBuf = kBPadCol + 4;                 // floats per staging buffer (16-byte multiple)
 constexpr uint32_t kBMaxBlocks = 32;                     // blocked when n <= 32 * kBCol
 constexpr uint32_t kBLongDeg = 512;                      // longer rows: whole-CTA global gathers
 
@@ -139,8 +144,8 @@ struct cb_graph {
   uint64_t *d_bseg_base = nullptr;       // first (tile, column block) segment of each tile
   uint64_t *d_bwstart = nullptr;         // per (segment, warp): first element of its region
   uint32_t *d_bwlen = nullptr;           // per (segment, warp): longest lane stream
-  uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per element
-  uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane; 0xff = padding
+  uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per element (padding: kBPadCol)
+  uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane (padding: 0)
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
   // captured ensemble pass (one CUDA graph per m / precision / outputs)
@@ -169,6 +174,18 @@ namespace cb {
 void parallel_for(uint32_t n, const std::function<void(uint32_t)> &fn);
 
 // error plumbing (cb_api.cu)
+// Device memory of handles and workspaces.  By default it comes from a
+// library-owned stream-ordered pool per device that keeps freed memory for
+// the next upload (cudaFree of multi-GB arrays costs ~1 ms per GB);
+// cb_release_cached_memory trims it, CB_NO_POOL selects plain cudaMalloc.
+// dev_free synchronises the device first, like cudaFree.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+template <typename P>
+inline cudaError_t dev_alloc_n(P **p, size_t count) {
+  return dev_alloc(reinterpret_cast<void **>(p), count * sizeof(P) + 64);
+}
+
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);
 

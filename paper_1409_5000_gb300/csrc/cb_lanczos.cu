@@ -347,14 +347,15 @@ __device__ __forceinline__ void stage_block(float *dst, const float *x, uint32_t
   for (uint32_t q = 4 * n4 + threadIdx.x; q < len; q += kBThreads) cp_async4(dst + q, x + lo + q);
 }
 
-// two column blocks of W_j, then kBRowsPerThread accumulator slots per thread
-constexpr size_t kBSmemBytes = (2 * kBCol + kBRowsPerThread * kBThreads) * sizeof(float);
+// two column blocks of W_j (each followed by its zero word), then
+// kBRowsPerThread accumulator slots per thread
+constexpr size_t kBSmemBytes = (2 * kBBuf + kBRowsPerThread * kBThreads) * sizeof(float);
 
 __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j,
                                                              uint32_t btile_off) {
   extern __shared__ float4 s_dyn4[];
   float *xs = reinterpret_cast<float *>(s_dyn4);  // two column blocks of W_j
-  float *sacc = xs + 2 * kBCol;                   // [slot][thread] row sums
+  float *sacc = xs + 2 * kBBuf;                   // [slot][thread] row sums
   __shared__ uint32_t s_long[kBTileRows / 32];    // bitmap of long rows
   __shared__ double s_red[32];
   __shared__ float s_rowsum[32];
@@ -375,6 +376,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
 
   for (uint32_t q = tid; q < kBRowsPerThread * kBThreads; q += kBThreads) sacc[q] = 0.f;
   for (uint32_t q = tid; q < kBTileRows / 32; q += kBThreads) s_long[q] = 0u;
+  if (tid < 2) xs[tid * kBBuf + kBPadCol] = 0.f;  // the padding elements read these
   __syncthreads();
   const uint32_t lp0 = a.blong_ptr[t], lp1 = a.blong_ptr[t + 1];
   for (uint32_t q = lp0 + tid; q < lp1; q += kBThreads) {
@@ -409,14 +411,14 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
       const uint64_t nseg = sbase + b + 1;
       my1 = a.bwstart[nseg * 32 + warp] + 4 * lane;
       ns1 = a.bwlen[nseg * 32 + warp] >> 2;
-      stage_block(xs + ((b + 1) & 1) * kBCol, x, I.n, b + 1);
+      stage_block(xs + ((b + 1) & 1) * kBBuf, x, I.n, b + 1);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float *cur = xs + (b & 1) * kBCol;
+    const float *cur = xs + (b & 1) * kBBuf;
     float *mine = sacc + tid;
     const uint32_t nr = (ns + 3) >> 2;
     const uint32_t iters = nr ? nr : 1u;  // one pass even when empty: prefetch the next block
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
             for (int e = 0; e < 4; ++e) {
               const uint32_t col = ((e < 2 ? cvA[u].x : cvA[u].y) >> (16 * (e & 1))) & 0xffffu;
               const uint32_t k = (svA[u] >> (8 * e)) & 0xffu;
-              if (k < (uint32_t)kBRowsPerThread) mine[k * kBThreads] += cur[col];  // else padding
+              mine[k * kBThreads] += cur[col];  // padding: cur[kBPadCol] = 0 into slot 0
             }
           }
       }

@@ -27,6 +27,12 @@ def test_every_declared_symbol_is_exported(libcb):
     assert not missing, missing
 
 
+def test_binding_wraps_every_declared_function():
+    """The Python binding mirrors the C ABI name for name."""
+    missing = [n for n in binding.declared_functions() if not callable(getattr(binding, n, None))]
+    assert not missing, missing
+
+
 def test_version_and_error_string(libcb):
     libcb.cb_version.restype = ctypes.c_uint32
     assert libcb.cb_version() >> 16 == 1

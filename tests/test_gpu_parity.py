@@ -223,6 +223,25 @@ def test_graph_replay(B, monkeypatch):
                 assert np.array_equal(ref30[1].cpu().numpy(), ref[30][1])
 
 
+def test_memory_pool_reuse_and_release(B):
+    """Freed handles leave their memory in the library's pool; a second upload
+    reuses it and computes the same scores; cb_release_cached_memory hands
+    it back to the driver."""
+    g = synth.er(200_000, 20.0 / 200_000, 5)
+    with B.GraphSet([g]) as gs:
+        ref = B.ensemble_scores(gs, 10, 0)[1].cpu().numpy()
+    torch.cuda.synchronize()
+    held, _ = torch.cuda.mem_get_info()
+    with B.GraphSet([g]) as gs:
+        again = B.ensemble_scores(gs, 10, 0)[1].cpu().numpy()
+    assert np.array_equal(ref, again)
+    torch.cuda.synchronize()
+    B.cb_release_cached_memory()
+    released, _ = torch.cuda.mem_get_info()
+    # the handle held ~16 MB of columns, ~9 MB of basis, ~12 MB of streams
+    assert released >= held + (20 << 20), (held, released)
+
+
 def test_max_depth(B):
     g = synth.er(3000, 8.0 / 3000, 9)
     th_o, y_o, _ = oc.krylov_expv(g.n, g.row_ptr, g.col, 128)
