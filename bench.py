@@ -377,8 +377,12 @@ def main():
         pgs = [_PG(g, pg) for g, pg in zip(ens.graphs, pinned)]
         n_e2e = max(1, min(args.steps, 3))
 
+        up_ms = []
+
         def e2e_step():
+            u0 = time.perf_counter()
             with B.GraphSet(pgs) as g2:
+                up_ms.append(1e3 * (time.perf_counter() - u0))  # the upload synchronises
                 S2 = torch.empty(g2.n_max, dtype=torch.float64, device=dev)
                 l2 = torch.empty(1, dtype=torch.float64, device=dev)
                 B.ensemble_scores(g2, m, B.CB_FP32, out=(S2, l2))
@@ -389,12 +393,14 @@ def main():
                 torch.cuda.synchronize()
 
         e2e_step()
+        up_ms.clear()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             e2e_step()
         e2e_ms = 1e3 * (time.perf_counter() - t0) / n_e2e
         e2e = {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": n_e2e,
+               "upload_ms": sum(up_ms) / len(up_ms),
                "api": "cb_graph_upload(pinned host) + cb_ensemble_scores + cb_topk + D2H + cb_graph_free"}
 
     cpu = None

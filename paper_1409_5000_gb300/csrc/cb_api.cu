@@ -340,6 +340,46 @@ CB_API uint32_t cb_graph_num_nodes(const cb_graph *h, uint32_t r) {
 }
 CB_API uint32_t cb_graph_max_nodes(const cb_graph *h) { return h ? h->n_max : 0; }
 
+// The copy stream and the per-group events of one upload.  finish() waits
+// for the copies and releases both.
+namespace {
+constexpr uint64_t kCopyGroups = 8;
+struct UploadCopies {
+  cudaStream_t stream = nullptr;
+  std::vector<CopyGroup> groups;
+  cudaError_t start(cudaStream_t caller) {
+    cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      stream = nullptr;
+      return e;
+    }
+    // inputs may come from work still queued on the caller's stream
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
+    cudaEventDestroy(ev);
+    return e;
+  }
+  cudaError_t mark(uint32_t r_end) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    groups.push_back({r_end, ev});
+    return cudaEventRecord(ev, stream);
+  }
+  void finish() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (const CopyGroup &g : groups) cudaEventDestroy(g.ev);
+    groups.clear();
+    if (stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+  ~UploadCopies() { finish(); }
+};
+}  // namespace
+
 CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
                            const uint32_t *const *row_ptr, const uint32_t *const *col,
                            uint32_t flags, void *stream, cb_graph **out) {
@@ -410,6 +450,36 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   if (node_off >= (1ull << 40) || tile_off >= 0x7fffffffu) {
     delete h;
     return set_error(CB_ERR_ARG, "cb_graph_upload: input too large");
+  }
+  // The bulk copies go first, on a stream of their own and in groups of
+  // realisations: the host builds the launch tables, and the count kernel of
+  // the blocked format runs on a group, while later groups are in flight.
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(dalloc(&h->col, edge_off + 4));
+  chk(dalloc(&h->row_ptr, rp_off));
+  UploadCopies cp;
+  chk(cp.start(s));
+  if (e == cudaSuccess) {
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    chk(cudaMemsetAsync(h->col + edge_off, 0, 16, cp.stream));
+    const uint64_t per_group = edge_off / kCopyGroups + 1;
+    uint64_t acc = 0;
+    for (uint32_t r = 0; r < n_inst && e == cudaSuccess; ++r) {
+      const InstDesc &I = h->inst[r];
+      if (nnz[r]) chk(cudaMemcpyAsync(h->col + I.edge_base, col[r], nnz[r] * 4, kind, cp.stream));
+      chk(cudaMemcpyAsync(h->row_ptr + I.rp_base, row_ptr[r], ((size_t)I.n + 1) * 4, kind, cp.stream));
+      acc += nnz[r];
+      if (r + 1 == n_inst || acc >= per_group * (cp.groups.size() + 1)) chk(cp.mark(r + 1));
+    }
+  }
+  if (e != cudaSuccess) {
+    cp.finish();
+    free_graph_arrays(h);
+    delete h;
+    return cuda_error(e, "cb_graph_upload: allocate / copy");
   }
   // heavy rows (degree > kHeavyDeg), in realisation and row order; the row
   // scans run in parallel over realisations
@@ -499,12 +569,6 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   for (uint32_t q = 0; q < h->total_heavy; ++q)
     for (uint32_t c = 0; c < h->heavy[q].n_chunks; ++c) chunk_heavy[h->heavy[q].chunk_base + c] = q;
 
-  cudaError_t e = cudaSuccess;
-  auto chk = [&](cudaError_t x) {
-    if (e == cudaSuccess) e = x;
-  };
-  chk(dalloc(&h->col, edge_off + 4));
-  chk(dalloc(&h->row_ptr, rp_off));
   chk(dalloc(&h->d_inst, n_inst));
   chk(dalloc(&h->d_tile_inst, tile_inst.size()));
   chk(dalloc(&h->d_tile_rows, tile_rows.size()));
@@ -512,15 +576,10 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   chk(dalloc(&h->d_heavy, std::max<size_t>(h->heavy.size(), 1)));
   chk(dalloc(&h->d_chunk_heavy, chunk_heavy.size()));
   if (e != cudaSuccess) {
+    cp.finish();
     free_graph_arrays(h);
     delete h;
     return cuda_error(e, "cb_graph_upload: allocate");
-  }
-  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (uint32_t r = 0; r < n_inst && e == cudaSuccess; ++r) {
-    const InstDesc &I = h->inst[r];
-    if (nnz[r]) chk(cudaMemcpyAsync(h->col + I.edge_base, col[r], nnz[r] * 4, kind, s));
-    chk(cudaMemcpyAsync(h->row_ptr + I.rp_base, row_ptr[r], ((size_t)I.n + 1) * 4, kind, s));
   }
   chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), n_inst * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(h->d_tile_inst, tile_inst.data(), tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
@@ -532,17 +591,23 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
                         cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(h->d_chunk_heavy, chunk_heavy.data(), chunk_heavy.size() * 4,
                       cudaMemcpyHostToDevice, s));
-  chk(cudaMemsetAsync(h->col + edge_off, 0, 16, s));
-  chk(cudaStreamSynchronize(s));
   if (e != cudaSuccess) {
+    cp.finish();
     free_graph_arrays(h);
     delete h;
     return cuda_error(e, "cb_graph_upload: copy");
   }
   std::vector<const uint32_t *> rpv(n_inst);
   for (uint32_t r = 0; r < n_inst; ++r) rpv[r] = rp_of(r);
-  int rc = build_blocked(h, rpv, s);
+  int rc = build_blocked(h, rpv, s, cp.groups);
+  if (rc == CB_OK) {  // every copy has landed before the handle is returned
+    for (const CopyGroup &g : cp.groups) chk(cudaStreamWaitEvent(s, g.ev, 0));
+    chk(cudaStreamSynchronize(s));
+    if (e != cudaSuccess) rc = cuda_error(e, "cb_graph_upload: copy");
+  }
+  cp.finish();
   if (rc != CB_OK) {
+    free_blocked(h);
     free_graph_arrays(h);
     delete h;
     return rc;

@@ -33,105 +33,133 @@ namespace cb {
 
 namespace {
 
-__global__ void __launch_bounds__(kBThreads) bcount_kernel(const InstDesc *inst,
-                                                           const uint32_t *btile_inst,
-                                                           const uint64_t *bseg_base,
-                                                           const uint32_t *row_ptr,
-                                                           const uint32_t *col, uint32_t *bwlen,
-                                                           uint32_t *unsorted) {
+constexpr uint32_t kFillThreads = 128;  // lanes of a tile per count / fill CTA
+
+// Per (segment, warp) stream length: the largest per-lane element count of the
+// warp in that column block, rounded up to a multiple of 4.  CTAs of
+// kFillThreads lanes of a tile; per-(block, lane) counters in shared memory.
+__global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *inst,
+                                                              const uint32_t *btile_inst,
+                                                              const uint64_t *bseg_base,
+                                                              const uint32_t *row_ptr,
+                                                              const uint32_t *col, uint32_t *bwlen,
+                                                              uint32_t *unsorted, uint32_t t_off) {
+  __shared__ uint16_t s_cnt[kBMaxBlocks][kFillThreads];
+  const uint32_t t = t_off + blockIdx.x;
+  const InstDesc I = inst[btile_inst[t]];
+  const uint32_t *rp = row_ptr + I.rp_base;
+  const uint32_t *cl = col + I.edge_base;
+  const uint32_t row0 = (t - I.btile_base) * kBTileRows;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t v = blockIdx.y * kFillThreads + tid;
+  const uint32_t nb = I.nb;
+  for (uint32_t b = 0; b < nb; ++b) s_cnt[b][tid] = 0;
+  bool bad = false;
+  for (int k = 0; k < kBRowsPerThread; ++k) {
+    const uint32_t row = row0 + v + kBThreads * k;
+    if (row >= I.n) break;
+    const uint32_t e0 = rp[row], e1 = rp[row + 1];
+    if (e1 - e0 > kBLongDeg) continue;
+    uint32_t prev = 0;
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t c = __ldg(cl + e);
+      const uint32_t b = c >> kBColBits;
+      if (b < nb) s_cnt[b][tid]++;  // columns >= n are invalid input: skipped
+      bad |= e > e0 && c < prev;    // the format needs sorted rows
+      prev = c;
+    }
+  }
+  if (bad) *unsorted = 1u;
+  for (uint32_t b = 0; b < nb; ++b) {
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, (uint32_t)s_cnt[b][tid]);
+    if ((tid & 31) == 0)
+      bwlen[(bseg_base[t] + b) * 32 + (v >> 5)] = (wmax + 3) & ~3u;
+  }
+}
+
+// Fill the streams in one pass over the CSR.  A CTA takes kFillThreads of the
+// tile's kBThreads lanes ("virtual threads" v); each walks its rows in slot
+// order and each row's columns once, appending every element to the stream
+// of its column block.  Per (block, lane), the 4 elements of the open stripe
+// wait in shared memory and go out as one 8-byte and one 4-byte store when
+// the stripe is full; partial stripes are written at the end (their unfilled
+// positions keep the padding values).  The element order within a stream is
+// the lane's rows in slot order, each row's columns in input order.
+__global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *inst,
+                                                             const uint32_t *btile_inst,
+                                                             const uint64_t *bseg_base,
+                                                             const uint64_t *bwstart,
+                                                             const uint32_t *row_ptr,
+                                                             const uint32_t *col, uint16_t *bcol,
+                                                             uint8_t *bslot, uint32_t nbmax) {
+  // dynamic shared memory, nbmax column blocks:
+  //   start[nbmax][4] u64, col[nbmax][4][128] u16, q[nbmax][128] u16, slot[nbmax][4][128] u8
+  extern __shared__ uint64_t s_dyn[];
+  uint64_t *s_start = s_dyn;
+  uint16_t *s_col = reinterpret_cast<uint16_t *>(s_start + nbmax * (kFillThreads / 32));
+  uint16_t *s_q = s_col + nbmax * 4 * kFillThreads;
+  uint8_t *s_slot = reinterpret_cast<uint8_t *>(s_q + nbmax * kFillThreads);
   const uint32_t t = blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
   const uint32_t *cl = col + I.edge_base;
   const uint32_t row0 = (t - I.btile_base) * kBTileRows;
-  uint32_t len[kBMaxBlocks];
-  for (uint32_t b = 0; b < kBMaxBlocks; ++b) len[b] = 0;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t v = blockIdx.y * kFillThreads + tid;  // lane index within the tile
+  const uint32_t lane = v & 31, wl = tid >> 5;          // wl: warp within this CTA
+  const uint32_t nb = I.nb;
+  // element (b, p) of this thread's open stripes
+#define COL(b, p) s_col[((b) * 4 + (p)) * kFillThreads + tid]
+#define SLOT(b, p) s_slot[((b) * 4 + (p)) * kFillThreads + tid]
+  for (uint32_t b = 0; b < nb; ++b) s_q[b * kFillThreads + tid] = 0;
+  for (uint32_t q = tid; q < nb * (kFillThreads / 32); q += kFillThreads) {
+    const uint32_t b = q / (kFillThreads / 32), w = q % (kFillThreads / 32);
+    s_start[q] = bwstart[(bseg_base[t] + b) * 32 + blockIdx.y * (kFillThreads / 32) + w];
+  }
+  __syncthreads();
+  auto flush = [&](uint32_t b, uint32_t stripe) {
+    uint2 cv;
+    cv.x = (uint32_t)COL(b, 0) | ((uint32_t)COL(b, 1) << 16);
+    cv.y = (uint32_t)COL(b, 2) | ((uint32_t)COL(b, 3) << 16);
+    const uint32_t sv = (uint32_t)SLOT(b, 0) | ((uint32_t)SLOT(b, 1) << 8) |
+                        ((uint32_t)SLOT(b, 2) << 16) | ((uint32_t)SLOT(b, 3) << 24);
+    const uint64_t st = s_start[b * (kFillThreads / 32) + wl];
+    reinterpret_cast<uint2 *>(bcol + st)[32 * stripe + lane] = cv;
+    reinterpret_cast<uint32_t *>(bslot + st)[32 * stripe + lane] = sv;
+  };
   for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t row = row0 + threadIdx.x + kBThreads * k;
+    const uint32_t row = row0 + v + kBThreads * k;
     if (row >= I.n) break;
     const uint32_t e0 = rp[row], e1 = rp[row + 1];
     if (e1 - e0 > kBLongDeg) continue;
     for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t b = cl[e] >> kBColBits;
-      if (b < I.nb) len[b]++;  // columns >= n are invalid input: skipped
-      if (e > e0 && cl[e] < cl[e - 1]) *unsorted = 1u;  // the fill needs sorted rows
+      const uint32_t c = __ldg(cl + e);
+      const uint32_t b = c >> kBColBits;
+      if (b >= nb) continue;  // columns >= n are invalid input: skipped
+      const uint32_t q = s_q[b * kFillThreads + tid];
+      const uint32_t p = q & 3;
+      COL(b, p) = (uint16_t)(c & (kBCol - 1));
+      SLOT(b, p) = (uint8_t)k;
+      s_q[b * kFillThreads + tid] = (uint16_t)(q + 1);
+      if (p == 3) flush(b, q >> 2);
     }
   }
-  for (uint32_t b = 0; b < I.nb; ++b) {
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, len[b]);
-    if ((threadIdx.x & 31) == 0)
-      bwlen[(bseg_base[t] + b) * 32 + (threadIdx.x >> 5)] = (wmax + 3) & ~3u;
+  for (uint32_t b = 0; b < nb; ++b) {
+    const uint32_t q = s_q[b * kFillThreads + tid];
+    if (q & 3) {
+      for (uint32_t p = q & 3; p < 4; ++p) {
+        COL(b, p) = (uint16_t)kBPadCol;
+        SLOT(b, p) = 0;
+      }
+      flush(b, q >> 2);
+    }
   }
+#undef COL
+#undef SLOT
 }
 
-// Fill the streams one column block at a time: each row keeps a cursor into
-// its (column-sorted) CSR row, so block b's edges of a row are the ones
-// under the cursor, and all writes of block b land in this warp's region.
-__global__ void __launch_bounds__(kBThreads) bfill_kernel(const InstDesc *inst,
-                                                          const uint32_t *btile_inst,
-                                                          const uint64_t *bseg_base,
-                                                          const uint64_t *bwstart,
-                                                          const uint32_t *row_ptr,
-                                                          const uint32_t *col, uint16_t *bcol,
-                                                          uint8_t *bslot) {
-  const uint32_t t = blockIdx.x;
-  const InstDesc I = inst[btile_inst[t]];
-  const uint32_t *rp = row_ptr + I.rp_base;
-  const uint32_t *cl = col + I.edge_base;
-  const uint32_t row0 = (t - I.btile_base) * kBTileRows;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t cur[kBRowsPerThread], end[kBRowsPerThread];
-#pragma unroll
-  for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t row = row0 + threadIdx.x + kBThreads * k;
-    cur[k] = end[k] = 0;
-    if (row < I.n) {
-      const uint32_t e0 = rp[row], e1 = rp[row + 1];
-      if (e1 - e0 <= kBLongDeg) {
-        cur[k] = e0;
-        end[k] = e1;
-      }
-    }
-  }
-  // Elements are collected 4 at a time in registers (the lane's stripe) and
-  // written with one 8-byte and one 4-byte store; unfilled positions of the
-  // last stripe keep the padding values.
-  constexpr uint32_t kPad2 = kBPadCol | (kBPadCol << 16);
-  for (uint32_t b = 0; b < I.nb; ++b) {
-    const uint64_t start = bwstart[(bseg_base[t] + b) * 32 + warp];
-    uint2 *dc = reinterpret_cast<uint2 *>(bcol + start) + lane;  // stripe s at dc[32 s]
-    uint32_t *dk = reinterpret_cast<uint32_t *>(bslot + start) + lane;
-    uint32_t q = 0;
-    uint2 cv = make_uint2(kPad2, kPad2);
-    uint32_t sv = 0;
-#pragma unroll
-    for (int k = 0; k < kBRowsPerThread; ++k) {
-      while (cur[k] < end[k]) {
-        const uint32_t c = __ldg(cl + cur[k]);
-        const uint32_t cb = c >> kBColBits;
-        if (cb > b) break;  // the row's next edges belong to a later block
-        if (cb == b) {
-          const uint32_t p = q & 3, sh = 16 * (p & 1);
-          const uint32_t v = c & (kBCol - 1);
-          if (p < 2) cv.x = (cv.x & ~(0xffffu << sh)) | (v << sh);
-          else cv.y = (cv.y & ~(0xffffu << sh)) | (v << sh);
-          sv |= (uint32_t)k << (8 * p);
-          if (p == 3) {
-            dc[32 * (q >> 2)] = cv;
-            dk[32 * (q >> 2)] = sv;
-            cv = make_uint2(kPad2, kPad2);
-            sv = 0;
-          }
-          ++q;
-        }
-        ++cur[k];
-      }
-    }
-    if (q & 3) {
-      dc[32 * (q >> 2)] = cv;
-      dk[32 * (q >> 2)] = sv;
-    }
-  }
+size_t fill_smem_bytes(uint32_t nbmax) {
+  return (size_t)nbmax * ((kFillThreads / 32) * 8 + kFillThreads * (4 * 2 + 2 + 4));
 }
 
 template <typename P>
@@ -160,7 +188,8 @@ void free_blocked(cb_graph *h) {
   h->total_bseg = 0;
 }
 
-int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s) {
+int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
+                  const std::vector<CopyGroup> &groups) {
   if (std::getenv("CB_NO_BLOCKED")) return CB_OK;
   // which realisations, their tiles, segments and reduction plans
   uint32_t nbt = 0, slot = 0, group = 0;
@@ -235,8 +264,17 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     uint32_t *d_unsorted = nullptr;
     chk(dalloc(&d_unsorted, 1));
     if (e == cudaSuccess) chk(cudaMemsetAsync(d_unsorted, 0, 4, s));
-    bcount_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr,
-                                            h->col, h->d_bwlen, d_unsorted);
+    // count each group of realisations as soon as its columns are on the device
+    uint32_t r_begin = 0;
+    for (const CopyGroup &g : groups) {
+      chk(cudaStreamWaitEvent(s, g.ev, 0));
+      const uint32_t t0 = h->inst[r_begin].btile_base;
+      const uint32_t t1 = h->inst[g.r_end - 1].btile_base + h->inst[g.r_end - 1].n_btiles;
+      if (t1 > t0 && e == cudaSuccess)
+        bcount_kernel<<<dim3(t1 - t0, kBThreads / kFillThreads), kFillThreads, 0, s>>>(
+            h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr, h->col, h->d_bwlen, d_unsorted, t0);
+      r_begin = g.r_end;
+    }
     chk(cudaGetLastError());
     std::vector<uint32_t> len(nw);
     uint32_t unsorted = 0;
@@ -262,9 +300,14 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       chk(cudaMemsetAsync(h->d_bcol, (int)(kBPadCol & 0xff), alloc * 2, s));  // padding: zero word
       chk(cudaMemsetAsync(h->d_bslot, 0, alloc, s));                          // into slot 0
       chk(cudaMemcpyAsync(h->d_bwstart, start.data(), nw * 8, cudaMemcpyHostToDevice, s));
-      bfill_kernel<<<nbt, kBThreads, 0, s>>>(h->d_inst, h->d_btile_inst, h->d_bseg_base,
-                                             h->d_bwstart, h->row_ptr, h->col, h->d_bcol,
-                                             h->d_bslot);
+      uint32_t nbmax = 1;
+      for (uint32_t r = 0; r < h->n_inst; ++r) nbmax = std::max(nbmax, h->inst[r].nb);
+      const size_t shm = fill_smem_bytes(nbmax);
+      if (shm > 48 * 1024)
+        chk(cudaFuncSetAttribute(bfill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      bfill_kernel<<<dim3(nbt, kBThreads / kFillThreads), kFillThreads, shm, s>>>(
+          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->row_ptr, h->col, h->d_bcol,
+          h->d_bslot, nbmax);
       chk(cudaGetLastError());
       chk(cudaStreamSynchronize(s));
     }

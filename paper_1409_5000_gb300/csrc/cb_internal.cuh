@@ -203,7 +203,15 @@ int prof_begin(int kernel, cudaStream_t s);
 void prof_end(int token, cudaStream_t s);
 
 // column-blocked format builder (cb_blocked.cu); host row_ptr views per realisation
-int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s);
+// Upload copies run in groups of realisations on a stream of their own; the
+// event of a group fires when realisations [previous end, r_end) are on the
+// device.
+struct CopyGroup {
+  uint32_t r_end;
+  cudaEvent_t ev;
+};
+int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
+                  const std::vector<CopyGroup> &groups);
 void free_blocked(cb_graph *h);
 
 // workspace for depth m in precision prec (cb_api.cu)
