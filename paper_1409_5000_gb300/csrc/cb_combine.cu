@@ -46,12 +46,36 @@ __global__ void __launch_bounds__(256) combine_y_kernel(const T *V, uint64_t vs,
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = T(0);
   const T *w = V + I.node_base + i0;
-  for (uint32_t j = 0; j < M; ++j) {
-    const T g = s_g[j];
-    const T *wj = w + (uint64_t)j * vs;
+  if (cnt == 8) {
+    // full group: vector loads (node_base is a multiple of 32 elements), four
+    // basis vectors per iteration so that 8 vector loads are in flight
+    uint32_t j = 0;
+    for (; j + 4 <= M; j += 4) {
+      T x[4][8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if ((uint32_t)q < cnt) acc[q] += g * wj[q];
+      for (int u = 0; u < 4; ++u) Vec8<T>::load(w + (uint64_t)(j + u) * vs, x[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T g = s_g[j + u];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += g * x[u][q];
+      }
+    }
+    for (; j < M; ++j) {
+      T x[8];
+      Vec8<T>::load(w + (uint64_t)j * vs, x);
+      const T g = s_g[j];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += g * x[q];
+    }
+  } else {
+    for (uint32_t j = 0; j < M; ++j) {
+      const T g = s_g[j];
+      const T *wj = w + (uint64_t)j * vs;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if ((uint32_t)q < cnt) acc[q] += g * wj[q];
+    }
   }
   OutT *o = out_is_basis ? out + I.node_base + i0 : out + i0;
 #pragma unroll

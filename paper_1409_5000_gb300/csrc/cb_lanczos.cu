@@ -498,35 +498,6 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
 // w = W_{j+1} - alpha_j scale_j W_j, in place; beta_j = ||w||.  Each thread
 // owns 8 consecutive nodes of the tile (16- or 32-byte aligned vectors).
 template <typename T>
-struct Vec8;
-template <>
-struct Vec8<float> {
-  static __device__ __forceinline__ void load(const float *p, float (&v)[8]) {
-    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-  }
-  static __device__ __forceinline__ void store(float *p, const float (&v)[8]) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
-  }
-};
-template <>
-struct Vec8<double> {
-  static __device__ __forceinline__ void load(const double *p, double (&v)[8]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double2 a = *reinterpret_cast<const double2 *>(p + 2 * q);
-      v[2 * q] = a.x;
-      v[2 * q + 1] = a.y;
-    }
-  }
-  static __device__ __forceinline__ void store(double *p, const double (&v)[8]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) *reinterpret_cast<double2 *>(p + 2 * q) = make_double2(v[2 * q], v[2 * q + 1]);
-  }
-};
-
-template <typename T>
 __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j, uint32_t fin_off) {
   static_assert(kFinRows == 8 * kThreads, "8 nodes per thread");
   __shared__ double s_red[32];
