@@ -104,6 +104,50 @@ int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
                     const uint32_t *const *row_ptr, const uint32_t *const *col,
                     uint32_t flags, void *stream, cb_graph **out);
 
+/*
+ * cb_graph_generate_er -- N Erdos-Renyi backgrounds with one embedded
+ * target, generated on the device into a new handle (paper, "Multiple
+ * backgrounds scenario": the N realisations summed by eq. 5, all sharing the
+ * target sub-graph; the backgrounds never cross the host-device link).
+ * Model: a fixed-draw G(n, M) reading of the paper's ER graphs.  With
+ * SplitMix64 in counter form, output(c) = mix(seed + (c + 1) * G),
+ * G = 0x9E3779B97F4A7C15 (Steele, Lea & Flood, OOPSLA 2014), realisation r
+ * makes draws t = 0 .. m_draws[r]-1 with c = r * 2^32 + t, and draw t is the
+ * pair u = (hi32(z) * n[r]) >> 32, v = (lo32(z) * n[r]) >> 32.  Draws with
+ * u == v are dropped, repeated pairs collapse, the target edges are added to
+ * every realisation (an edge with an endpoint >= n[r] is skipped there), and
+ * each row is sorted: a simple undirected graph as a symmetric CSR pattern.
+ * m_draws = dbar * n / 2 gives mean degree ~dbar.
+ *   n_inst     N >= 1.
+ *   n          host uint32[N], nodes per realisation, each >= 1.
+ *   m_draws    host uint64[N], draws per realisation, each < 2^32.
+ *   seed       generator seed.
+ *   n_tedges   number of target edges (0 for none).
+ *   tedges     host uint32[2 * n_tedges], pairs (u, v); read during the call.
+ *   stream     stream for the work; the call synchronises it.
+ *   out        receives the handle (as from cb_graph_upload).
+ * Errors: CB_ERR_ARG (null arrays, n = 0, m_draws >= 2^32, endpoints
+ * >= 2^31, >= 2^32 entries in one realisation), CB_ERR_CUDA.  Device
+ * temporaries (about 3x the final CSR) are released before returning.
+ */
+int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64_t *m_draws,
+                         uint64_t seed, uint32_t n_tedges, const uint32_t *tedges, void *stream,
+                         cb_graph **out);
+
+/* Number of CSR entries (2 x undirected edges) of realisation r; 0 when r is
+ * out of range or h is null. */
+uint64_t cb_graph_num_entries(const cb_graph *h, uint32_t r);
+
+/*
+ * cb_graph_read -- copy realisation r's CSR pattern out of the handle (for
+ * inspection, e.g. of a generated ensemble).
+ *   row_ptr    uint32[n[r] + 1], host or device (any pointer CUDA can copy to).
+ *   col        uint32[cb_graph_num_entries(h, r)], host or device.
+ *   stream     the copies are queued on it; the call synchronises it.
+ * Errors: CB_ERR_ARG (null handle or array, r out of range), CB_ERR_CUDA.
+ */
+int cb_graph_read(const cb_graph *h, uint32_t r, uint32_t *row_ptr, uint32_t *col, void *stream);
+
 /* Release a handle and its device memory (synchronises the device).  The
  * memory goes back to the library's per-device pool (see below), not to the
  * driver. */

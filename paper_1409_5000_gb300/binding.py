@@ -71,6 +71,12 @@ def lib():
         L.cb_version.argtypes = []
         L.cb_scores_backward.restype = i32
         L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
+        L.cb_graph_generate_er.restype = i32
+        L.cb_graph_generate_er.argtypes = [u32, vp, vp, u64, u32, vp, vp, ctypes.POINTER(vp)]
+        L.cb_graph_read.restype = i32
+        L.cb_graph_read.argtypes = [vp, u32, vp, vp, vp]
+        L.cb_graph_num_entries.restype = u64
+        L.cb_graph_num_entries.argtypes = [vp, u32]
         L.cb_release_cached_memory.restype = i32
         L.cb_release_cached_memory.argtypes = []
         L.cb_topk_noalloc.restype = i32
@@ -130,6 +136,37 @@ def cb_graph_upload(n, nnz, row_ptr_ptrs, col_ptrs, flags, stream):
 
 def cb_graph_free(h):
     _check(lib().cb_graph_free(ctypes.c_void_p(h)))
+
+
+def cb_graph_generate_er(n, m_draws, seed, tedges, stream):
+    """Returns the handle (int).  tedges: None or an (E, 2) integer array."""
+    N = len(n)
+    n_arr = np.ascontiguousarray(n, dtype=np.uint32)
+    m_arr = np.ascontiguousarray(m_draws, dtype=np.uint64)
+    te = np.zeros((0, 2), np.uint32) if tedges is None else np.ascontiguousarray(tedges, dtype=np.uint32).reshape(-1, 2)
+    te_buf = te if len(te) else np.zeros((1, 2), np.uint32)
+    out = ctypes.c_void_p()
+    _check(lib().cb_graph_generate_er(N, n_arr.ctypes.data, m_arr.ctypes.data, seed & (2**64 - 1),
+                                      len(te), te_buf.ctypes.data, ctypes.c_void_p(stream),
+                                      ctypes.byref(out)))
+    return out.value
+
+
+def cb_graph_read(h, r, row_ptr_ptr, col_ptr, stream):
+    _check(lib().cb_graph_read(ctypes.c_void_p(h), r, ctypes.c_void_p(row_ptr_ptr),
+                               ctypes.c_void_p(col_ptr), ctypes.c_void_p(stream)))
+
+
+def read_graph(gs, r, stream=None):
+    """Realisation r of a handle as host numpy arrays (row_ptr, col)."""
+    rp = np.empty(gs.n[r] + 1, dtype=np.uint32)
+    col = np.empty(max(gs.nnz[r], 1), dtype=np.uint32)
+    cb_graph_read(gs.h, r, rp.ctypes.data, col.ctypes.data, _stream_handle(stream))
+    return rp, col[:gs.nnz[r]]
+
+
+def cb_graph_num_entries(h, r):
+    return int(lib().cb_graph_num_entries(ctypes.c_void_p(h), r))
 
 
 def cb_graph_num_instances(h):
@@ -242,6 +279,24 @@ class GraphSet:
         self.n_max = max(n)
         self.device = torch.cuda.current_device()
         self.h = cb_graph_upload(n, nnz, rps, cols, flags, _stream_handle(stream))
+
+    @classmethod
+    def generate_er(cls, n, dbar, seed, target_edges=None, stream=None):
+        """N Erdos-Renyi backgrounds generated on the device (cb_graph_generate_er).
+        `n`: nodes per realisation; `dbar`: mean degree (scalar or per
+        realisation), m_draws = floor(dbar * n / 2 + 1/2)."""
+        import torch
+
+        n = [int(x) for x in n]
+        dbar = list(dbar) if hasattr(dbar, "__len__") else [dbar] * len(n)
+        m = [int(np.floor(float(d) * float(x) * 0.5 + 0.5)) for d, x in zip(dbar, n)]
+        self = cls.__new__(cls)
+        self.device = torch.cuda.current_device()
+        self.h = cb_graph_generate_er(n, m, seed, target_edges, _stream_handle(stream))
+        self.n = n
+        self.nnz = [cb_graph_num_entries(self.h, r) for r in range(len(n))]
+        self.n_max = max(n)
+        return self
 
     def close(self):
         if getattr(self, "h", None):

@@ -297,6 +297,27 @@ using namespace cb;
 
 CB_API const char *cb_last_error(void) { return g_err.c_str(); }
 
+CB_API int cb_graph_read(const cb_graph *h, uint32_t r, uint32_t *row_ptr, uint32_t *col,
+                         void *stream) {
+  if (!h || !row_ptr || !col) return set_error(CB_ERR_ARG, "cb_graph_read: null argument");
+  if (r >= h->n_inst) return set_error(CB_ERR_ARG, "cb_graph_read: realisation index out of range");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const InstDesc &I = h->inst[r];
+  const uint64_t end = r + 1 < h->n_inst ? h->inst[r + 1].edge_base : h->total_nnz;
+  cudaError_t e = cudaMemcpyAsync(row_ptr, h->row_ptr + I.rp_base, ((size_t)I.n + 1) * 4,
+                                  cudaMemcpyDefault, s);
+  if (e == cudaSuccess && end > I.edge_base)
+    e = cudaMemcpyAsync(col, h->col + I.edge_base, (end - I.edge_base) * 4, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_error(e, "cb_graph_read");
+}
+
+CB_API uint64_t cb_graph_num_entries(const cb_graph *h, uint32_t r) {
+  if (!h || r >= h->n_inst) return 0;
+  const uint64_t end = r + 1 < h->n_inst ? h->inst[r + 1].edge_base : h->total_nnz;
+  return end - h->inst[r].edge_base;
+}
+
 CB_API int cb_release_cached_memory(void) {
   cudaError_t e = cudaDeviceSynchronize();
   std::lock_guard<std::mutex> lk(g_pool_mu);

@@ -49,6 +49,15 @@ static inline uint64_t sm64_below(uint64_t *s, uint64_t bound) { /* [0,bound) */
 }
 
 /* Exposed so Python can derive per-realisation seeds from one base. */
+/* `count` consecutive SplitMix64 outputs from state `seed` (the sequential
+ * form of the generator; the counter form used for on-device generation is
+ * output(c) = mix(seed + (c + 1) * golden)). */
+int cbs_sm64_stream(uint64_t seed, uint64_t count, uint64_t *out) {
+  uint64_t s = seed;
+  for (uint64_t i = 0; i < count; ++i) out[i] = sm64_next(&s);
+  return 0;
+}
+
 uint64_t cbs_mix(uint64_t a, uint64_t b, uint64_t c) {
   uint64_t s = a;
   uint64_t x = sm64_next(&s);

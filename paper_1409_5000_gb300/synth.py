@@ -62,6 +62,8 @@ def _lib():
         lib.cbs_free.argtypes = [vp]
         lib.cbs_target_edges.restype = i64
         lib.cbs_target_edges.argtypes = [vp, u32, u32, ctypes.c_int, u64, vp, vp, u64]
+        lib.cbs_sm64_stream.restype = ctypes.c_int
+        lib.cbs_sm64_stream.argtypes = [u64, u64, vp]
         lib.cbs_sample_nodes.restype = ctypes.c_int
         lib.cbs_sample_nodes.argtypes = [u32, u32, u64, vp]
         _LIB = lib
@@ -127,6 +129,71 @@ def _finish(h, extra_edges=None) -> Graph:
     if rc != 0:
         raise ValueError("graph too large for uint32 row offsets")
     return Graph(int(n), row_ptr, col)
+
+
+# ---------------------------------------------------------------------------
+# Counter-based ER backgrounds (the definition the device generator
+# cb_graph_generate_er follows; this is its CPU statement).
+#
+# SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+# generators", OOPSLA 2014) in counter form: output(c) = mix(seed + (c+1) G),
+# G = 0x9E3779B97F4A7C15, mix = the generator's output function.  Realisation
+# r takes draws t = 0 .. M_r - 1 with counter c = r * 2^32 + t; draw t gives
+# the pair u = (hi32(z) * n) >> 32, v = (lo32(z) * n) >> 32.  Draws with
+# u == v are dropped and repeated pairs collapse (a fixed-draw G(n, M)
+# reading of the paper's Erdos-Renyi backgrounds); the target's edges are
+# OR-ed in; rows come out sorted.
+# ---------------------------------------------------------------------------
+SM64_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def sm64_stream(seed: int, count: int) -> np.ndarray:
+    """`count` consecutive SplitMix64 outputs from state `seed` (C reference)."""
+    out = np.empty(max(count, 1), dtype=np.uint64)
+    _lib().cbs_sm64_stream(seed & (2**64 - 1), count, out.ctypes.data)
+    return out[:count]
+
+
+def sm64_counter(seed: int, counters) -> np.ndarray:
+    """Counter form of SplitMix64: mix(seed + (c + 1) * G) for each counter c."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & (2**64 - 1)) + (c + np.uint64(1)) * np.uint64(SM64_GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def er_draw_count(n: int, dbar: float) -> int:
+    """M = floor(dbar * n / 2 + 1/2) draws give mean degree ~dbar."""
+    return int(np.floor(float(dbar) * float(n) * 0.5 + 0.5))
+
+
+def er_draws(n: int, m_draws: int, seed: int, r: int):
+    """(u, v) of the M draws of realisation r (u == v not yet dropped)."""
+    t = np.arange(m_draws, dtype=np.uint64)
+    z = sm64_counter(seed, (np.uint64(r) << np.uint64(32)) + t)
+    with np.errstate(over="ignore"):
+        u = ((z >> np.uint64(32)) * np.uint64(n)) >> np.uint64(32)
+        v = ((z & np.uint64(0xFFFFFFFF)) * np.uint64(n)) >> np.uint64(32)
+    return u.astype(np.int64), v.astype(np.int64)
+
+
+def er_generated(n: int, m_draws: int, seed: int, r: int, target_edges=None) -> Graph:
+    """Realisation r of the counter-based ER recipe, target edges OR-ed in."""
+    u, v = er_draws(n, m_draws, seed, r)
+    if target_edges is not None and len(target_edges):
+        te = np.asarray(target_edges, dtype=np.int64).reshape(-1, 2)
+        te = te[(te[:, 0] < n) & (te[:, 1] < n)]
+        u = np.concatenate([u, te[:, 0]])
+        v = np.concatenate([v, te[:, 1]])
+    keep = u != v
+    u, v = u[keep], v[keep]
+    key = np.unique(np.concatenate([u * n + v, v * n + u]))
+    rows = key // n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return Graph(int(n), np.cumsum(row_ptr).astype(np.uint32), (key % n).astype(np.uint32))
 
 
 def er(n: int, p: float, seed: int, extra_edges=None) -> Graph:

@@ -1,0 +1,86 @@
+"""On-device ER generation (cb_graph_generate_er) vs its CPU statement (needs a GB300).
+
+The device generator and synth.er_generated implement the same counter-based
+definition independently (CUDA vs numpy); the CSR patterns must agree bit for
+bit, and the scores of a generated handle must equal those of the same graphs
+uploaded from the host.
+"""
+import numpy as np
+import pytest
+
+from paper_1409_5000_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1409_5000_gb300 import binding
+
+    binding.lib()
+    return binding
+
+
+def _cpu(n, dbar, seed, tedges):
+    return [synth.er_generated(x, synth.er_draw_count(x, dbar), seed, r, tedges)
+            for r, x in enumerate(n)]
+
+
+@pytest.mark.parametrize("case", ["small", "uneven", "no_target", "dense"])
+def test_generated_csr_matches_cpu_definition(B, case):
+    if case == "small":
+        n, dbar, tedges = [500] * 10, 3.2, synth.target_edges(np.arange(15, dtype=np.uint32) * 7, 8, False, 3)
+    elif case == "uneven":
+        n, dbar, tedges = [20_000, 3_000, 150_000, 777], 20.0, [(0, 1), (1, 2), (2, 0), (5, 900), (10, 2999)]
+    elif case == "no_target":
+        n, dbar, tedges = [100_000, 100_000], 16.0, None
+    else:  # dense: many repeated pairs collapse
+        n, dbar, tedges = [64, 64, 64], 40.0, [(1, 2)]
+    seed = synth.seed_for(901, 0)
+    ref = _cpu(n, dbar, seed, tedges)
+    gs = B.GraphSet.generate_er(n, dbar, seed, tedges)
+    try:
+        assert gs.nnz == [g.nnz for g in ref]
+        for r, g in enumerate(ref):
+            rp, col = B.read_graph(gs, r)
+            assert np.array_equal(rp, g.row_ptr), r
+            assert np.array_equal(col, g.col), r
+    finally:
+        gs.close()
+
+
+def test_generated_scores_equal_uploaded(B):
+    """Same graphs through both entry points give bit-identical scores."""
+    n = [30_000, 60_000, 45_000, 30_000]
+    nodes = synth.sample_nodes(30_000, 20, 5)
+    tedges = synth.target_edges(nodes, 10, False, 6)
+    seed = synth.seed_for(902, 0)
+    ref = _cpu(n, 12.0, seed, tedges)
+    with B.GraphSet(ref) as up, B.GraphSet.generate_er(n, 12.0, seed, tedges) as gen:
+        for prec in (0, 1):
+            a = B.ensemble_scores(up, 20, prec)
+            b = B.ensemble_scores(gen, 20, prec)
+            assert float(a[0].item()) == float(b[0].item())
+            assert torch.equal(a[1], b[1])
+
+
+def test_generate_argument_errors(B):
+    with pytest.raises(B.CBError):
+        B.cb_graph_generate_er([100, 0], [10, 10], 1, None, 0)  # n = 0
+    with pytest.raises(B.CBError):
+        B.cb_graph_generate_er([100], [2**32], 1, None, 0)  # too many draws
+    with pytest.raises(B.CBError):
+        B.cb_graph_generate_er([100], [10], 1, [(1, 2**31)], 0)  # endpoint range
+
+
+def test_read_argument_errors(B):
+    gs = B.GraphSet.generate_er([50], 4.0, 1)
+    try:
+        rp = np.empty(51, np.uint32)
+        with pytest.raises(B.CBError):
+            B.cb_graph_read(gs.h, 1, rp.ctypes.data, rp.ctypes.data, 0)
+    finally:
+        gs.close()

@@ -82,3 +82,54 @@ def test_paper_sparse_target_shape():
                 seen.add(int(v))
                 stack.append(int(v))
     assert len(seen) == k
+
+
+# --- counter-based ER recipe (the definition the device generator follows) ---
+
+def _mix_py(x):
+    """SplitMix64 output function on a Python int (mod 2^64), written out."""
+    M = (1 << 64) - 1
+    z = x & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 12345, 2**63 + 17, 2**64 - 1])
+def test_sm64_counter_matches_sequential_c(seed):
+    """Counter form c -> mix(seed + (c+1) G) equals the C generator's stream."""
+    ref = synth.sm64_stream(seed, 64)
+    got = synth.sm64_counter(seed, np.arange(64))
+    assert np.array_equal(ref, got)
+    assert int(got[5]) == _mix_py(seed + 6 * synth.SM64_GOLDEN)
+
+
+def test_er_generated_matches_loop_statement():
+    """The vectorised recipe equals a plain loop over the draws (tiny n)."""
+    n, M, seed, r = 37, 60, 2024, 5
+    tedges = [(0, 1), (1, 2), (2, 3), (3, 0), (1, 36)]
+    adj = set()
+    for t in range(M):
+        z = _mix_py(seed + ((r << 32) + t + 1) * synth.SM64_GOLDEN)
+        u, v = ((z >> 32) * n) >> 32, ((z & 0xFFFFFFFF) * n) >> 32
+        if u != v:
+            adj |= {(u, v), (v, u)}
+    for u, v in tedges:
+        adj |= {(u, v), (v, u)}
+    g = synth.er_generated(n, M, seed, r, tedges)
+    _check_simple(g)
+    src = np.repeat(np.arange(n), g.degrees())
+    assert set(zip(src.tolist(), g.col.tolist())) == adj
+
+
+def test_er_generated_degree_and_independence():
+    n = 20_000
+    M = synth.er_draw_count(n, 8.0)
+    g0 = synth.er_generated(n, M, 7, 0)
+    g1 = synth.er_generated(n, M, 7, 1)
+    # each draw is a uniform pair; collisions and u == v are O(1/n) rare
+    assert abs(g0.nnz - 2 * M) <= 2 * M * 5e-3
+    assert abs(g0.degrees().mean() - 8.0) < 0.05
+    # realisations differ, and their degree variance is Poisson-like
+    assert not np.array_equal(g0.col[:1000], g1.col[:1000])
+    assert 6.5 < g0.degrees().var() < 9.5
