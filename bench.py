@@ -402,6 +402,39 @@ def main():
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": n_e2e,
                "upload_ms": sum(up_ms) / len(up_ms),
                "api": "cb_graph_upload(pinned host) + cb_ensemble_scores + cb_topk + D2H + cb_graph_free"}
+        # the same shape with the backgrounds generated on the device
+        # (cb_graph_generate_er: same n_r, mean degree and target; its own ER model)
+        if ens.meta.get("dbar") is not None and ens.target_edges is not None:
+            ns = [g.n for g in ens.graphs]
+            gen_ms, gen_units = [], []
+
+            def gen_step(q):
+                u0 = time.perf_counter()
+                with B.GraphSet.generate_er(ns, ens.meta["dbar"], synth.seed_for(77, q),
+                                            ens.target_edges) as g3:
+                    gen_ms.append(1e3 * (time.perf_counter() - u0))
+                    gen_units.append(sum(g3.nnz) * m)
+                    S3 = torch.empty(g3.n_max, dtype=torch.float64, device=dev)
+                    l3 = torch.empty(1, dtype=torch.float64, device=dev)
+                    B.ensemble_scores(g3, m, B.CB_FP32, out=(S3, l3))
+                    i3, v3 = B.topk(S3, k)
+                    host_idx.copy_(i3, non_blocking=True)
+                    host_val.copy_(v3, non_blocking=True)
+                    host_ls.copy_(l3, non_blocking=True)
+                    torch.cuda.synchronize()
+
+            gen_step(0)
+            gen_ms.clear()
+            gen_units.clear()
+            t0 = time.perf_counter()
+            for q in range(n_e2e):
+                gen_step(q + 1)
+            g_ms = 1e3 * (time.perf_counter() - t0) / n_e2e
+            extra["e2e_generated_on_device"] = {
+                "value": sum(gen_units) / len(gen_units) / (g_ms * 1e-3), "unit": UNIT,
+                "ms_per_step": g_ms, "generate_ms": sum(gen_ms) / len(gen_ms), "steps": n_e2e,
+                "h2d_bytes_per_step": 8 * len(ens.target_edges) + 20 * len(ns), "d2h_bytes_per_step": d2h,
+                "api": "cb_graph_generate_er + cb_ensemble_scores + cb_topk + D2H + cb_graph_free"}
 
     cpu = None
     if rank == 0 and not args.skip_extra and world == 1:
