@@ -120,13 +120,13 @@ int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
  * m_draws = dbar * n / 2 gives mean degree ~dbar.
  *   n_inst     N >= 1.
  *   n          host uint32[N], nodes per realisation, each >= 1.
- *   m_draws    host uint64[N], draws per realisation, each < 2^32.
+ *   m_draws    host uint64[N], draws per realisation; m_draws[r] + n_tedges < 2^31.
  *   seed       generator seed.
  *   n_tedges   number of target edges (0 for none).
  *   tedges     host uint32[2 * n_tedges], pairs (u, v); read during the call.
  *   stream     stream for the work; the call synchronises it.
  *   out        receives the handle (as from cb_graph_upload).
- * Errors: CB_ERR_ARG (null arrays, n = 0, m_draws >= 2^32, endpoints
+ * Errors: CB_ERR_ARG (null arrays, n = 0, too many draws, endpoints
  * >= 2^31, >= 2^32 entries in one realisation), CB_ERR_CUDA.  Device
  * temporaries (about 3x the final CSR) are released before returning.
  */

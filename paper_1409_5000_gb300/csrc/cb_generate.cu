@@ -85,39 +85,101 @@ __global__ void __launch_bounds__(kGenThreads) gen_count_kernel(GenArgs a, uint3
   }
 }
 
-__global__ void __launch_bounds__(kGenThreads) gen_fill_kernel(GenArgs a,
-                                                               unsigned long long *cursor,
-                                                               uint32_t *raw) {
+// cursor[row] counts from the realisation's first entry (32-bit atomics)
+__global__ void __launch_bounds__(kGenThreads) gen_fill_kernel(GenArgs a, const uint64_t *ebase,
+                                                               uint32_t *cursor, uint32_t *raw) {
   for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < a.items;
        g += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t r, u, v;
     if (!gen_item(a, g, r, u, v)) continue;
-    raw[atomicAdd(cursor + a.node_off[r] + u, 1ull)] = v;
-    raw[atomicAdd(cursor + a.node_off[r] + v, 1ull)] = u;
+    const uint64_t eb = ebase[r];
+    raw[eb + atomicAdd(cursor + a.node_off[r] + u, 1u)] = v;
+    raw[eb + atomicAdd(cursor + a.node_off[r] + v, 1u)] = u;
   }
 }
 
-// Sort each row ascending (insertion sort: rows are short) and drop repeats;
-// deg[i] becomes the number of distinct columns.
-__global__ void __launch_bounds__(kGenThreads) gen_sort_kernel(const uint64_t *off, uint32_t *raw,
-                                                               uint32_t *deg, uint64_t rows) {
+__global__ void __launch_bounds__(kGenThreads) gen_cursor_kernel(GenArgs a, const uint64_t *off,
+                                                                 const uint64_t *ebase,
+                                                                 uint32_t *cursor, uint64_t rows) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows;
        i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = a.n_inst;  // node_off[lo] <= i < node_off[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (a.node_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    cursor[i] = (uint32_t)(off[i] - ebase[lo]);
+  }
+}
+
+// Sort each row ascending and drop repeats, one warp per row; deg[i] becomes
+// the number of distinct columns.  Rows of up to 64 entries are sorted in
+// registers by a bitonic network over shuffles (entry e of the row sits in
+// lane e % 32, register e / 32; unused slots hold UINT32_MAX); longer rows
+// (rare: degrees are ~Poisson) fall back to an insertion sort by lane 0.
+__device__ __forceinline__ uint32_t bitonic_cx(uint32_t x, uint32_t y, bool keep_min) {
+  return keep_min ? min(x, y) : max(x, y);
+}
+
+__global__ void __launch_bounds__(kGenThreads) gen_sort_kernel(const uint64_t *off, uint32_t *raw,
+                                                               uint32_t *deg, uint64_t rows) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < rows;
+       i += warps) {
     uint32_t *p = raw + off[i];
     const uint32_t d = (uint32_t)(off[i + 1] - off[i]);
-    for (uint32_t q = 1; q < d; ++q) {
-      const uint32_t x = p[q];
-      uint32_t s = q;
-      while (s > 0 && p[s - 1] > x) {
-        p[s] = p[s - 1];
-        --s;
+    if (d > 64) {
+      uint32_t w = 0;
+      if (lane == 0) {
+        for (uint32_t q = 1; q < d; ++q) {
+          const uint32_t x = p[q];
+          uint32_t s = q;
+          while (s > 0 && p[s - 1] > x) {
+            p[s] = p[s - 1];
+            --s;
+          }
+          p[s] = x;
+        }
+        for (uint32_t q = 0; q < d; ++q)
+          if (w == 0 || p[q] != p[w - 1]) p[w++] = p[q];
+        deg[i] = w;
       }
-      p[s] = x;
+      __syncwarp();
+      continue;
     }
-    uint32_t w = 0;
-    for (uint32_t q = 0; q < d; ++q)
-      if (w == 0 || p[q] != p[w - 1]) p[w++] = p[q];
-    deg[i] = w;
+    uint32_t x0 = lane < d ? p[lane] : 0xffffffffu;
+    uint32_t x1 = lane + 32 < d ? p[lane + 32] : 0xffffffffu;
+    const uint32_t kmax = d > 32 ? 64u : 32u;
+    for (uint32_t k = 2; k <= kmax; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        if (j == 32) {  // partner is the other register of the same lane (k = 64)
+          const uint32_t lo = min(x0, x1), hi = max(x0, x1);
+          x0 = lo;
+          x1 = hi;
+          continue;
+        }
+        const bool lower = (lane & j) == 0;
+        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, x0, j);
+        x0 = bitonic_cx(x0, y0, lower == ((lane & k) == 0));
+        if (kmax == 64) {
+          const uint32_t y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+          x1 = bitonic_cx(x1, y1, lower == (((lane + 32) & k) == 0));
+        }
+      }
+    }
+    // distinct values: keep an entry unless it equals its predecessor
+    const uint32_t pr0 = __shfl_up_sync(0xffffffffu, x0, 1);
+    const uint32_t pr1 = __shfl_up_sync(0xffffffffu, x1, 1);
+    const uint32_t last0 = __shfl_sync(0xffffffffu, x0, 31);
+    const bool k0 = lane < d && (lane == 0 || x0 != pr0);
+    const bool k1 = lane + 32 < d && (lane == 0 ? x1 != last0 : x1 != pr1);
+    const uint32_t b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+    const uint32_t lt = (1u << lane) - 1u;
+    __syncwarp();  // every lane has read its entries before any is overwritten
+    if (k0) p[__popc(b0 & lt)] = x0;
+    if (k1) p[__popc(b0) + __popc(b1 & lt)] = x1;
+    if (lane == 0) deg[i] = __popc(b0) + __popc(b1);
   }
 }
 
@@ -128,8 +190,10 @@ __global__ void __launch_bounds__(kGenThreads) gen_compact_kernel(GenArgs a, con
                                                                   const uint64_t *off2,
                                                                   uint32_t *col, uint32_t *rp,
                                                                   uint64_t rows) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows;
-       i += (uint64_t)gridDim.x * blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < rows;
+       i += warps) {
     uint32_t lo = 0, hi = a.n_inst;  // node_off[lo] <= i < node_off[hi]
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
@@ -140,10 +204,13 @@ __global__ void __launch_bounds__(kGenThreads) gen_compact_kernel(GenArgs a, con
     const uint64_t d = off2[i + 1] - off2[i];
     const uint32_t *src = raw + off[i];
     uint32_t *dst = col + off2[i];
-    for (uint64_t q = 0; q < d; ++q) dst[q] = src[q];
-    const uint64_t local = i - a.node_off[r];
-    rp[a.node_off[r] + r + local] = (uint32_t)(off2[i] - base);
-    if (i + 1 == a.node_off[r + 1]) rp[a.node_off[r] + r + local + 1] = (uint32_t)(off2[i + 1] - base);
+    for (uint64_t q = lane; q < d; q += 32) dst[q] = src[q];
+    if (lane == 0) {
+      const uint64_t local = i - a.node_off[r];
+      rp[a.node_off[r] + r + local] = (uint32_t)(off2[i] - base);
+      if (i + 1 == a.node_off[r + 1])
+        rp[a.node_off[r] + r + local + 1] = (uint32_t)(off2[i + 1] - base);
+    }
   }
 }
 
@@ -282,8 +349,8 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   std::vector<uint64_t> node_off(n_inst + 1, 0), draw_off(n_inst + 1, 0);
   for (uint32_t r = 0; r < n_inst; ++r) {
     if (n[r] == 0) return set_error(CB_ERR_ARG, "cb_graph_generate_er: realisation with n = 0");
-    if (m_draws[r] >= (1ull << 32))
-      return set_error(CB_ERR_ARG, "cb_graph_generate_er: need m_draws < 2^32 per realisation");
+    if (m_draws[r] + n_tedges >= (1ull << 31))  // 2 entries per draw, 32-bit cursors
+      return set_error(CB_ERR_ARG, "cb_graph_generate_er: need m_draws + n_tedges < 2^31 per realisation");
     node_off[r + 1] = node_off[r] + n[r];
     draw_off[r + 1] = draw_off[r] + m_draws[r];
   }
@@ -302,7 +369,8 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
            *rp = nullptr;
   uint64_t *d_node_off = nullptr, *d_draw_off = nullptr, *off = nullptr, *off2 = nullptr,
            *bsum = nullptr, *bound = nullptr;
-  unsigned long long *cursor = nullptr;
+  uint32_t *cursor = nullptr;
+  uint64_t *ebase = nullptr;
   chk(B.alloc(&d_n, n_inst));
   chk(B.alloc(&d_node_off, n_inst + 1));
   chk(B.alloc(&d_draw_off, n_inst + 1));
@@ -313,6 +381,7 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   chk(B.alloc(&cursor, rows));
   chk(B.alloc(&bsum, (rows + kScanBlock - 1) / kScanBlock + 2));
   chk(B.alloc(&bound, n_inst + 1));
+  chk(B.alloc(&ebase, n_inst + 1));
   if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: allocate");
   chk(cudaMemcpyAsync(d_n, n, n_inst * 4, cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(d_node_off, node_off.data(), (n_inst + 1) * 8, cudaMemcpyHostToDevice, s));
@@ -331,10 +400,11 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: count");
   chk(B.alloc(&raw, std::max<uint64_t>(entries, 1)));
   if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: allocate entries");
-  chk(cudaMemcpyAsync(cursor, off, rows * 8, cudaMemcpyDeviceToDevice, s));
   if (e == cudaSuccess) {
-    gen_fill_kernel<<<grid_for(items), kGenThreads, 0, s>>>(a, cursor, raw);
-    gen_sort_kernel<<<grid_for(rows), kGenThreads, 0, s>>>(off, raw, deg, rows);
+    gather_bounds_kernel<<<(n_inst + 256) / 256, 256, 0, s>>>(off, d_node_off, n_inst, ebase);
+    gen_cursor_kernel<<<grid_for(rows), kGenThreads, 0, s>>>(a, off, ebase, cursor, rows);
+    gen_fill_kernel<<<grid_for(items), kGenThreads, 0, s>>>(a, ebase, cursor, raw);
+    gen_sort_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(off, raw, deg, rows);
     chk(cudaGetLastError());
     chk(exclusive_scan(deg, rows, off2, bsum, s));
     gather_bounds_kernel<<<(n_inst + 256) / 256, 256, 0, s>>>(off2, d_node_off, n_inst, bound);
@@ -353,7 +423,7 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   chk(B.alloc(&col, std::max<uint64_t>(hb[n_inst], 1)));
   chk(B.alloc(&rp, rows + n_inst));
   if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: allocate CSR");
-  gen_compact_kernel<<<grid_for(rows), kGenThreads, 0, s>>>(a, off, raw, off2, col, rp, rows);
+  gen_compact_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(a, off, raw, off2, col, rp, rows);
   chk(cudaGetLastError());
   chk(cudaStreamSynchronize(s));  // the upload reads row_ptr back with a plain copy
   if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: compact");

@@ -29,7 +29,7 @@ def _cpu(n, dbar, seed, tedges):
             for r, x in enumerate(n)]
 
 
-@pytest.mark.parametrize("case", ["small", "uneven", "no_target", "dense"])
+@pytest.mark.parametrize("case", ["small", "uneven", "no_target", "dense", "very_dense"])
 def test_generated_csr_matches_cpu_definition(B, case):
     if case == "small":
         n, dbar, tedges = [500] * 10, 3.2, synth.target_edges(np.arange(15, dtype=np.uint32) * 7, 8, False, 3)
@@ -37,8 +37,10 @@ def test_generated_csr_matches_cpu_definition(B, case):
         n, dbar, tedges = [20_000, 3_000, 150_000, 777], 20.0, [(0, 1), (1, 2), (2, 0), (5, 900), (10, 2999)]
     elif case == "no_target":
         n, dbar, tedges = [100_000, 100_000], 16.0, None
-    else:  # dense: many repeated pairs collapse
+    elif case == "dense":  # many repeated pairs collapse; rows of 33-64 raw entries
         n, dbar, tedges = [64, 64, 64], 40.0, [(1, 2)]
+    else:  # rows of > 64 raw entries take the serial sort path
+        n, dbar, tedges = [64, 96], 200.0, [(1, 2)]
     seed = synth.seed_for(901, 0)
     ref = _cpu(n, dbar, seed, tedges)
     gs = B.GraphSet.generate_er(n, dbar, seed, tedges)
@@ -71,7 +73,7 @@ def test_generate_argument_errors(B):
     with pytest.raises(B.CBError):
         B.cb_graph_generate_er([100, 0], [10, 10], 1, None, 0)  # n = 0
     with pytest.raises(B.CBError):
-        B.cb_graph_generate_er([100], [2**32], 1, None, 0)  # too many draws
+        B.cb_graph_generate_er([100], [2**31], 1, None, 0)  # too many draws
     with pytest.raises(B.CBError):
         B.cb_graph_generate_er([100], [10], 1, [(1, 2**31)], 0)  # endpoint range
 
