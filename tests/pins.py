@@ -245,6 +245,60 @@ def check_topk(mod):
         assert np.array_equal(val, S[ref])
 
 
+def _closed_walk_sc(n, edges, kmax=60):
+    """SC_i = sum_k (A^k)_ii / k! from exact integer closed-walk counts."""
+    from fractions import Fraction
+
+    A = [[0] * n for _ in range(n)]
+    for u, v in edges:
+        A[u][v] = A[v][u] = 1
+    P = [[int(i == j) for j in range(n)] for i in range(n)]
+    tot = [Fraction(1)] * n
+    fact = 1
+    for k in range(1, kmax + 1):
+        P = [[sum(P[i][q] * A[q][j] for q in range(n)) for j in range(n)] for i in range(n)]
+        fact *= k
+        tot = [tot[i] + Fraction(P[i][i], fact) for i in range(n)]
+    return np.array([float(t) for t in tot])
+
+
+def check_subgraph_centrality(mod):
+    """SC = diag(e^A) (eq. 3): dense and Gauss-quadrature forms."""
+    s6 = math.sqrt(6.0)
+    cases = [
+        (graph(5, []), np.ones(5)),
+        (graph(7, complete(7)), np.full(7, (math.exp(6) + 6 * math.exp(-1)) / 7)),
+        (graph(7, bipartite(1, 6)),  # star: centre cosh(sqrt s), leaves 1 + (cosh(sqrt s) - 1)/s
+         np.concatenate([[math.cosh(s6)], np.full(6, 1 + (math.cosh(s6) - 1) / 6)])),
+        (graph(9, cycle(9)),
+         np.full(9, sum(math.exp(2 * math.cos(2 * math.pi * j / 9)) for j in range(9)) / 9)),
+    ]
+    for g, ref in cases:
+        assert rel(mod.subgraph_centrality_dense(*g), ref) < 1e-13
+        th, c0 = mod.subgraph_centrality_krylov(*g, range(g[0]), g[0])
+        assert rel(np.exp(th) * c0, ref) < 1e-11
+    for seed, n in [(11, 6), (12, 9), (13, 10)]:
+        n, edges = _small_random(seed, n)
+        g = graph(n, edges)
+        ref = _closed_walk_sc(n, edges)
+        assert rel(mod.subgraph_centrality_dense(*g), ref) < 1e-13, seed
+        th, c0 = mod.subgraph_centrality_krylov(*g, range(n), n)  # exact at m = n
+        assert rel(np.exp(th) * c0, ref) < 1e-11, seed
+    # Gauss rule for exp: a lower bound that grows with m
+    g = synth.er(80, 0.06, 21)
+    dense = mod.subgraph_centrality_dense(g.n, g.row_ptr, g.col)
+    nodes = [0, 7, 33, 79]
+    prev = np.zeros(len(nodes))
+    for m in (1, 2, 3, 5, 8):
+        th, c0 = mod.subgraph_centrality_krylov(g.n, g.row_ptr, g.col, nodes, m)
+        est = np.exp(th) * c0
+        assert np.all(est >= prev * (1 - 1e-13)) and np.all(est <= dense[nodes] * (1 + 1e-12)), m
+        prev = est
+    th, c0 = mod.subgraph_centrality_krylov(g.n, g.row_ptr, g.col, nodes, 40)
+    assert rel(np.exp(th) * c0, dense[nodes]) < 1e-10
+
+
 ALL_CHECKS = [check_closed_forms_dense, check_closed_forms_krylov, check_disjoint_union,
               check_walk_counts, check_library_expm, check_invariants, check_krylov_converges,
-              check_lanczos_relation, check_tridiag, check_ensemble, check_topk]
+              check_lanczos_relation, check_tridiag, check_ensemble, check_topk,
+              check_subgraph_centrality]

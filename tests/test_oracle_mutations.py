@@ -47,6 +47,10 @@ MUTATIONS = [
     ("V[0] = b / beta0", "V[0] = b / n"),
     # walk-count brute force: factorial off by one
     ("fact *= k\n", "fact *= k + 1\n"),
+    # sub-graph centrality: last instead of first quadrature coefficient
+    ("c0.append(float(c[0]))", "c0.append(float(c[-1]))"),
+    # sub-graph centrality: start vector on the wrong node
+    ("b[int(i)] = 1.0", "b[(int(i) + 1) % n] = 1.0"),
 ]
 
 
