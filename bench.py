@@ -436,6 +436,24 @@ def main():
                 "h2d_bytes_per_step": 8 * len(ens.target_edges) + 20 * len(ns), "d2h_bytes_per_step": d2h,
                 "api": "cb_graph_generate_er + cb_ensemble_scores + cb_topk + D2H + cb_graph_free"}
 
+    if rank == 0 and not args.skip_extra:
+        # sub-graph centrality (eq. 3) of the top-k nodes in the largest realisation
+        r_big = max(range(len(gs.n)), key=lambda r: gs.n[r])
+        B.ensemble_scores(gs, m, B.CB_FP32, out=(S, ls))
+        B.topk(S, k, out=(idx, val))
+        cand = idx.clone()
+        sc = torch.empty(k, dtype=torch.float64, device=dev)
+        B.cb_subgraph_centrality(gs.h, r_big, m, B.CB_FP32, k, cand.data_ptr(), sc.data_ptr(),
+                                 ls1.data_ptr(), stream.cuda_stream)
+        t0 = time.perf_counter()
+        B.cb_subgraph_centrality(gs.h, r_big, m, B.CB_FP32, k, cand.data_ptr(), sc.data_ptr(),
+                                 ls1.data_ptr(), stream.cuda_stream)
+        sc_ms = 1e3 * (time.perf_counter() - t0)
+        extra["subgraph_centrality_topk"] = {
+            "ms": sc_ms, "nodes": k, "m": m, "realisation_n": gs.n[r_big],
+            "realisation_nnz": gs.nnz[r_big],
+            "api": "cb_subgraph_centrality (k copies of the realisation, k Lanczos runs, Gauss rule)"}
+
     cpu = None
     if rank == 0 and not args.skip_extra and world == 1:
         v, done, t, res = cpu_oracle_sample(ens, m, budget_s=15.0, want={0, 1})

@@ -62,6 +62,7 @@ extern "C" {
 #define CB_MAX_M 128
 /* largest k accepted by cb_topk */
 #define CB_MAX_TOPK 4096
+#define CB_MAX_SC_NODES 1024
 
 typedef struct cb_graph cb_graph;
 
@@ -147,6 +148,31 @@ uint64_t cb_graph_num_entries(const cb_graph *h, uint32_t r);
  * Errors: CB_ERR_ARG (null handle or array, r out of range), CB_ERR_CUDA.
  */
 int cb_graph_read(const cb_graph *h, uint32_t r, uint32_t *row_ptr, uint32_t *col, void *stream);
+
+/*
+ * cb_subgraph_centrality -- Estrada's sub-graph centrality SC(i) = (e^A)_ii
+ * (eq. 3) for k nodes of realisation inst, by Gauss quadrature: m Lanczos
+ * steps started at e_i give the m-point Gauss rule e1^T exp(T_m) e1 for
+ * e_i^T e^A e_i (Golub & Meurant, "Matrices, Moments and Quadrature with
+ * Applications", 2010).  For exp the rule is a lower bound that increases
+ * with m; it is exact once the Krylov space from e_i is invariant.  The
+ * paper calls SC expensive at scale; per node it costs one m-step Lanczos
+ * run over the whole realisation, and the k runs go together.
+ *   h, inst    handle and realisation index (< N).
+ *   m          Krylov depth, 1 <= m <= CB_MAX_M.
+ *   prec       CB_FP32 or CB_FP64 (vectors; scalars and the quadrature FP64).
+ *   k          number of nodes, 1 <= k <= CB_MAX_SC_NODES.
+ *   nodes      uint32[k] node indices (< n[inst]), host or device.
+ *   sc_scaled  device double[k], written: SC(nodes[q]) = exp(*log_scale) * sc_scaled[q].
+ *   log_scale  device double[1], written: max over q of lambda_max(T_m) from e_q.
+ * The call builds a temporary handle with k copies of the realisation
+ * (k * (nnz + n) * 4 bytes plus their formats and a (m+1) * k * n basis),
+ * synchronises `stream` and frees it before returning.
+ * Errors: CB_ERR_ARG (null arguments, ranges), CB_ERR_CUDA.
+ */
+int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int prec, uint32_t k,
+                           const uint32_t *nodes, double *sc_scaled, double *log_scale,
+                           void *stream);
 
 /* Release a handle and its device memory (synchronises the device).  The
  * memory goes back to the library's per-device pool (see below), not to the

@@ -24,7 +24,8 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["cb_api.cu", "cb_lanczos.cu", "cb_tridiag.cu", "cb_combine.cu", "cb_topk.cu",
-              "cb_adjoint.cu", "cb_blocked.cu", "cb_generate.cu"]
+              "cb_adjoint.cu", "cb_blocked.cu", "cb_generate.cu",
+              "cb_subgraph.cu"]
 
 
 def cb_lib_path() -> str:

@@ -73,6 +73,8 @@ def lib():
         L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
         L.cb_graph_generate_er.restype = i32
         L.cb_graph_generate_er.argtypes = [u32, vp, vp, u64, u32, vp, vp, ctypes.POINTER(vp)]
+        L.cb_subgraph_centrality.restype = i32
+        L.cb_subgraph_centrality.argtypes = [vp, u32, u32, i32, u32, vp, vp, vp, vp]
         L.cb_graph_read.restype = i32
         L.cb_graph_read.argtypes = [vp, u32, vp, vp, vp]
         L.cb_graph_num_entries.restype = u64
@@ -150,6 +152,24 @@ def cb_graph_generate_er(n, m_draws, seed, tedges, stream):
                                       len(te), te_buf.ctypes.data, ctypes.c_void_p(stream),
                                       ctypes.byref(out)))
     return out.value
+
+
+def cb_subgraph_centrality(h, inst, m, prec, k, nodes_ptr, sc_ptr, log_scale_ptr, stream):
+    _check(lib().cb_subgraph_centrality(ctypes.c_void_p(h), inst, m, prec, k,
+                                        ctypes.c_void_p(nodes_ptr), ctypes.c_void_p(sc_ptr),
+                                        ctypes.c_void_p(log_scale_ptr), ctypes.c_void_p(stream)))
+
+
+def subgraph_centrality(gs, inst: int, m: int, nodes, prec: int = CB_FP32, stream=None):
+    """(log_scale, sc) with SC(nodes[q]) = (e^A)_ii ~= exp(log_scale) * sc[q] (eq. 3)."""
+    import torch
+
+    nodes = torch.as_tensor(np.asarray(nodes, dtype=np.int64).astype(np.int32), device="cuda")
+    sc = torch.empty(nodes.numel(), dtype=torch.float64, device="cuda")
+    ls = torch.empty(1, dtype=torch.float64, device="cuda")
+    cb_subgraph_centrality(gs.h, inst, m, prec, nodes.numel(), nodes.data_ptr(), sc.data_ptr(),
+                           ls.data_ptr(), _stream_handle(stream))
+    return ls, sc
 
 
 def cb_graph_read(h, r, row_ptr_ptr, col_ptr, stream):

@@ -222,8 +222,11 @@ void free_backwork(BackWork &B);  // cb_adjoint.cu
 // kernel launchers (cb_lanczos.cu).  Range of realisations [r0, r1).  The
 // start vector is 1, or, with start_idx, the indicator of the k distinct
 // node indices start_idx[0..k) (device array) restricted to [0, n_r).
+// start_idx: none (start vector 1), an index set shared by all realisations
+// (k entries), or with per_inst one start node per realisation (e_idx[r-r0]).
 int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
-                cudaStream_t s, const uint32_t *start_idx = nullptr, uint32_t k = 0);
+                cudaStream_t s, const uint32_t *start_idx = nullptr, uint32_t k = 0,
+                bool per_inst = false);
 // tridiagonal exp (cb_tridiag.cu)
 int tridiag_run(cb_graph *h, uint32_t r0, uint32_t r1, int prec, cudaStream_t s);
 // combine (cb_combine.cu)

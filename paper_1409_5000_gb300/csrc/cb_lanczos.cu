@@ -94,13 +94,19 @@ __global__ void __launch_bounds__(kThreads) init_vec_kernel(LArgs a, uint32_t r0
   }
 }
 
-// W_0[idx[q]] = 1 for the start indices inside each realisation's range.
+// W_0[idx[q]] = 1 for the start indices inside each realisation's range
+// (per_inst: realisation r0 + q starts from the single node idx[q]).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) init_indicator_kernel(LArgs a, uint32_t r0,
-                                                                  const uint32_t *idx, uint32_t k) {
+                                                                  const uint32_t *idx, uint32_t k,
+                                                                  bool per_inst) {
   const uint32_t r = r0 + blockIdx.x;
   const InstDesc I = a.inst[r];
   T *w0 = reinterpret_cast<T *>(a.V) + I.node_base;
+  if (per_inst) {
+    if (threadIdx.x == 0 && idx[blockIdx.x] < I.n) w0[idx[blockIdx.x]] = T(1);
+    return;
+  }
   for (uint32_t q = threadIdx.x; q < k; q += blockDim.x) {
     const uint32_t i = idx[q];
     if (i < I.n) w0[i] = T(1);
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) init_indicator_kernel(LArgs a, uint3
 
 __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_t r0, uint32_t r1,
                                                                 uint32_t m, const uint32_t *idx,
-                                                                uint32_t k) {
+                                                                uint32_t k, bool per_inst) {
   const uint32_t ms = a.sc.ms;
   const uint64_t total = (uint64_t)(r1 - r0) * ms;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -122,7 +128,10 @@ __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_
     uint32_t cnt = a.inst[r].n;  // ||start||^2
     if (idx && jj == 0) {
       cnt = 0;
-      for (uint32_t q = 0; q < k; ++q) cnt += (idx[q] < a.inst[r].n);
+      if (per_inst)
+        cnt = idx[r - r0] < a.inst[r].n ? 1u : 0u;
+      else
+        for (uint32_t q = 0; q < k; ++q) cnt += (idx[q] < a.inst[r].n);
     }
     a.sc.scale[o] = (jj == 0 && cnt) ? 1.0 / sqrt((double)cnt) : 0.0;
     if (jj == 0) {
@@ -569,7 +578,7 @@ static void launch_spmv_lanes(int lanes, const LArgs &a, uint32_t j, uint32_t co
 
 template <typename T>
 static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t s,
-                 const uint32_t *start_idx, uint32_t k) {
+                 const uint32_t *start_idx, uint32_t k, bool per_inst) {
   LArgs a;
   a.inst = h->d_inst;
   a.tile_inst = h->d_tile_inst;
@@ -629,10 +638,11 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   int tok = prof_begin(CB_K_INIT, s);
   init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1,
                                                                     start_idx ? T(0) : T(1));
-  if (start_idx) init_indicator_kernel<T><<<r1 - r0, kThreads, 0, s>>>(a, r0, start_idx, k);
+  if (start_idx)
+    init_indicator_kernel<T><<<r1 - r0, kThreads, 0, s>>>(a, r0, start_idx, k, per_inst);
   const uint64_t nsc = (uint64_t)(r1 - r0) * W.sc.ms;
   init_scalars_kernel<<<(uint32_t)((nsc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-      a, r0, r1, m, start_idx, k);
+      a, r0, r1, m, start_idx, k, per_inst);
   prof_end(tok, s);
   for (uint32_t j = 0; j < m; ++j) {
     tok = prof_begin(CB_K_SPMV, s);
@@ -647,9 +657,9 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
 }
 
 int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
-                cudaStream_t s, const uint32_t *start_idx, uint32_t k) {
-  return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k)
-                         : run_t<float>(h, W, r0, r1, m, s, start_idx, k);
+                cudaStream_t s, const uint32_t *start_idx, uint32_t k, bool per_inst) {
+  return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k, per_inst)
+                         : run_t<float>(h, W, r0, r1, m, s, start_idx, k, per_inst);
 }
 
 }  // namespace cb
