@@ -23,6 +23,7 @@
 // node) and every CSR entry (i, j) gets g = P_i . U_j + P_j . U_i, computed
 // in the basis precision (FP32 or FP64).  Realisations share one shift theta* =
 // max_r theta_r; dL/da_e = exp(theta*) * grad[e].
+#include <algorithm>
 #include <cstdlib>
 
 #include "cb_contour.cuh"
@@ -207,12 +208,47 @@ __device__ __forceinline__ double dot4(const double *a, const double *b) {
   return x0.x * y0.x + x0.y * y0.y + x1.x * y1.x + x1.y * y1.y;
 }
 
-// g_e = P_i . U_j + P_j . U_i for every CSR entry e = (i, j) of one SpMV tile.
-// A group of kEdgeLanes lanes shares an edge: lane c takes the 4-value chunks
-// c, c + kEdgeLanes, ... of the four node-major rows, so each row is read as
-// whole 128-byte lines; the partials are summed across the group with a
-// shuffle tree.  Arithmetic in T (FP32 in CB_FP32 mode): FP64 instructions
-// are scarce on GB300 and would bound this kernel.
+// mirror[e] for every CSR entry e = (i, j) of one SpMV tile: the position of
+// (j, i) in row j (rows are sorted; binary search).  An entry without a
+// mirror (asymmetric input) points at itself.
+__global__ void __launch_bounds__(256) bw_mirror_kernel(const InstDesc *inst,
+                                                        const uint32_t *tile_inst,
+                                                        const uint2 *tile_rows,
+                                                        const uint32_t *row_ptr, const uint32_t *col,
+                                                        uint32_t *mirror) {
+  __shared__ uint32_t s_rp[kTileRows + 1];
+  const uint32_t t = blockIdx.x;
+  const InstDesc I = inst[tile_inst[t]];
+  const uint32_t *rp = row_ptr + I.rp_base;
+  const uint32_t *cl = col + I.edge_base;
+  const uint2 tr = tile_rows[t];
+  const uint32_t row0 = tr.x, nrows = tr.y - tr.x;
+  for (uint32_t q = threadIdx.x; q <= nrows; q += blockDim.x) s_rp[q] = rp[row0 + q];
+  __syncthreads();
+  for (uint32_t e = s_rp[0] + threadIdx.x; e < s_rp[nrows]; e += blockDim.x) {
+    uint32_t lo = 0, hi = nrows;  // last lr with s_rp[lr] <= e
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_rp[mid] <= e) lo = mid; else hi = mid;
+    }
+    const uint32_t i = row0 + lo, j = __ldg(cl + e);
+    uint32_t a = rp[j], b = rp[j + 1];  // first position in row j with col >= i
+    while (a < b) {
+      const uint32_t mid = (a + b) >> 1;
+      if (__ldg(cl + mid) < i) a = mid + 1; else b = mid;
+    }
+    mirror[I.edge_base + e] = (a < rp[j + 1] && __ldg(cl + a) == i) ? a : e;
+  }
+}
+
+// The gradient is symmetric: g(i, j) = P_i . U_j + P_j . U_i = g(j, i).  Each
+// undirected edge is computed once, from its upper entry (j >= i, a suffix
+// of the sorted row i), and written to both CSR entries (the lower one
+// through mirror).  A group of kEdgeLanes lanes shares an edge: lane c takes
+// the 4-value chunks c, c + kEdgeLanes, ... of the four node-major rows, so
+// each row is read as whole 128-byte lines; the partials are summed across
+// the group with a shuffle tree.  Arithmetic in T (FP32 in CB_FP32 mode):
+// FP64 instructions are scarce on GB300 and would bound this kernel.
 constexpr uint32_t kEdgeLanes = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, uint32_t mpad,
@@ -220,8 +256,11 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
                                                       const uint32_t *tile_inst,
                                                       const uint2 *tile_rows,
                                                       const uint32_t *row_ptr, const uint32_t *col,
+                                                      const uint32_t *mirror,
                                                       const double *theta_in, float *grad) {
   __shared__ uint32_t s_rp[kTileRows + 1];
+  __shared__ uint32_t s_first[kTileRows];   // first upper entry of each row
+  __shared__ uint32_t s_up[kTileRows + 1];  // prefix of upper-entry counts
   const uint32_t t = blockIdx.x;
   const uint32_t r = tile_inst[t];
   const InstDesc I = inst[r];
@@ -232,30 +271,72 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
   const uint32_t nrows = tr.y - tr.x;
   for (uint32_t q = threadIdx.x; q <= nrows; q += blockDim.x) s_rp[q] = rp[row0 + q];
   __syncthreads();
-  const uint32_t e0 = s_rp[0], e1 = s_rp[nrows];
+  for (uint32_t lr = threadIdx.x; lr < nrows; lr += blockDim.x) {
+    uint32_t a = s_rp[lr], b = s_rp[lr + 1];
+    const uint32_t row = row0 + lr;
+    while (a < b) {
+      const uint32_t mid = (a + b) >> 1;
+      if (__ldg(cl + mid) < row) a = mid + 1; else b = mid;
+    }
+    s_first[lr] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // warp 0: prefix over up to 32 x 8 rows
+    constexpr uint32_t kPer = kTileRows / 32;
+    const uint32_t lane = threadIdx.x, base = lane * kPer;
+    uint32_t c[kPer], sum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q) {
+      const uint32_t lr = base + q;
+      c[q] = lr < nrows ? s_rp[lr + 1] - s_first[lr] : 0u;
+      sum += c[q];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q) {
+      if (base + q <= nrows) s_up[base + q] = run;
+      run += c[q];
+    }
+    if (lane == 31 && nrows == kTileRows) s_up[kTileRows] = run;
+  }
+  __syncthreads();
+  const uint32_t nup = s_up[nrows];
   const bool active = theta_in[r] > -1e307;
   const uint32_t nv = mpad / 4;
   const uint32_t c0 = threadIdx.x % kEdgeLanes;
   constexpr uint32_t kGroups = 256 / kEdgeLanes;
   // the loop bound is uniform across each group, so the shuffles see all lanes
-  for (uint32_t eb = e0; eb < e1; eb += kGroups) {
-    const uint32_t e = eb + threadIdx.x / kEdgeLanes;
+  for (uint32_t ub = 0; ub < nup; ub += kGroups) {
+    const uint32_t u = ub + threadIdx.x / kEdgeLanes;
     T g = T(0);
-    if (active && e < e1) {
-      uint32_t lo = 0, hi = nrows;  // last lr with s_rp[lr] <= e
+    uint32_t e = 0;
+    if (u < nup) {
+      uint32_t lo = 0, hi = nrows;  // s_up[lo] <= u < s_up[hi]
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (s_rp[mid] <= e) lo = mid; else hi = mid;
+        if (s_up[mid] <= u) lo = mid; else hi = mid;
       }
-      const uint64_t i = I.node_base + row0 + lo;
-      const uint64_t j = I.node_base + __ldg(cl + e);
-      const T *Pi = P + i * mpad, *Ui = U + i * mpad, *Pj = P + j * mpad, *Uj = U + j * mpad;
-      for (uint32_t c = c0; c < nv; c += kEdgeLanes)
-        g += dot4(Pi + 4 * c, Uj + 4 * c) + dot4(Pj + 4 * c, Ui + 4 * c);
+      e = s_first[lo] + (u - s_up[lo]);
+      if (active) {
+        const uint64_t i = I.node_base + row0 + lo;
+        const uint64_t j = I.node_base + __ldg(cl + e);
+        const T *Pi = P + i * mpad, *Ui = U + i * mpad, *Pj = P + j * mpad, *Uj = U + j * mpad;
+        for (uint32_t c = c0; c < nv; c += kEdgeLanes)
+          g += dot4(Pi + 4 * c, Uj + 4 * c) + dot4(Pj + 4 * c, Ui + 4 * c);
+      }
     }
     for (uint32_t off = kEdgeLanes / 2; off > 0; off >>= 1)
       g += __shfl_xor_sync(0xffffffffu, g, off, kEdgeLanes);
-    if (c0 == 0 && e < e1) grad[I.edge_base + e] = (float)g;
+    if (c0 == 0 && u < nup) {
+      grad[I.edge_base + e] = (float)g;
+      grad[I.edge_base + mirror[I.edge_base + e]] = (float)g;
+    }
   }
 }
 
@@ -277,7 +358,7 @@ static int backward_t(cb_graph *h, uint32_t m, const uint32_t *idx, uint32_t k, 
                                     B.theta, B.mpad, (T *)B.P, (T *)B.U, log_scale);
   bw_edge_kernel<T><<<h->total_tiles, 256, 0, s>>>((const T *)B.P, (const T *)B.U, B.mpad,
                                                    h->d_inst, h->d_tile_inst, h->d_tile_rows,
-                                                   h->row_ptr, h->col,
+                                                   h->row_ptr, h->col, h->d_mirror,
                                                    B.theta, grad);
   prof_end(tok, s);
   (void)idx;
@@ -303,6 +384,19 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
   int rc = ensure_workspace(h, h->ws, m, prec, s);
   if (rc == CB_OK) rc = ensure_workspace(h, h->ws2, m, prec, s);
   if (rc == CB_OK) rc = ensure_backwork(h, m, prec, s);
+  if (rc == CB_OK && !h->d_mirror) {  // once per handle: the position of each entry's mirror
+    cudaError_t e = dev_alloc_n(&h->d_mirror, std::max<uint64_t>(h->total_nnz, 1));
+    if (e == cudaSuccess && h->total_tiles) {
+      bw_mirror_kernel<<<h->total_tiles, 256, 0, s>>>(h->d_inst, h->d_tile_inst, h->d_tile_rows,
+                                                      h->row_ptr, h->col, h->d_mirror);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      dev_free(h->d_mirror);
+      h->d_mirror = nullptr;
+      rc = cuda_error(e, "adjoint: mirror index");
+    }
+  }
   // the basis from 1 is the forward pass's when an ensemble pass at this m
   // and precision ran last on the handle (same stream order assumed)
   const bool reuse = rc == CB_OK && h->basis_m == m && h->basis_prec == prec &&

@@ -190,6 +190,8 @@ static void free_graph_arrays(cb_graph *h) {
   dev_free(h->d_heavy);
   dev_free(h->d_chunk_heavy);
   dev_free(h->d_fin_inst);
+  dev_free(h->d_mirror);
+  h->d_mirror = nullptr;
   h->col = nullptr;
   h->row_ptr = nullptr;
   h->d_inst = nullptr;

@@ -137,6 +137,8 @@ struct cb_graph {
   cb::HeavyRow *d_heavy = nullptr;
   uint32_t *d_chunk_heavy = nullptr;     // heavy-row index of each chunk
   uint32_t *d_fin_inst = nullptr;        // instance of each finalize tile
+  uint32_t *d_mirror = nullptr;          // per CSR entry (i, j): position of (j, i) in its
+                                         // realisation (built by the first adjoint call)
   // column-blocked format (FP32 SpMV), for realisations with blocked = 1
   uint32_t total_btiles = 0;
   uint64_t total_bseg = 0;               // (tile, column block) segments
