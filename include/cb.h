@@ -174,6 +174,28 @@ int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int prec, uin
                            const uint32_t *nodes, double *sc_scaled, double *log_scale,
                            void *stream);
 
+/*
+ * cb_graph_tune -- pick the group width of the tiled-CSR SpMV (rows of up to
+ * 8 * lanes entries share `lanes` lanes of a warp; longer rows go to a warp,
+ * a CTA, or several CTAs) for this handle by measurement.  The tiled-CSR
+ * kernel serves FP64 mode and FP32 realisations above the column-blocked
+ * kernel's size limit (n > 32 * 16384).  Each candidate 1, 2, 4, 8, 16, 32 is
+ * timed on a 3-step Lanczos run over all realisations (CUDA events, two
+ * repetitions after a warm-up, on a workspace of its own) and the fastest is
+ * kept.  Without a realisation on the tiled-CSR kernel at `prec` nothing is
+ * timed and the current width is reported.  The upload's default comes from
+ * the mean degree.  Results do not depend on the width beyond FP summation
+ * order.  Synchronises `stream`.
+ *   lanes_out  optional host uint32[1]: the width kept.
+ *   ms_out     optional host double[6]: ms per run for each candidate (-1 when not timed).
+ */
+int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_out, void *stream);
+
+/* Set / read the tiled-CSR group width (1, 2, 4, 8, 16 or 32), e.g. from a
+ * cached tuning result.  Setting drops the handle's captured passes. */
+int cb_graph_set_lanes(cb_graph *h, uint32_t lanes);
+uint32_t cb_graph_lanes(const cb_graph *h);
+
 /* Release a handle and its device memory (synchronises the device).  The
  * memory goes back to the library's per-device pool (see below), not to the
  * driver. */
@@ -316,6 +338,23 @@ int cb_profile_read(int kernel, double *total_ms, uint64_t *launches);
  */
 int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx, uint32_t k,
                        float *grad, double *log_scale, void *stream);
+
+/*
+ * cb_scores_backward_budget -- cb_scores_backward under a device-memory
+ * budget.  The adjoint keeps, per realisation, two Krylov bases and the
+ * node-major P and U: about esz * n * (2 (m + 1) + 2 * roundup4(m)) bytes,
+ * esz = 4 (FP32) or 8 (FP64).  When the sum over realisations (plus ~12
+ * bytes per CSR entry) exceeds mem_budget bytes, consecutive realisations
+ * are processed in groups that fit (a single realisation always runs): each
+ * group is copied device-to-device into a temporary handle, its basis from 1
+ * is recomputed there (the forward pass's basis is not reused), and every
+ * group's gradient is rescaled to the common shift max_r theta_r.  The
+ * result equals cb_scores_backward's up to FP32 rounding of that rescaling.
+ * Arguments as cb_scores_backward; synchronises `stream`.
+ */
+int cb_scores_backward_budget(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx,
+                              uint32_t k, float *grad, double *log_scale, size_t mem_budget,
+                              void *stream);
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *cb_last_error(void);

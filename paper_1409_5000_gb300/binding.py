@@ -73,6 +73,14 @@ def lib():
         L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
         L.cb_graph_generate_er.restype = i32
         L.cb_graph_generate_er.argtypes = [u32, vp, vp, u64, u32, vp, vp, ctypes.POINTER(vp)]
+        L.cb_scores_backward_budget.restype = i32
+        L.cb_scores_backward_budget.argtypes = [vp, u32, i32, vp, u32, vp, vp, ctypes.c_size_t, vp]
+        L.cb_graph_tune.restype = i32
+        L.cb_graph_tune.argtypes = [vp, i32, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double), vp]
+        L.cb_graph_set_lanes.restype = i32
+        L.cb_graph_set_lanes.argtypes = [vp, u32]
+        L.cb_graph_lanes.restype = u32
+        L.cb_graph_lanes.argtypes = [vp]
         L.cb_subgraph_centrality.restype = i32
         L.cb_subgraph_centrality.argtypes = [vp, u32, u32, i32, u32, vp, vp, vp, vp]
         L.cb_graph_read.restype = i32
@@ -152,6 +160,31 @@ def cb_graph_generate_er(n, m_draws, seed, tedges, stream):
                                       len(te), te_buf.ctypes.data, ctypes.c_void_p(stream),
                                       ctypes.byref(out)))
     return out.value
+
+
+def cb_scores_backward_budget(h, m, prec, topk_idx_ptr, k, grad_ptr, log_scale_ptr, mem_budget,
+                              stream):
+    _check(lib().cb_scores_backward_budget(ctypes.c_void_p(h), m, prec, ctypes.c_void_p(topk_idx_ptr),
+                                           k, ctypes.c_void_p(grad_ptr),
+                                           ctypes.c_void_p(log_scale_ptr), mem_budget,
+                                           ctypes.c_void_p(stream)))
+
+
+def cb_graph_tune(h, prec, stream):
+    """Returns (lanes kept, [ms per candidate 1, 2, 4, 8, 16, 32; -1 = not timed])."""
+    lanes = ctypes.c_uint32()
+    ms = (ctypes.c_double * 6)()
+    _check(lib().cb_graph_tune(ctypes.c_void_p(h), prec, ctypes.byref(lanes), ms,
+                               ctypes.c_void_p(stream)))
+    return int(lanes.value), list(ms)
+
+
+def cb_graph_set_lanes(h, lanes):
+    _check(lib().cb_graph_set_lanes(ctypes.c_void_p(h), lanes))
+
+
+def cb_graph_lanes(h):
+    return int(lib().cb_graph_lanes(ctypes.c_void_p(h)))
 
 
 def cb_subgraph_centrality(h, inst, m, prec, k, nodes_ptr, sc_ptr, log_scale_ptr, stream):

@@ -645,6 +645,83 @@ static void drop_graphs(cb_graph *h) {
   h->graphs.clear();
 }
 
+static bool valid_lanes(uint32_t g) {
+  return g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32;
+}
+
+CB_API int cb_graph_set_lanes(cb_graph *h, uint32_t lanes) {
+  if (!h) return set_error(CB_ERR_ARG, "cb_graph_set_lanes: null handle");
+  if (!valid_lanes(lanes)) return set_error(CB_ERR_ARG, "cb_graph_set_lanes: lanes must be 1, 2, 4, 8, 16 or 32");
+  if (h->lanes != (int)lanes) {
+    h->lanes = (int)lanes;
+    drop_graphs(h);  // captured passes hold the old kernel choice
+  }
+  return CB_OK;
+}
+
+CB_API uint32_t cb_graph_lanes(const cb_graph *h) { return h ? (uint32_t)h->lanes : 0u; }
+
+// Times a short Lanczos run (kProbe steps over all realisations, twice, on a
+// workspace of its own) for every group width of the tiled-CSR SpMV and keeps
+// the fastest.  Realisations on the column-blocked kernel are timed too but
+// do not depend on the width.
+CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_out, void *stream) {
+  if (!h) return set_error(CB_ERR_ARG, "cb_graph_tune: null handle");
+  if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_graph_tune: bad precision");
+  static const uint32_t kCand[6] = {1, 2, 4, 8, 16, 32};
+  for (int c = 0; ms_out && c < 6; ++c) ms_out[c] = -1.0;
+  bool any_csr = prec == CB_FP64 || h->total_btiles == 0;
+  for (uint32_t r = 0; r < h->n_inst && !any_csr; ++r) any_csr = !h->inst[r].blocked;
+  if (!any_csr) {  // every realisation runs the column-blocked kernel: nothing to choose
+    if (lanes_out) *lanes_out = (uint32_t)h->lanes;
+    return CB_OK;
+  }
+  constexpr uint32_t kProbe = 3;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Workspace W;
+  int rc = ensure_workspace(h, W, kProbe, prec, s);
+  if (rc != CB_OK) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int keep = h->lanes;
+  int best = keep;
+  double best_ms = 1e300;
+  for (int c = 0; c < 6 && e == cudaSuccess && rc == CB_OK; ++c) {
+    h->lanes = (int)kCand[c];
+    rc = lanczos_run(h, W, 0, h->n_inst, kProbe, prec, s);  // warm-up
+    if (rc == CB_OK) e = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 2 && rc == CB_OK && e == cudaSuccess; ++rep)
+      rc = lanczos_run(h, W, 0, h->n_inst, kProbe, prec, s);
+    if (rc == CB_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (rc == CB_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (rc == CB_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == CB_OK && e == cudaSuccess) {
+      if (ms_out) ms_out[c] = ms / 2.0;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = (int)kCand[c];
+      }
+    }
+  }
+  h->lanes = best;
+  if (best != keep) drop_graphs(h);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  free_workspace(W);
+  if (rc != CB_OK) {
+    h->lanes = keep;
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    h->lanes = keep;
+    return cuda_error(e, "cb_graph_tune");
+  }
+  if (lanes_out) *lanes_out = (uint32_t)best;
+  return CB_OK;
+}
+
 CB_API int cb_graph_free(cb_graph *h) {
   if (!h) return set_error(CB_ERR_ARG, "cb_graph_free: null handle");
   cudaError_t e = cudaDeviceSynchronize();

@@ -1,0 +1,67 @@
+"""Tiled-CSR group widths: parity at every width, the tuner, the cache (needs a GB300)."""
+import numpy as np
+import pytest
+
+import oracle.communicability as oc
+from paper_1409_5000_gb300 import synth, tune
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1409_5000_gb300 import binding
+
+    binding.lib()
+    return binding
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_every_width_matches_oracle(B, lanes):
+    """FP64 (always the tiled-CSR kernel) on a heavy-tailed graph and an ER graph."""
+    graphs = [synth.ba(30_000, 6, 31), synth.er(20_000, 10.0 / 20_000, 32)]
+    th_o, S_o = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], 20)
+    with B.GraphSet(graphs) as gs:
+        B.cb_graph_set_lanes(gs.h, lanes)
+        assert B.cb_graph_lanes(gs.h) == lanes
+        ls, S = B.ensemble_scores(gs, 20, B.CB_FP64)
+        parity.assert_scores(float(ls.item()), S.cpu().numpy(), th_o, S_o, "fp64")
+
+
+def test_tuner_keeps_fastest(B):
+    graphs = [synth.ba(200_000, 8, 41)]
+    with B.GraphSet(graphs) as gs:
+        lanes, ms = B.cb_graph_tune(gs.h, B.CB_FP64, 0)
+        assert lanes in (1, 2, 4, 8, 16, 32) and B.cb_graph_lanes(gs.h) == lanes
+        timed = [x for x in ms if x >= 0]
+        assert len(timed) == 6
+        assert ms[[1, 2, 4, 8, 16, 32].index(lanes)] == min(timed)
+
+
+def test_tuner_noop_when_all_blocked(B):
+    with B.GraphSet([synth.er(5_000, 0.002, 5)]) as gs:
+        before = B.cb_graph_lanes(gs.h)
+        lanes, ms = B.cb_graph_tune(gs.h, B.CB_FP32, 0)
+        assert lanes == before and all(x == -1.0 for x in ms)
+
+
+def test_autotune_cache(B, tmp_path):
+    path = str(tmp_path / "tune.json")
+    graphs = [synth.er(50_000, 12.0 / 50_000, 51)]
+    with B.GraphSet(graphs) as gs:
+        lanes, cached = tune.autotune(gs, B.CB_FP64, graphs, path)
+        assert not cached and lanes == B.cb_graph_lanes(gs.h)
+    with B.GraphSet(graphs) as gs:
+        B.cb_graph_set_lanes(gs.h, 1 if lanes != 1 else 2)
+        lanes2, cached = tune.autotune(gs, B.CB_FP64, graphs, path)
+        assert cached and lanes2 == lanes == B.cb_graph_lanes(gs.h)
+
+
+def test_set_lanes_errors(B):
+    with B.GraphSet([synth.er(100, 0.05, 1)]) as gs:
+        with pytest.raises(B.CBError):
+            B.cb_graph_set_lanes(gs.h, 3)
