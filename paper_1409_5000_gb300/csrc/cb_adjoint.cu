@@ -416,3 +416,103 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
                          : backward_t<float>(h, m, topk_idx, k, grad, log_scale, s);
   return rc;
 }
+
+namespace cb {
+namespace {
+
+__global__ void scale_grad_kernel(float *g, uint64_t n, const double *ls_group,
+                                  const double *ls_all) {
+  const float f = (float)exp(*ls_group - *ls_all);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    g[i] *= f;
+}
+
+__global__ void max_shift_kernel(const double *ls, uint32_t n, double *out) {
+  if (threadIdx.x == 0) {
+    double t = ls[0];
+    for (uint32_t q = 1; q < n; ++q) t = fmax(t, ls[q]);
+    *out = t;
+  }
+}
+
+}  // namespace
+}  // namespace cb
+
+// Working set of the adjoint for realisation r: two (m + 1)-vector bases and
+// the node-major P and U, plus the copy of its graph and format in a group
+// handle (about 12 bytes per CSR entry).
+static uint64_t adjoint_bytes(const cb::InstDesc &I, uint64_t nnz, uint32_t m, int prec) {
+  const uint64_t esz = prec == CB_FP64 ? 8 : 4;
+  const uint64_t npad = (I.n + cb::kNodeAlign - 1) / cb::kNodeAlign * cb::kNodeAlign;
+  const uint64_t mpad = (m + 3) / 4 * 4;
+  return esz * npad * (2 * (uint64_t)(m + 1) + 2 * mpad) + 12 * nnz + 8ull * I.n;
+}
+
+CB_API int cb_scores_backward_budget(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx,
+                                     uint32_t k, float *grad, double *log_scale,
+                                     size_t mem_budget, void *stream) {
+  if (!h || !topk_idx || !grad || !log_scale)
+    return set_error(CB_ERR_ARG, "cb_scores_backward_budget: null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const uint32_t N = h->n_inst;
+  std::vector<uint64_t> nnz(N), need(N);
+  uint64_t total = 0;
+  for (uint32_t r = 0; r < N; ++r) {
+    nnz[r] = (r + 1 < N ? h->inst[r + 1].edge_base : h->total_nnz) - h->inst[r].edge_base;
+    need[r] = adjoint_bytes(h->inst[r], nnz[r], m, prec);
+    total += need[r];
+  }
+  if (total <= mem_budget || N == 1)
+    return cb_scores_backward(h, m, prec, topk_idx, k, grad, log_scale, stream);
+  // groups of consecutive realisations whose working set fits (at least one each)
+  std::vector<uint32_t> starts;
+  uint64_t acc = 0;
+  for (uint32_t r = 0; r < N; ++r) {
+    if (starts.empty() || acc + need[r] > mem_budget) {
+      starts.push_back(r);
+      acc = 0;
+    }
+    acc += need[r];
+  }
+  starts.push_back(N);
+  const uint32_t G = (uint32_t)starts.size() - 1;
+  double *d_ls = nullptr;  // per-group shift, then the common one
+  cudaError_t e = dev_alloc_n(&d_ls, G + 1);
+  if (e != cudaSuccess) return cuda_error(e, "cb_scores_backward_budget: allocate");
+  int rc = CB_OK;
+  for (uint32_t g = 0; g < G && rc == CB_OK; ++g) {
+    const uint32_t r0 = starts[g], r1 = starts[g + 1];
+    std::vector<uint32_t> vn(r1 - r0);
+    std::vector<const uint32_t *> vrp(r1 - r0), vcol(r1 - r0);
+    for (uint32_t r = r0; r < r1; ++r) {
+      vn[r - r0] = h->inst[r].n;
+      vrp[r - r0] = h->row_ptr + h->inst[r].rp_base;
+      vcol[r - r0] = h->col + h->inst[r].edge_base;
+    }
+    cb_graph *v = nullptr;
+    rc = cb_graph_upload(r1 - r0, vn.data(), nnz.data() + r0, vrp.data(), vcol.data(),
+                         CB_DEVICE_PTRS, stream, &v);
+    if (rc != CB_OK) break;
+    rc = cb_scores_backward(v, m, prec, topk_idx, k, grad + h->inst[r0].edge_base, d_ls + g, stream);
+    if (rc == CB_OK) rc = cuda_error(cudaStreamSynchronize(s), "cb_scores_backward_budget");
+    const int rf = cb_graph_free(v);
+    if (rc == CB_OK) rc = rf;
+  }
+  if (rc == CB_OK) {
+    max_shift_kernel<<<1, 32, 0, s>>>(d_ls, G, d_ls + G);
+    for (uint32_t g = 0; g < G; ++g) {
+      const uint64_t e0 = h->inst[starts[g]].edge_base;
+      const uint64_t e1 = starts[g + 1] < N ? h->inst[starts[g + 1]].edge_base : h->total_nnz;
+      if (e1 > e0)
+        scale_grad_kernel<<<(uint32_t)std::min<uint64_t>((e1 - e0 + 255) / 256, 152 * 8), 256, 0, s>>>(
+            grad + e0, e1 - e0, d_ls + g, d_ls + G);
+    }
+    e = cudaMemcpyAsync(log_scale, d_ls + G, 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    rc = cuda_error(e, "cb_scores_backward_budget: combine");
+  }
+  dev_free(d_ls);
+  return rc;
+}

@@ -173,6 +173,26 @@ def test_forward_basis_reuse(B, monkeypatch):
             assert np.array_equal(g.cpu().numpy(), g0), between
 
 
+@pytest.mark.parametrize("budget", [1, 40 << 20])
+def test_memory_budget_groups(B, budget):
+    """A budget below the working set runs the adjoint over groups of
+    realisations (one per group at budget 1) in temporary handles; the result
+    is the unbudgeted gradient up to the FP32 rounding of the rescaling."""
+    ens = synth.er_ensemble([20_000, 60_000, 5_000, 40_000, 30_000], 12.0, 20, 8, config=506)
+    nodes = torch.as_tensor(np.asarray(ens.target, dtype=np.int32), device="cuda")
+    with B.GraphSet(ens.graphs) as gs:
+        ls0, g0 = B.scores_backward(gs, 25, [int(x) for x in ens.target])
+        g = torch.empty_like(g0)
+        ls = torch.empty(1, dtype=torch.float64, device="cuda")
+        B.cb_scores_backward_budget(gs.h, 25, 0, nodes.data_ptr(), nodes.numel(), g.data_ptr(),
+                                    ls.data_ptr(), budget, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert float(ls.item()) == float(ls0.item())
+        a, b = g.cpu().numpy().astype(np.float64), g0.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
+        assert np.array_equal(a == 0, b == 0)
+
+
 def test_backward_argument_errors(B):
     g = synth.er(100, 0.05, 1)
     with B.GraphSet([g]) as gs:
