@@ -188,6 +188,21 @@ def cpu_oracle_sample(ens, m, budget_s=15.0, max_inst=None, want=None):
     return units / t_tot, done, t_tot, results
 
 
+def combine_ranks(ms, units, dist=None, device="cpu"):
+    """Whole-job figures over ranks: the slowest rank's ms per step, and the
+    units all ranks processed per step divided by it."""
+    if dist is None:
+        return ms, units / (ms * 1e-3)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(u.item()) / (ms * 1e-3)
+
+
 def run_reference(args, ens, desc, rank, world):
     if rank != 0:
         return
@@ -294,11 +309,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms * 1e-3)
+    ms, value = combine_ranks(ms, units, dist, dev)
 
     # per-kernel times (CUDA events around each launch, same stream), separate pass
     B.cb_profile_enable(1)
