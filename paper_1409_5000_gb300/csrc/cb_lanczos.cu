@@ -512,19 +512,25 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j,
   __shared__ double s_red[32];
   const uint32_t t = fin_off + blockIdx.x;
   const uint32_t r = a.fin_inst[t];
-  if (j >= a.sc.meff[r]) return;
   const InstDesc &I = a.inst[r];
   const uint32_t ms = a.sc.ms;
   T *Vb = reinterpret_cast<T *>(a.V);
   const T *x = Vb + (uint64_t)j * a.vs + I.node_base;
   T *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
-  const T coef = (T)(a.sc.alpha[r * ms + j] * a.sc.scale[r * ms + j]);
   const uint32_t i0 = (t - I.fin_base) * kFinRows + 8 * threadIdx.x;
-  T acc = T(0);
-  if (i0 + 8 <= I.n) {
-    T u[8], v[8];
+  const bool full = i0 + 8 <= I.n;
+  // the vector loads go out before the scalars they do not depend on (the
+  // CTA's latency chain is most of its lifetime); a finished realisation
+  // only reads them
+  T u[8], v[8];
+  if (full) {
     Vec8<T>::load(out + i0, u);
     Vec8<T>::load(x + i0, v);
+  }
+  if (j >= a.sc.meff[r]) return;
+  const T coef = (T)(a.sc.alpha[r * ms + j] * a.sc.scale[r * ms + j]);
+  T acc = T(0);
+  if (full) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       u[q] -= coef * v[q];
