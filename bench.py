@@ -95,7 +95,7 @@ def _kernel_sources_hash():
     with open(os.path.join(csrc, "cb_lanczos.cu")) as f:
         lz = f.read()
     parts = []
-    a = lz.index("__device__ __forceinline__ void cp_async16")
+    a = lz.index("// mbarrier and bulk-copy helpers")
     b = lz.index("\n}\n", lz.index("bspmv_kernel(LArgs a"))
     parts.append(lz[a:b])
     a = lz.index("__device__ __forceinline__ T row_epilogue")

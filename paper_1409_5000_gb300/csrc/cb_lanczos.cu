@@ -148,7 +148,7 @@ __device__ __forceinline__ void finish_alpha(const LArgs &a, uint32_t r, uint32_
   const double alpha = a.sc.scale[r * ms + j] * total;
   a.sc.alpha[r * ms + j] = alpha;
   if (!isfinite(alpha)) {
-    a.sc.status[r] = CB_ERR_NONFINITE;
+    if (a.sc.status[r] == CB_OK) a.sc.status[r] = CB_ERR_NONFINITE;
     a.sc.meff[r] = j;  // stop; this realisation is reported as failed
   }
 }
@@ -328,32 +328,49 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
 // (u = scale_j A W_j - beta_{j-1} scale_{j-1} W_{j-1}, alpha_j partial), but
 // every gather of W_j is a shared-memory load: the CTA walks the column
 // blocks of its tile, double-buffering each block of W_j into shared memory
-// with cp.async while the previous block is consumed.  Thread i owns rows
+// with one bulk copy (cp.async.bulk, completion on an mbarrier) while the
+// previous block is consumed.  Thread i owns rows
 // i + kBThreads k (k = 0..15) of the tile and accumulates them in shared memory
 // (slot-major, so the accumulator traffic is conflict-free); every row has a
 // single writer, so the result is deterministic.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+// mbarrier and bulk-copy helpers (shared-window addresses).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
-
-// Stage x[b*kBCol, min((b+1)*kBCol, n)) into dst (x is 128-byte aligned).
-__device__ __forceinline__ void stage_block(float *dst, const float *x, uint32_t n, uint32_t b) {
-  const uint32_t lo = b * kBCol;
-  const uint32_t len = min(kBCol, n - lo);
-  const uint32_t n4 = len >> 2;
-  for (uint32_t q = threadIdx.x; q < n4; q += kBThreads) cp_async16(dst + 4 * q, x + lo + 4 * q);
-  for (uint32_t q = 4 * n4 + threadIdx.x; q < len; q += kBThreads) cp_async4(dst + q, x + lo + q);
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete; false after the limit.
+constexpr uint32_t kSpinLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// One bulk copy global -> shared whose bytes complete on `bar` (16-byte
+// aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // two column blocks of W_j (each followed by its zero word), then
@@ -368,6 +385,10 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   __shared__ uint32_t s_long[kBTileRows / 32];    // bitmap of long rows
   __shared__ double s_red[32];
   __shared__ float s_rowsum[32];
+  __shared__ __align__(8) uint64_t s_full[2];     // block of W_j landed in buffer p
+  __shared__ uint32_t s_done[2];                  // warps finished with buffer p
+  __shared__ uint32_t s_issued[2];                // copies issued into buffer p
+  __shared__ int s_abort;
   const uint32_t t = btile_off + blockIdx.x;
   const uint32_t r = a.btile_inst[t];
   if (j >= a.sc.meff[r]) return;
@@ -385,7 +406,14 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
 
   for (uint32_t q = tid; q < kBRowsPerThread * kBThreads; q += kBThreads) sacc[q] = 0.f;
   for (uint32_t q = tid; q < kBTileRows / 32; q += kBThreads) s_long[q] = 0u;
-  if (tid < 2) xs[tid * kBBuf + kBPadCol] = 0.f;  // the padding elements read these
+  if (tid < 2) {
+    xs[tid * kBBuf + kBPadCol] = 0.f;  // the padding elements read these
+    mbar_init(&s_full[tid], 1);
+    s_done[tid] = 0;
+    s_issued[tid] = 0;
+  }
+  if (tid == 0) s_abort = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   const uint32_t lp0 = a.blong_ptr[t], lp1 = a.blong_ptr[t + 1];
   for (uint32_t q = lp0 + tid; q < lp1; q += kBThreads) {
@@ -411,8 +439,24 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
       cvA[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * u));
       svA[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * u));
     }
-  stage_block(xs, x, I.n, 0);
-  cp_async_commit();
+  // Column block b of W_j goes to buffer b & 1 by one bulk copy that
+  // completes on s_full[b & 1].  No CTA-wide barrier per block: each warp
+  // waits only for the block it needs, and the last warp to finish with a
+  // buffer issues the copy of block b + 2 into it, so warps drift apart by up
+  // to a block instead of all waiting for the slowest at every block.
+  const uint32_t n_cols = I.n;
+  auto block_bytes = [&](uint32_t b) -> uint32_t {
+    const uint32_t len = min(kBCol, n_cols - b * kBCol);
+    return ((len + 3u) & ~3u) * 4u;  // whole 16-byte units (reads up to 3 floats of padding)
+  };
+  if (tid == 0) {
+    for (uint32_t b = 0; b < 2 && b < nb; ++b) {
+      mbar_expect_tx(&s_full[b], block_bytes(b));
+      bulk_g2s(xs + b * kBBuf, x + (uint64_t)b * kBCol, block_bytes(b), &s_full[b]);
+      s_issued[b] = 1;
+    }
+  }
+  bool aborted = false;
   for (uint32_t b = 0; b < nb; ++b) {
     uint64_t my1 = 0;
     uint32_t ns1 = 0;
@@ -420,13 +464,11 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
       const uint64_t nseg = sbase + b + 1;
       my1 = a.bwstart[nseg * 32 + warp] + 4 * lane;
       ns1 = a.bwlen[nseg * 32 + warp] >> 2;
-      stage_block(xs + ((b + 1) & 1) * kBBuf, x, I.n, b + 1);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
     }
-    __syncthreads();
+    if (!mbar_wait(&s_full[b & 1], (b >> 1) & 1u)) {
+      aborted = true;  // the copy never landed: give up on this tile
+      break;
+    }
     const float *cur = xs + (b & 1) * kBBuf;
     float *mine = sacc + tid;
     const uint32_t nr = (ns + 3) >> 2;
@@ -469,8 +511,25 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     }
     my = my1;
     ns = ns1;
-    __syncthreads();  // the buffer of block b is refilled at iteration b + 1
+    // this warp is done with buffer b & 1; the last warp refills it with block b + 2
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const uint32_t p = b & 1;
+      if (atomicAdd(&s_done[p], 1u) == kBThreads / 32 - 1) {
+        s_done[p] = 0;
+        if (b + 2 < nb) {
+          __threadfence_block();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect_tx(&s_full[p], block_bytes(b + 2));
+          bulk_g2s(xs + p * kBBuf, x + (uint64_t)(b + 2) * kBCol, block_bytes(b + 2), &s_full[p]);
+          s_issued[p] += 1;
+        }
+      }
+    }
   }
+  if (aborted) s_abort = 1;
+  __syncthreads();  // s_long and s_abort complete; sacc rows are per thread
 
   float acc = 0.f;
 #pragma unroll 4
@@ -498,7 +557,16 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     }
     __syncthreads();
   }
-  const double part = block_sum_to_double<float>(acc, s_red);
+  double part = block_sum_to_double<float>(acc, s_red);
+  if (tid == 0) {
+    if (s_abort) {  // a block never arrived: this step of the realisation fails
+      a.sc.status[r] = CB_ERR_TIMEOUT;
+      part = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    // every copy issued into a buffer has landed before the CTA ends (bounded)
+    for (int p = 0; p < 2; ++p)
+      if (s_issued[p]) mbar_wait(&s_full[p], (s_issued[p] - 1) & 1u);
+  }
   double total;
   if (arrive_and_reduce(I.bspmv, t - I.btile_base, r, part, a.red, &total))
     finish_alpha<float>(a, r, j, total);
