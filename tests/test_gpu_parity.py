@@ -295,6 +295,19 @@ def test_column_blocked_matches_tiled_csr(B, monkeypatch):
     parity.assert_scores(tb, yb, th_o, y_o, "fp32")
 
 
+@pytest.mark.parametrize("n", [16_384, 16_385, 32_771, 49_152])
+def test_column_block_boundaries(B, n):
+    """n at and just past multiples of the 16384-entry column block: the last
+    block's bulk copy is rounded up to whole 16-byte units (a 1-entry block
+    copies 4 floats), and a tile's row range ends exactly on a block edge.
+    Ensemble of the boundary size with a smaller realisation, FP32 vs oracle."""
+    graphs = [synth.er(n, 10.0 / n, 60 + n % 97), synth.er(5_000, 0.002, 61)]
+    th_o, S_o = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], 20)
+    with B.GraphSet(graphs) as gs:
+        ls, S = B.ensemble_scores(gs, 20, B.CB_FP32)
+        parity.assert_scores(float(ls.item()), S.cpu().numpy(), th_o, S_o, "fp32")
+
+
 def test_unsorted_rows_rejected(B):
     """The column-blocked format needs each row sorted: an unsorted row is an
     argument error at upload, not a silent miscount."""
