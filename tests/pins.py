@@ -298,7 +298,47 @@ def check_subgraph_centrality(mod):
     assert rel(np.exp(th) * c0, dense[nodes]) < 1e-10
 
 
+def check_restarted(mod):
+    """Restarted Lanczos (the paper's ref [10]): one cycle is the plain
+    m-step approximation; the cycles converge to e^A 1 (dense form and
+    closed forms); a cycle whose start vector spans an invariant subspace
+    makes the result exact."""
+    g = synth.er(60, 0.1, 77)
+    gg = (g.n, g.row_ptr, g.col)
+    ref = mod.total_communicability_dense(*gg)
+    th0, y0, _ = mod.krylov_expv(*gg, 6)
+    th1, y1, run = mod.krylov_expv_restarted(*gg, 6, 1)
+    assert run == 1 and abs(th0 - th1) < 1e-13 * th0 and rel(y1, y0) < 1e-13
+    errs = []
+    for cyc in (1, 2, 3, 4, 6):
+        th, y, run = mod.krylov_expv_restarted(*gg, 5, cyc)
+        assert run == cyc
+        errs.append(rel(np.exp(th) * y, ref))
+    assert errs[0] > 1e-3 and all(b < 1e-2 * a for a, b in zip(errs[:3], errs[1:4])), errs
+    assert errs[-1] < 1e-12, errs
+    b = synth.ba(400, 3, 11)
+    bb = (b.n, b.row_ptr, b.col)
+    th, y, _ = mod.krylov_expv_restarted(*bb, 8, 4)
+    assert rel(np.exp(th) * y, mod.total_communicability_dense(*bb)) < 1e-12
+    # closed forms: path (m = 2) and star (m = 1) need many cycles
+    th, y, _ = mod.krylov_expv_restarted(*graph(9, path(9)), 2, 8)
+    assert rel(np.exp(th) * y, path_closed_form(9)) < 1e-12
+    th, y, _ = mod.krylov_expv_restarted(*graph(7, bipartite(1, 6)), 1, 20)
+    assert rel(np.exp(th) * y, bipartite_closed_form(1, 6)) < 1e-12
+    th, y, _ = mod.krylov_expv_restarted(*graph(7, bipartite(3, 4)), 3, 6)
+    assert rel(np.exp(th) * y, bipartite_closed_form(3, 4)) < 1e-12
+    # 1 is an eigenvector of a regular graph: the first cycle breaks down, exact
+    th, y, run = mod.krylov_expv_restarted(*graph(7, complete(7)), 3, 5)
+    assert run == 1 and rel(np.exp(th) * y, np.full(7, math.exp(6))) < 1e-14
+    # a start vector other than 1 (an indicator): column 0 of e^A
+    e0 = np.zeros(g.n)
+    e0[0] = 1.0
+    th, y, _ = mod.krylov_expv_restarted(*gg, 6, 6, b=e0)
+    col0 = sla.expm(mod.dense_adjacency(*gg))[:, 0]
+    assert np.max(np.abs(np.exp(th) * y - col0)) < 1e-12 * np.max(col0)
+
+
 ALL_CHECKS = [check_closed_forms_dense, check_closed_forms_krylov, check_disjoint_union,
               check_walk_counts, check_library_expm, check_invariants, check_krylov_converges,
               check_lanczos_relation, check_tridiag, check_ensemble, check_topk,
-              check_subgraph_centrality]
+              check_subgraph_centrality, check_restarted]

@@ -51,6 +51,14 @@ MUTATIONS = [
     ("c0.append(float(c[0]))", "c0.append(float(c[-1]))"),
     # sub-graph centrality: start vector on the wrong node
     ("b[int(i)] = 1.0", "b[(int(i) + 1) % n] = 1.0"),
+    # restarted Krylov: coupling above instead of below the diagonal
+    ("H[o, o - 1] = couple[i - 1]", "H[o - 1, o] = couple[i - 1]"),
+    # restarted Krylov: coupling with the wrong residual norm
+    ("couple.append(beta[m - 1])", "couple.append(beta[m - 2])"),
+    # restarted Krylov: next cycle restarts from the last kept vector
+    ("v = V[m]\n", "v = V[m - 1]\n"),
+    # restarted Krylov: first row instead of first column of exp(H)
+    ("c = expm_taylor(H - theta * np.eye(K))[:, 0]", "c = expm_taylor(H - theta * np.eye(K))[0, :]"),
 ]
 
 
