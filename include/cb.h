@@ -63,6 +63,7 @@ extern "C" {
 /* largest k accepted by cb_topk */
 #define CB_MAX_TOPK 4096
 #define CB_MAX_SC_NODES 1024
+#define CB_MAX_CYCLES 1024 /* restart cycles of cb_ensemble_scores_restarted */
 
 typedef struct cb_graph cb_graph;
 
@@ -257,6 +258,38 @@ int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, double 
  */
 int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out, double *S,
                        double *log_scale, cb_inst_report *rep, void *stream);
+
+/*
+ * cb_ensemble_scores_restarted -- eq. 5, with every realisation's e^A 1
+ * evaluated by the restarted Lanczos method of the paper's Krylov reference
+ * ([10], Afanasjew, Eiermann, Ernst & Guettel 2008): `cycles` cycles of m
+ * steps, each started from the last Lanczos vector of the one before, so
+ * that the basis held on the device is m + 1 vectors for any total depth
+ * cycles * m.  After k cycles the approximation is
+ *   e^A 1 ~= beta0 [V_1 ... V_k] exp(H_k) e1,
+ * H_k block lower bidiagonal: the cycles' tridiagonal matrices T_i on the
+ * diagonal, the residual norm of cycle i coupling the first row of block
+ * i + 1 to the last column of block i.  exp(H_k) e1 is evaluated block by
+ * block with the contour rule of cb_communicability (partial fractions).
+ *   m          1 <= m <= CB_MAX_M, the cycle length.
+ *   cycles     1 <= cycles <= CB_MAX_CYCLES.  A realisation whose cycle
+ *              breaks down (invariant Krylov subspace) stops there; its
+ *              result is then exact.  cycles = 1 is cb_ensemble_scores.
+ *   prec, n_out, S, log_scale   as cb_ensemble_scores; log_scale is the
+ *              largest shift, each realisation's shift being the largest
+ *              lambda_max(T_i) of its cycles.
+ *   rep        optional host cb_inst_report[N]: m_eff = Lanczos steps over
+ *              all cycles, beta_last = the last residual norm computed.
+ * Accuracy: very short cycles (m <= 2) over many cycles amplify the contour
+ * rule's error (H_k is far from normal); m >= 4 keeps FP64 results within
+ * about 1e-12 of the exact block form.
+ * Synchronous.  Temporary device memory: 8 bytes per node (padded) plus
+ * 16 (cycles m + 14) bytes per realisation; the call overwrites the
+ * handle's forward basis (cb_scores_backward recomputes it).
+ */
+int cb_ensemble_scores_restarted(cb_graph *h, uint32_t m, uint32_t cycles, int prec,
+                                 uint32_t n_out, double *S, double *log_scale,
+                                 cb_inst_report *rep, void *stream);
 
 /*
  * cb_topk -- indices and values of the k largest entries of S ("the

@@ -22,7 +22,7 @@ from ._build import cb_lib_path, INCLUDE
 CB_OK, CB_ERR_ARG, CB_ERR_CUDA, CB_ERR_OOM, CB_ERR_TIMEOUT, CB_ERR_NONFINITE, CB_ERR_STATE = range(7)
 CB_FP32, CB_FP64 = 0, 1
 CB_VALIDATE, CB_DEVICE_PTRS = 1, 2
-CB_MAX_M, CB_MAX_TOPK = 128, 4096
+CB_MAX_M, CB_MAX_TOPK, CB_MAX_CYCLES = 128, 4096, 1024
 
 
 class CBError(RuntimeError):
@@ -63,6 +63,8 @@ def lib():
         L.cb_communicability.argtypes = [vp, u32, u32, i32, vp, vp, vp, vp]
         L.cb_ensemble_scores.restype = i32
         L.cb_ensemble_scores.argtypes = [vp, u32, i32, u32, vp, vp, vp, vp]
+        L.cb_ensemble_scores_restarted.restype = i32
+        L.cb_ensemble_scores_restarted.argtypes = [vp, u32, u32, i32, u32, vp, vp, vp, vp]
         L.cb_topk.restype = i32
         L.cb_topk.argtypes = [vp, u32, u32, vp, vp, vp]
         L.cb_last_error.restype = ctypes.c_char_p
@@ -250,6 +252,13 @@ def cb_ensemble_scores(h, m, prec, n_out, S_ptr, log_scale_ptr, report, stream):
                                     ctypes.c_void_p(log_scale_ptr), rep, ctypes.c_void_p(stream)))
 
 
+def cb_ensemble_scores_restarted(h, m, cycles, prec, n_out, S_ptr, log_scale_ptr, report, stream):
+    rep = ctypes.c_void_p(ctypes.addressof(report)) if report is not None else None
+    _check(lib().cb_ensemble_scores_restarted(ctypes.c_void_p(h), m, cycles, prec, n_out,
+                                              ctypes.c_void_p(S_ptr), ctypes.c_void_p(log_scale_ptr),
+                                              rep, ctypes.c_void_p(stream)))
+
+
 def cb_topk(S_ptr, n, k, idx_ptr, val_ptr, stream):
     _check(lib().cb_topk(ctypes.c_void_p(S_ptr), n, k, ctypes.c_void_p(idx_ptr),
                          ctypes.c_void_p(val_ptr), ctypes.c_void_p(stream)))
@@ -396,6 +405,24 @@ def ensemble_scores(gs: GraphSet, m: int, prec: int = CB_FP32, n_out=None, out=N
     rep = (InstReport * len(gs.n))() if report else None
     cb_ensemble_scores(gs.h, m, prec, n_out, S.data_ptr(), ls.data_ptr(), rep,
                        _stream_handle(stream))
+    return (ls, S, list(rep)) if report else (ls, S)
+
+
+def ensemble_scores_restarted(gs: GraphSet, m: int, cycles: int, prec: int = CB_FP32, n_out=None,
+                              out=None, stream=None, report: bool = False):
+    """(log_scale, S) as ensemble_scores, each e^{A_r} 1 by `cycles` restarted
+    Lanczos cycles of m steps (block bidiagonal form of the restarted method)."""
+    import torch
+
+    n_out = gs.n_max if n_out is None else n_out
+    if out is None:
+        S = torch.empty(n_out, dtype=torch.float64, device="cuda")
+        ls = torch.empty(1, dtype=torch.float64, device="cuda")
+    else:
+        S, ls = out
+    rep = (InstReport * len(gs.n))() if report else None
+    cb_ensemble_scores_restarted(gs.h, m, cycles, prec, n_out, S.data_ptr(), ls.data_ptr(), rep,
+                                 _stream_handle(stream))
     return (ls, S, list(rep)) if report else (ls, S)
 
 

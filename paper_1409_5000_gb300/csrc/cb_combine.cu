@@ -179,4 +179,17 @@ int combine_ensemble(cb_graph *h, int prec, uint32_t n_out, double *S, double *l
   return cuda_error(cudaGetLastError(), "combine launch");
 }
 
+int combine_sum_f64(cb_graph *h, const double *Y, uint32_t n_out, double *S, double *log_scale,
+                    cudaStream_t s) {
+  const size_t shm = (sizeof(double) + sizeof(uint64_t) + sizeof(uint32_t)) * h->n_inst;
+  if (shm > 200 * 1024) return set_error(CB_ERR_ARG, "too many realisations for one combine");
+  auto k = combine_sum_kernel<double>;
+  prefer_shared(k);
+  if (shm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  const int tok = prof_begin(CB_K_COMBINE, s);
+  k<<<(n_out + 255) / 256, 256, shm, s>>>(Y, h->ws.sc, h->d_inst, h->n_inst, n_out, S, log_scale);
+  prof_end(tok, s);
+  return cuda_error(cudaGetLastError(), "combine launch");
+}
+
 }  // namespace cb

@@ -226,9 +226,11 @@ void free_backwork(BackWork &B);  // cb_adjoint.cu
 // node indices start_idx[0..k) (device array) restricted to [0, n_r).
 // start_idx: none (start vector 1), an index set shared by all realisations
 // (k entries), or with per_inst one start node per realisation (e_idx[r-r0]).
+// restart_scale (device, double[N]): a restarted cycle; W_0 already holds
+// the start vector with scale restart_scale[r] (0: nothing to do).
 int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
                 cudaStream_t s, const uint32_t *start_idx = nullptr, uint32_t k = 0,
-                bool per_inst = false);
+                bool per_inst = false, const double *restart_scale = nullptr);
 // tridiagonal exp (cb_tridiag.cu)
 int tridiag_run(cb_graph *h, uint32_t r0, uint32_t r1, int prec, cudaStream_t s);
 // combine (cb_combine.cu)
@@ -236,6 +238,9 @@ int combine_single(cb_graph *h, uint32_t r, int prec, double *y, double *log_sca
                    cudaStream_t s);
 int combine_ensemble(cb_graph *h, int prec, uint32_t n_out, double *S, double *log_scale,
                      cudaStream_t s);
+// eq. 5 sum of FP64 per-realisation terms Y (node_base layout), shifts in h->ws.sc.theta
+int combine_sum_f64(cb_graph *h, const double *Y, uint32_t n_out, double *S, double *log_scale,
+                    cudaStream_t s);
 // 8 consecutive elements (16- or 32-byte aligned) as one or two vector accesses.
 template <typename T>
 struct Vec8;

@@ -113,9 +113,12 @@ __global__ void __launch_bounds__(kThreads) init_indicator_kernel(LArgs a, uint3
   }
 }
 
+// rscale (restart): W_0 already holds the start vector and scale_0 =
+// rscale[r]; 0 marks a realisation that has nothing left to do.
 __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_t r0, uint32_t r1,
                                                                 uint32_t m, const uint32_t *idx,
-                                                                uint32_t k, bool per_inst) {
+                                                                uint32_t k, bool per_inst,
+                                                                const double *rscale) {
   const uint32_t ms = a.sc.ms;
   const uint64_t total = (uint64_t)(r1 - r0) * ms;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -133,7 +136,12 @@ __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_
       else
         for (uint32_t q = 0; q < k; ++q) cnt += (idx[q] < a.inst[r].n);
     }
-    a.sc.scale[o] = (jj == 0 && cnt) ? 1.0 / sqrt((double)cnt) : 0.0;
+    double s0 = cnt ? 1.0 / sqrt((double)cnt) : 0.0;
+    if (rscale) {
+      s0 = rscale[r];
+      cnt = s0 > 0.0 ? 1u : 0u;
+    }
+    a.sc.scale[o] = jj == 0 ? s0 : 0.0;
     if (jj == 0) {
       a.sc.meff[r] = cnt ? m : 0u;  // no start vector: nothing to do
       a.sc.status[r] = CB_OK;
@@ -652,7 +660,7 @@ static void launch_spmv_lanes(int lanes, const LArgs &a, uint32_t j, uint32_t co
 
 template <typename T>
 static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, cudaStream_t s,
-                 const uint32_t *start_idx, uint32_t k, bool per_inst) {
+                 const uint32_t *start_idx, uint32_t k, bool per_inst, const double *rscale) {
   LArgs a;
   a.inst = h->d_inst;
   a.tile_inst = h->d_tile_inst;
@@ -710,13 +718,14 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   prefer_shared(init_scalars_kernel);
   prefer_shared(finalize_kernel<T>);
   int tok = prof_begin(CB_K_INIT, s);
-  init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1,
-                                                                    start_idx ? T(0) : T(1));
-  if (start_idx)
+  if (!rscale)
+    init_vec_kernel<T><<<init_grid ? init_grid : 1, kThreads, 0, s>>>(a, r0, r1,
+                                                                      start_idx ? T(0) : T(1));
+  if (start_idx && !rscale)
     init_indicator_kernel<T><<<r1 - r0, kThreads, 0, s>>>(a, r0, start_idx, k, per_inst);
   const uint64_t nsc = (uint64_t)(r1 - r0) * W.sc.ms;
   init_scalars_kernel<<<(uint32_t)((nsc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-      a, r0, r1, m, start_idx, k, per_inst);
+      a, r0, r1, m, start_idx, k, per_inst, rscale);
   prof_end(tok, s);
   for (uint32_t j = 0; j < m; ++j) {
     tok = prof_begin(CB_K_SPMV, s);
@@ -731,9 +740,10 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
 }
 
 int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
-                cudaStream_t s, const uint32_t *start_idx, uint32_t k, bool per_inst) {
-  return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k, per_inst)
-                         : run_t<float>(h, W, r0, r1, m, s, start_idx, k, per_inst);
+                cudaStream_t s, const uint32_t *start_idx, uint32_t k, bool per_inst,
+                const double *restart_scale) {
+  return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k, per_inst, restart_scale)
+                         : run_t<float>(h, W, r0, r1, m, s, start_idx, k, per_inst, restart_scale);
 }
 
 }  // namespace cb
