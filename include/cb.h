@@ -215,6 +215,31 @@ int cb_graph_free(cb_graph *h);
  */
 int cb_release_cached_memory(void);
 
+/*
+ * cb_set_memory_limit -- cap the device memory the library holds in live
+ * allocations (handles, workspaces, adjoint and restart buffers; not the
+ * top-k scratch).  An allocation that would exceed the cap fails with
+ * CB_ERR_OOM as if the device were full, and the call that made it frees
+ * what it had taken.  0 (the default) means no cap.  Process-wide.
+ * cb_memory_in_use returns the bytes currently held.
+ */
+int cb_set_memory_limit(size_t bytes);
+size_t cb_memory_in_use(void);
+
+/*
+ * cb_debug_stall_tile -- test hook for the bounded waits.  The column-
+ * blocked SpMV (FP32) stages column blocks of the Krylov vector into shared
+ * memory with bulk copies and waits for each on an mbarrier, for at most
+ * 1 s of global time.  After this call, tile `btile` (0 <= btile <
+ * number of column-blocked tiles, in realisation order) expects its first
+ * column block but never copies it: its wait runs out, the step of that
+ * realisation records CB_ERR_TIMEOUT (its scores become NaN, a report names
+ * it and the call returns CB_ERR_TIMEOUT) and the other realisations are
+ * unaffected.  No copy is left in flight and the context stays usable.
+ * UINT32_MAX switches the hook off.  Drops the handle's captured passes.
+ */
+int cb_debug_stall_tile(cb_graph *h, uint32_t btile);
+
 /* Number of realisations / node count of realisation r / largest n. */
 uint32_t cb_graph_num_instances(const cb_graph *h);
 uint32_t cb_graph_num_nodes(const cb_graph *h, uint32_t r);

@@ -91,6 +91,12 @@ def lib():
         L.cb_graph_num_entries.argtypes = [vp, u32]
         L.cb_release_cached_memory.restype = i32
         L.cb_release_cached_memory.argtypes = []
+        L.cb_set_memory_limit.restype = i32
+        L.cb_set_memory_limit.argtypes = [ctypes.c_size_t]
+        L.cb_memory_in_use.restype = ctypes.c_size_t
+        L.cb_memory_in_use.argtypes = []
+        L.cb_debug_stall_tile.restype = i32
+        L.cb_debug_stall_tile.argtypes = [vp, u32]
         L.cb_topk_noalloc.restype = i32
         L.cb_topk_noalloc.argtypes = [vp, u32, u32, vp, vp, vp]
         L.cb_profile_enable.restype = i32
@@ -262,6 +268,18 @@ def cb_ensemble_scores_restarted(h, m, cycles, prec, n_out, S_ptr, log_scale_ptr
 def cb_topk(S_ptr, n, k, idx_ptr, val_ptr, stream):
     _check(lib().cb_topk(ctypes.c_void_p(S_ptr), n, k, ctypes.c_void_p(idx_ptr),
                          ctypes.c_void_p(val_ptr), ctypes.c_void_p(stream)))
+
+
+def cb_set_memory_limit(nbytes):
+    _check(lib().cb_set_memory_limit(int(nbytes)))
+
+
+def cb_memory_in_use():
+    return int(lib().cb_memory_in_use())
+
+
+def cb_debug_stall_tile(h, btile):
+    _check(lib().cb_debug_stall_tile(ctypes.c_void_p(h), btile))
 
 
 def cb_topk_noalloc(S_ptr, n, k, idx_ptr, val_ptr, stream):

@@ -17,6 +17,7 @@
 #include <atomic>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
 
 #include "cb_internal.cuh"
 
@@ -149,19 +150,47 @@ static cudaError_t device_pool(cudaMemPool_t *pool) {
 
 // Pool allocations are ordered on the legacy default stream and completed
 // before returning, so the memory is usable from any stream.
+// Live bytes of the library's device allocations and the optional cap
+// (cb_set_memory_limit); sizes are kept per pointer for dev_free.
+static std::mutex g_alloc_mu;
+static std::unordered_map<void *, size_t> g_alloc_size;
+static size_t g_alloc_live = 0, g_alloc_limit = 0;
+
 cudaError_t dev_alloc(void **p, size_t bytes) {
   *p = nullptr;
-  if (!use_pool()) return cudaMalloc(p, bytes);
-  cudaMemPool_t pool;
-  cudaError_t e = device_pool(&pool);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, 0);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
-  if (e != cudaSuccess) *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc_limit && g_alloc_live + bytes > g_alloc_limit) return cudaErrorMemoryAllocation;
+  }
+  cudaError_t e;
+  if (!use_pool()) {
+    e = cudaMalloc(p, bytes);
+  } else {
+    cudaMemPool_t pool;
+    e = device_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  }
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_size[*p] = bytes;
+  g_alloc_live += bytes;
   return e;
 }
 
 void dev_free(void *p) {
   if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = g_alloc_size.find(p);
+    if (it != g_alloc_size.end()) {
+      g_alloc_live -= it->second;
+      g_alloc_size.erase(it);
+    }
+  }
   if (!use_pool()) {
     cudaFree(p);
     return;
@@ -318,6 +347,28 @@ CB_API uint64_t cb_graph_num_entries(const cb_graph *h, uint32_t r) {
   if (!h || r >= h->n_inst) return 0;
   const uint64_t end = r + 1 < h->n_inst ? h->inst[r + 1].edge_base : h->total_nnz;
   return end - h->inst[r].edge_base;
+}
+
+static void drop_graphs(cb_graph *h);
+
+CB_API int cb_set_memory_limit(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_limit = bytes;
+  return CB_OK;
+}
+
+CB_API size_t cb_memory_in_use(void) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc_live;
+}
+
+CB_API int cb_debug_stall_tile(cb_graph *h, uint32_t btile) {
+  if (!h) return set_error(CB_ERR_ARG, "cb_debug_stall_tile: null handle");
+  if (btile != UINT32_MAX && btile >= h->total_btiles)
+    return set_error(CB_ERR_ARG, "cb_debug_stall_tile: no such column-blocked tile");
+  h->stall_btile = btile;
+  drop_graphs(h);  // captured launches hold the previous setting
+  return CB_OK;
 }
 
 CB_API int cb_release_cached_memory(void) {
@@ -736,6 +787,12 @@ CB_API int cb_graph_free(cb_graph *h) {
   return cuda_error(e, "cb_graph_free");
 }
 
+int cb::status_error(int32_t st) {
+  if (st == CB_ERR_TIMEOUT)
+    return set_error(CB_ERR_TIMEOUT, "a bounded device-side wait gave up (column-blocked SpMV)");
+  return set_error(CB_ERR_NONFINITE, "a recurrence scalar became non-finite");
+}
+
 static int fill_report(cb_graph *h, uint32_t r0, uint32_t r1, cb_inst_report *rep, cudaStream_t s) {
   const uint32_t N = r1 - r0, ms = h->ws.sc.ms;
   std::vector<uint32_t> meff(N);
@@ -755,7 +812,7 @@ static int fill_report(cb_graph *h, uint32_t r0, uint32_t r1, cb_inst_report *re
     rep[q].theta = th[q];
     rep[q].beta_last = meff[q] ? be[(size_t)q * ms + meff[q] - 1] : 0.0;
     rep[q].beta0 = std::sqrt((double)h->inst[r0 + q].n);
-    if (st[q] != CB_OK) rc = set_error(CB_ERR_NONFINITE, "a recurrence scalar became non-finite");
+    if (st[q] != CB_OK && rc == CB_OK) rc = status_error(st[q]);
   }
   return rc;
 }

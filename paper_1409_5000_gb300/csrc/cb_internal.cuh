@@ -166,6 +166,9 @@ struct cb_graph {
   uint32_t basis_m = 0;
   int basis_prec = -1;
   uint64_t basis_gen = 0;
+  // test hook (cb_debug_stall_tile): this column-blocked tile's first column
+  // block is expected but never copied, so its bounded wait runs out
+  uint32_t stall_btile = UINT32_MAX;
   cb::Workspace ws;   // Krylov basis from 1 (forward)
   cb::Workspace ws2;  // Krylov basis from the top-k indicator (adjoint)
   cb::BackWork bw;    // adjoint buffers
@@ -189,6 +192,8 @@ inline cudaError_t dev_alloc_n(P **p, size_t count) {
 }
 
 int set_error(int code, const std::string &msg);
+// host error for a failed realisation's device status (CB_ERR_TIMEOUT or CB_ERR_NONFINITE)
+int status_error(int32_t st);
 int cuda_error(cudaError_t e, const char *what);
 
 // One-time hint that a kernel should run with the shared-memory-heavy L1 /

@@ -61,6 +61,7 @@ struct LArgs {
   const uint8_t *bslot;
   const uint32_t *blong_ptr, *blong_rows;
   uint32_t skip_blocked;  // the tiled-CSR kernel leaves blocked realisations alone
+  uint32_t stall_btile;   // test hook: this tile's first column block is never copied
 };
 
 // Column indices are read once per step: streaming (evict-first) load.
@@ -364,11 +365,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of `parity` to complete; false after the limit.
-constexpr uint32_t kSpinLimit = 1u << 22;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase of `parity` to complete: false after 1 s of
+// global time or kSpinLimit polls, whichever comes first.
+constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 15u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 // One bulk copy global -> shared whose bytes complete on `bar` (16-byte
@@ -460,6 +472,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   if (tid == 0) {
     for (uint32_t b = 0; b < 2 && b < nb; ++b) {
       mbar_expect_tx(&s_full[b], block_bytes(b));
+      if (b == 0 && t == a.stall_btile) continue;  // test hook: block 0 never arrives
       bulk_g2s(xs + b * kBBuf, x + (uint64_t)b * kBCol, block_bytes(b), &s_full[b]);
       s_issued[b] = 1;
     }
@@ -687,6 +700,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.blong_rows = h->d_blong_rows;
   const bool use_blocked = sizeof(T) == 4 && h->total_btiles > 0;
   a.skip_blocked = use_blocked ? 1u : 0u;
+  a.stall_btile = h->stall_btile;
 
   const InstDesc &A0 = h->inst[r0], &A1 = h->inst[r1 - 1];
   const uint32_t chunk_off = A0.chunk_base;

@@ -312,7 +312,7 @@ CB_API int cb_ensemble_scores_restarted(cb_graph *h, uint32_t m, uint32_t cycles
       rep[r].beta0 = std::sqrt((double)h->inst[r].n);
     }
     for (uint32_t r = 0; r < N && rc == CB_OK; ++r)
-      if (st[r] != CB_OK) rc = set_error(CB_ERR_NONFINITE, "a recurrence scalar became non-finite");
+      if (st[r] != CB_OK) rc = status_error(st[r]);
   }
   dev_free(blob);
   dev_free(Y);
