@@ -393,6 +393,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
+// Prefetch of a global range into L2 (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // two column blocks of W_j (each followed by its zero word), then
 // kBRowsPerThread accumulator slots per thread
 constexpr size_t kBSmemBytes = (2 * kBBuf + kBRowsPerThread * kBThreads) * sizeof(float);
@@ -409,6 +414,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   __shared__ uint32_t s_done[2];                  // warps finished with buffer p
   __shared__ uint32_t s_issued[2];                // copies issued into buffer p
   __shared__ int s_abort;
+  __shared__ uint64_t s_seg[kBMaxBlocks + 1];     // stream offset of each column block's segment
   const uint32_t t = btile_off + blockIdx.x;
   const uint32_t r = a.btile_inst[t];
   if (j >= a.sc.meff[r]) return;
@@ -433,6 +439,12 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     s_issued[tid] = 0;
   }
   if (tid == 0) s_abort = 0;
+  const uint32_t nb = I.nb;
+  const uint64_t sbase = a.bseg_base[t];
+  for (uint32_t q = tid; q <= nb; q += kBThreads) {
+    const uint64_t w = (sbase + (q < nb ? q : nb - 1)) * 32;
+    s_seg[q] = q < nb ? a.bwstart[w] : a.bwstart[w + 31] + 32ull * a.bwlen[w + 31];
+  }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   const uint32_t lp0 = a.blong_ptr[t], lp1 = a.blong_ptr[t + 1];
@@ -441,8 +453,6 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     atomicOr(&s_long[lr >> 5], 1u << (lr & 31));
   }
 
-  const uint32_t nb = I.nb;
-  const uint64_t sbase = a.bseg_base[t];
   const uint32_t lane = tid & 31, warp = tid >> 5;
   // Stripe rounds: a warp's stream of block b has ns_b = len_b / 4 stripes,
   // read 4 stripes (16 elements per lane) per round.  The loads of the next
@@ -469,7 +479,17 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     const uint32_t len = min(kBCol, n_cols - b * kBCol);
     return ((len + 3u) & ~3u) * 4u;  // whole 16-byte units (reads up to 3 floats of padding)
   };
+  // The edge streams of column block b + 3 are prefetched into L2 when block
+  // b + 2 is staged, so the warps' stream loads find them there.
+  auto prefetch_seg = [&](uint32_t b) {
+    const uint64_t e0 = s_seg[b], e1 = s_seg[b + 1];
+    if (e1 > e0) {
+      l2_prefetch(a.bcol + e0, (uint32_t)(2 * (e1 - e0)));
+      l2_prefetch(a.bslot + e0, (uint32_t)(e1 - e0));
+    }
+  };
   if (tid == 0) {
+    for (uint32_t b = 1; b < 3 && b < nb; ++b) prefetch_seg(b);
     for (uint32_t b = 0; b < 2 && b < nb; ++b) {
       mbar_expect_tx(&s_full[b], block_bytes(b));
       if (b == 0 && t == a.stall_btile) continue;  // test hook: block 0 never arrives
@@ -545,6 +565,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
           mbar_expect_tx(&s_full[p], block_bytes(b + 2));
           bulk_g2s(xs + p * kBBuf, x + (uint64_t)(b + 2) * kBCol, block_bytes(b + 2), &s_full[p]);
           s_issued[p] += 1;
+          if (b + 3 < nb) prefetch_seg(b + 3);
         }
       }
     }
