@@ -250,8 +250,7 @@ def er_ensemble(sizes, dbar: float, k: int, extra: int, config: int,
     realisation (paper, "Multiple backgrounds scenario").  p = dbar/(n-1).
     """
     sizes = [int(s) for s in sizes]
-    nodes = sample_nodes(min(sizes), k, seed_for(config, 0, salt=1))
-    tedges = target_edges(nodes, extra, clique, seed_for(config, 0, salt=2))
+    nodes, tedges = _ensemble_target(sizes, k, extra, clique, config)
 
     def one(r):
         n = sizes[r]
@@ -260,6 +259,27 @@ def er_ensemble(sizes, dbar: float, k: int, extra: int, config: int,
     with ThreadPoolExecutor(threads or _threads()) as ex:
         graphs = list(ex.map(one, range(len(sizes))))
     return Ensemble(graphs, nodes, tedges, dict(kind="er", dbar=dbar, config=config))
+
+
+def _ensemble_target(sizes, k, extra, clique, config):
+    nodes = sample_nodes(min(sizes), k, seed_for(config, 0, salt=1))
+    return nodes, target_edges(nodes, extra, clique, seed_for(config, 0, salt=2))
+
+
+def er_ensemble_member(sizes, dbar: float, k: int, extra: int, config: int, r: int,
+                       clique: bool = False) -> Graph:
+    """Realisation r of er_ensemble(sizes, dbar, k, extra, config, clique) alone."""
+    sizes = [int(s) for s in sizes]
+    _, tedges = _ensemble_target(sizes, k, extra, clique, config)
+    n = sizes[r]
+    return er(n, dbar / (n - 1), seed_for(config, r + 1), tedges)
+
+
+def er_ensemble_uneven_sizes(n_inst: int = 256, n_lo: int = 20_000, n_hi: int = 400_000,
+                             config: int = 3):
+    """The realisation sizes er_ensemble_uneven draws."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(config, 0, salt=3)))
+    return [int(x) for x in rng.integers(n_lo, n_hi + 1, size=n_inst)]
 
 
 def single_background(kind: str, n: int, k: int, config: int, clique: bool = True,
@@ -304,8 +324,7 @@ def er_ensemble_uneven(n_inst: int = 256, n_lo: int = 20_000, n_hi: int = 400_00
                        dbar: float = 20.0, k: int = 30, extra: int = 15, config: int = 3):
     """N ER realisations, n ~ U[n_lo, n_hi] per instance, dbar=20, 30-node
     tree(+15) target on [0, n_lo); m=25, k=30."""
-    rng = np.random.Generator(np.random.PCG64(seed_for(config, 0, salt=3)))
-    sizes = rng.integers(n_lo, n_hi + 1, size=n_inst)
+    sizes = er_ensemble_uneven_sizes(n_inst, n_lo, n_hi, config)
     ens = er_ensemble(sizes, dbar, k, extra, config=config)
     ens.meta.update(m=25, k=k)
     return ens
