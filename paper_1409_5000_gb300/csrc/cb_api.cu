@@ -119,19 +119,30 @@ static int pick_lanes(double avg_deg) {
 }
 
 static std::mutex g_pool_mu;
-static std::vector<cudaMemPool_t> g_pools;  // per device, created on first use
+static std::vector<cudaMemPool_t> g_pools;        // per device, created on first use
+static std::vector<cudaStream_t> g_alloc_streams;  // per device, non-blocking
 
 static bool use_pool() {
   static const bool on = std::getenv("CB_NO_POOL") == nullptr;
   return on;
 }
 
-static cudaError_t device_pool(cudaMemPool_t *pool) {
+static cudaError_t device_pool(cudaMemPool_t *pool, cudaStream_t *stream) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_pool_mu);
-  if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+  if ((int)g_pools.size() <= dev) {
+    g_pools.resize(dev + 1, nullptr);
+    g_alloc_streams.resize(dev + 1, nullptr);
+  }
+  if (!g_alloc_streams[dev]) {
+    e = cudaStreamCreateWithFlags(&g_alloc_streams[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_alloc_streams[dev] = nullptr;
+      return e;
+    }
+  }
   if (!g_pools[dev]) {
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
@@ -145,11 +156,14 @@ static cudaError_t device_pool(cudaMemPool_t *pool) {
     g_pools[dev] = p;
   }
   *pool = g_pools[dev];
+  *stream = g_alloc_streams[dev];
   return cudaSuccess;
 }
 
-// Pool allocations are ordered on the legacy default stream and completed
-// before returning, so the memory is usable from any stream.
+// Pool allocations are ordered on a library stream of their own
+// (non-blocking, so they wait for no caller's work) and completed before
+// returning, so the memory is usable from any stream.  An upload on one host
+// thread therefore proceeds while another thread's kernels run.
 // Live bytes of the library's device allocations and the optional cap
 // (cb_set_memory_limit); sizes are kept per pointer for dev_free.
 static std::mutex g_alloc_mu;
@@ -167,9 +181,10 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
     e = cudaMalloc(p, bytes);
   } else {
     cudaMemPool_t pool;
-    e = device_pool(&pool);
-    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    cudaStream_t as = nullptr;
+    e = device_pool(&pool, &as);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, as);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(as);
   }
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -195,8 +210,10 @@ void dev_free(void *p) {
     cudaFree(p);
     return;
   }
+  cudaMemPool_t pool;
+  cudaStream_t as = nullptr;
   cudaDeviceSynchronize();  // no kernel may still use it
-  cudaFreeAsync(p, 0);
+  if (device_pool(&pool, &as) == cudaSuccess) cudaFreeAsync(p, as);
 }
 
 template <typename P>

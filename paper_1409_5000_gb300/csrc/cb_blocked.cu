@@ -246,7 +246,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     chk(dalloc(&h->d_btile_inst, nbt));
     chk(dalloc(&h->d_bseg_base, nbt));
     chk(dalloc(&h->d_bwstart, nw));
-    chk(dalloc(&h->d_bwlen, nw));
+    chk(dalloc(&h->d_bwlen, nw + 1));  // + the sortedness flag of the count pass
     chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
     chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
     if (e != cudaSuccess) {
@@ -261,8 +261,9 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
                           cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
                         cudaMemcpyHostToDevice, s));
-    uint32_t *d_unsorted = nullptr;
-    chk(dalloc(&d_unsorted, 1));
+    // no temporary allocation here: a free synchronises the device, which
+    // would stall an upload behind another thread's kernels
+    uint32_t *d_unsorted = h->d_bwlen + nw;
     if (e == cudaSuccess) chk(cudaMemsetAsync(d_unsorted, 0, 4, s));
     // count each group of realisations as soon as its columns are on the device
     uint32_t r_begin = 0;
@@ -281,7 +282,6 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     chk(cudaMemcpyAsync(len.data(), h->d_bwlen, nw * 4, cudaMemcpyDeviceToHost, s));
     chk(cudaMemcpyAsync(&unsorted, d_unsorted, 4, cudaMemcpyDeviceToHost, s));
     chk(cudaStreamSynchronize(s));
-    dev_free(d_unsorted);
     if (e == cudaSuccess && unsorted) {
       free_blocked(h);
       return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
