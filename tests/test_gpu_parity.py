@@ -318,3 +318,30 @@ def test_unsorted_rows_rejected(B):
     col[rp[i]:rp[i + 1]] = col[rp[i]:rp[i + 1]][::-1].copy()
     with pytest.raises(B.CBError):
         B.GraphSet([_G(g.n, rp, col)])
+
+
+def test_upload_concurrent_with_compute(B):
+    """An upload on a second host thread and stream while this thread runs an
+    ensemble (the double-buffered end-to-end pattern): both results are
+    bit-identical to the same calls made one after the other."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    ens_a = synth.er_ensemble_uneven(n_inst=6, n_lo=20_000, n_hi=120_000, config=311)
+    ens_b = synth.er_ensemble_uneven(n_inst=5, n_lo=10_000, n_hi=90_000, config=312)
+    with B.GraphSet(ens_a.graphs) as ga:
+        ref_a = B.ensemble_scores(ga, 25, B.CB_FP32)[1].cpu().numpy()
+    with B.GraphSet(ens_b.graphs) as gb:
+        ref_b = B.ensemble_scores(gb, 25, B.CB_FP32)[1].cpu().numpy()
+    up = torch.cuda.Stream()
+    with B.GraphSet(ens_a.graphs) as ga, ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(lambda: B.GraphSet(ens_b.graphs, stream=up))
+        for _ in range(3):
+            got_a = B.ensemble_scores(ga, 25, B.CB_FP32)[1]
+        torch.cuda.current_stream().synchronize()
+        gb = fut.result()
+        try:
+            got_b = B.ensemble_scores(gb, 25, B.CB_FP32)[1].cpu().numpy()
+        finally:
+            gb.close()
+        assert np.array_equal(got_a.cpu().numpy(), ref_a)
+    assert np.array_equal(got_b, ref_b)
