@@ -611,6 +611,29 @@ def main():
             "head_max_rel_vs_plain": float(np.max(np.abs(a - b)[head] / b[head])),
             "api": "cb_ensemble_scores_restarted (FP32), wall time of one synchronous call"}
 
+    if rank == 0 and not args.skip_extra:
+        # full reorthogonalisation (CB_REORTH), the oracle's scheme, on the
+        # device: its cost on the same workload (third call: a graph replay)
+        B.ensemble_scores(gs, m, B.CB_FP32, out=(S, ls))
+        b = S.cpu().numpy()
+        ls_plain = float(ls.item())
+        Sr2 = torch.empty_like(S)
+        lr2 = torch.empty_like(ls)
+        for _ in range(2):
+            B.ensemble_scores(gs, m, B.CB_FP32 | B.CB_REORTH, out=(Sr2, lr2))
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        B.ensemble_scores(gs, m, B.CB_FP32 | B.CB_REORTH, out=(Sr2, lr2))
+        q1.record(stream)
+        torch.cuda.synchronize()
+        a = Sr2.cpu().numpy() * math.exp(float(lr2.item()) - ls_plain)
+        head = b >= 1e-3 * b.max()
+        extra["reorth"] = {"ms": q0.elapsed_time(q1),
+                           "head_max_rel_vs_plain": float(np.max(np.abs(a - b)[head] / b[head])),
+                           "api": "cb_ensemble_scores(CB_FP32 | CB_REORTH), graph replay"}
+
     cpu = None
     if rank == 0 and not args.skip_extra and world == 1:
         v, done, t, res = cpu_oracle_sample(ens, m, budget_s=15.0, want={0, 1})

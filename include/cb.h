@@ -53,6 +53,14 @@ extern "C" {
 /* precision modes */
 #define CB_FP32 0
 #define CB_FP64 1
+/* OR-ed into a prec argument: full reorthogonalisation.  Each new Lanczos
+ * vector is orthogonalised against every previous one by two passes of
+ * classical Gram-Schmidt (the scheme of the FP64 oracle), before its norm
+ * beta_j is taken.  Step j then reads about 4 (j + 2) extra vectors.  The
+ * paper does not fix this; without it the approximation of e^A 1 stays
+ * accurate in finite precision (Greenbaum 1989; Musco, Musco & Sidford 2018),
+ * so it is off by default. */
+#define CB_REORTH 0x100
 
 /* cb_graph_upload flags */
 #define CB_VALIDATE 1u    /* check CSR invariants on the host before upload */

@@ -21,6 +21,7 @@ from ._build import cb_lib_path, INCLUDE
 
 CB_OK, CB_ERR_ARG, CB_ERR_CUDA, CB_ERR_OOM, CB_ERR_TIMEOUT, CB_ERR_NONFINITE, CB_ERR_STATE = range(7)
 CB_FP32, CB_FP64 = 0, 1
+CB_REORTH = 0x100  # OR into prec: full reorthogonalisation (two Gram-Schmidt passes)
 CB_VALIDATE, CB_DEVICE_PTRS = 1, 2
 CB_MAX_M, CB_MAX_TOPK, CB_MAX_CYCLES = 128, 4096, 1024
 

@@ -378,8 +378,10 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
     return set_error(CB_ERR_ARG, "cb_scores_backward: need 1 <= m <= 64");
   if (k < 1 || k > CB_MAX_TOPK)
     return set_error(CB_ERR_ARG, "cb_scores_backward: need 1 <= k <= CB_MAX_TOPK");
+  const bool reorth = split_prec(prec);
   if (prec != CB_FP32 && prec != CB_FP64)
     return set_error(CB_ERR_ARG, "cb_scores_backward: bad precision");
+  h->reorth = reorth;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = ensure_workspace(h, h->ws, m, prec, s);
   if (rc == CB_OK) rc = ensure_workspace(h, h->ws2, m, prec, s);
@@ -400,13 +402,15 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
   // the basis from 1 is the forward pass's when an ensemble pass at this m
   // and precision ran last on the handle (same stream order assumed)
   const bool reuse = rc == CB_OK && h->basis_m == m && h->basis_prec == prec &&
-                     h->basis_gen == h->ws.gen && !std::getenv("CB_NO_REUSE");
+                     h->basis_reorth == reorth && h->basis_gen == h->ws.gen &&
+                     !std::getenv("CB_NO_REUSE");
   if (rc == CB_OK && !reuse) {
     h->basis_m = 0;
     rc = lanczos_run(h, h->ws, 0, h->n_inst, m, prec, s);
     if (rc == CB_OK) {
       h->basis_m = m;
       h->basis_prec = prec;
+      h->basis_reorth = reorth;
       h->basis_gen = h->ws.gen;
     }
   }
@@ -460,7 +464,7 @@ CB_API int cb_scores_backward_budget(cb_graph *h, uint32_t m, int prec, const ui
   uint64_t total = 0;
   for (uint32_t r = 0; r < N; ++r) {
     nnz[r] = (r + 1 < N ? h->inst[r + 1].edge_base : h->total_nnz) - h->inst[r].edge_base;
-    need[r] = adjoint_bytes(h->inst[r], nnz[r], m, prec);
+    need[r] = adjoint_bytes(h->inst[r], nnz[r], m, prec & ~CB_REORTH);
     total += need[r];
   }
   if (total <= mem_budget || N == 1)

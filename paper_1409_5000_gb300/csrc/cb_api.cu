@@ -266,7 +266,8 @@ int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream
   const size_t nchunks = std::max<size_t>(h->total_chunks, 1);
   const size_t nheavy = std::max<size_t>(h->total_heavy, 1);
   // doubles first, then 32-bit words
-  const size_t nd = 4 * (size_t)N * ms + N + nslots + ngroups + nchunks;
+  const size_t nfin = std::max<size_t>(h->total_fin, 1);
+  const size_t nd = 4 * (size_t)N * ms + N + nslots + ngroups + nchunks + nfin * ms + (size_t)N * ms;
   const size_t nw = 2 * (size_t)N + ngroups + N + nheavy;
   const size_t bytes = nd * sizeof(double) + nw * sizeof(uint32_t) + 256;
   e = dev_alloc(&W.blob, bytes);
@@ -284,6 +285,8 @@ int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream
   W.part = d; d += nslots;
   W.gpart = d; d += ngroups;
   W.cpart = d; d += nchunks;
+  W.rpart = d; d += nfin * ms;
+  W.rh = d; d += (size_t)N * ms;
   uint32_t *w = reinterpret_cast<uint32_t *>(d);
   W.sc.meff = w; w += N;
   W.sc.status = reinterpret_cast<int32_t *>(w); w += N;
@@ -735,6 +738,8 @@ CB_API uint32_t cb_graph_lanes(const cb_graph *h) { return h ? (uint32_t)h->lane
 // do not depend on the width.
 CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_out, void *stream) {
   if (!h) return set_error(CB_ERR_ARG, "cb_graph_tune: null handle");
+  split_prec(prec);  // reorthogonalisation does not change the SpMV being tuned
+  if (h) h->reorth = false;
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_graph_tune: bad precision");
   static const uint32_t kCand[6] = {1, 2, 4, 8, 16, 32};
   for (int c = 0; ms_out && c < 6; ++c) ms_out[c] = -1.0;
@@ -839,7 +844,9 @@ CB_API int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, 
   if (!h || !y_scaled || !log_scale) return set_error(CB_ERR_ARG, "cb_communicability: null argument");
   if (inst >= h->n_inst) return set_error(CB_ERR_ARG, "cb_communicability: realisation index out of range");
   if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_communicability: need 1 <= m <= CB_MAX_M");
+  const bool reorth = split_prec(prec);
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_communicability: bad precision");
+  h->reorth = reorth;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = ensure_workspace(h, h->ws, m, prec, s);
   h->basis_m = 0;  // overwrites part of the ensemble basis
@@ -868,7 +875,8 @@ static int ensemble_graph(cb_graph *h, uint32_t m, int prec, uint32_t n_out, dou
                           double *log_scale, cudaStream_t s) {
   cb_graph::GraphEntry *hit = nullptr;
   for (auto &g : h->graphs)
-    if (g.m == m && g.prec == prec && g.n_out == n_out && g.S == S && g.log_scale == log_scale &&
+    if (g.m == m && g.prec == prec && g.reorth == h->reorth && g.n_out == n_out && g.S == S &&
+        g.log_scale == log_scale &&
         g.ws_gen == h->ws.gen)
       hit = &g;
   if (hit && hit->exec) return cuda_error(cudaGraphLaunch(hit->exec, s), "cb_ensemble_scores: graph launch");
@@ -877,7 +885,7 @@ static int ensemble_graph(cb_graph *h, uint32_t m, int prec, uint32_t n_out, dou
       if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
       h->graphs.erase(h->graphs.begin());
     }
-    h->graphs.push_back({m, prec, n_out, S, log_scale, h->ws.gen, nullptr});
+    h->graphs.push_back({m, prec, n_out, S, log_scale, h->ws.gen, h->reorth, nullptr});
     return ensemble_enqueue(h, m, prec, n_out, S, log_scale, s);
   }
   cudaError_t e = cudaSuccess;
@@ -907,7 +915,9 @@ CB_API int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out,
                               double *log_scale, cb_inst_report *rep, void *stream) {
   if (!h || !S || !log_scale) return set_error(CB_ERR_ARG, "cb_ensemble_scores: null argument");
   if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_ensemble_scores: need 1 <= m <= CB_MAX_M");
+  const bool reorth = split_prec(prec);
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_ensemble_scores: bad precision");
+  h->reorth = reorth;
   if (n_out < h->n_max) return set_error(CB_ERR_ARG, "cb_ensemble_scores: n_out < largest n");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = ensure_workspace(h, h->ws, m, prec, s);
@@ -919,6 +929,7 @@ CB_API int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out,
   if (rc == CB_OK) {  // ws now holds the basis from 1 of every realisation
     h->basis_m = m;
     h->basis_prec = prec;
+    h->basis_reorth = h->reorth;
     h->basis_gen = h->ws.gen;
   }
   if (rc == CB_OK && rep) rc = fill_report(h, 0, h->n_inst, rep, s);

@@ -97,6 +97,8 @@ struct Workspace {
   uint32_t *gcnt = nullptr;// arrival counters per group
   uint32_t *icnt = nullptr;// arrival counters per instance
   double *cpart = nullptr; // heavy-row chunk partials
+  double *rpart = nullptr; // reorthogonalisation: per finalize tile, ms dot partials
+  double *rh = nullptr;    // reorthogonalisation: per realisation, ms coefficients
   uint32_t *hcnt = nullptr;// heavy-row arrival counters
   size_t blob_bytes = 0;
   void *blob = nullptr;    // single allocation backing sc/part/gpart/cnt
@@ -157,6 +159,7 @@ struct cb_graph {
     uint32_t n_out;
     double *S, *log_scale;
     uint64_t ws_gen;  // workspace allocation the graph was captured against
+    bool reorth;      // captured with reorthogonalisation
     cudaGraphExec_t exec;
   };
   std::vector<GraphEntry> graphs;
@@ -165,6 +168,10 @@ struct cb_graph {
   // precision (an ensemble pass or an adjoint ran last); 0 = not valid
   uint32_t basis_m = 0;
   int basis_prec = -1;
+  bool basis_reorth = false;
+  // the current call's CB_REORTH flag (set by every entry point that runs
+  // the Lanczos recurrence; read by lanczos_run)
+  bool reorth = false;
   uint64_t basis_gen = 0;
   // test hook (cb_debug_stall_tile): this column-blocked tile's first column
   // block is expected but never copied, so its bounded wait runs out
@@ -192,6 +199,13 @@ inline cudaError_t dev_alloc_n(P **p, size_t count) {
 }
 
 int set_error(int code, const std::string &msg);
+// Splits a prec argument into the precision (returned in prec) and the
+// CB_REORTH flag (returned).
+inline bool split_prec(int &prec) {
+  const bool r = (prec & CB_REORTH) != 0;
+  prec &= ~CB_REORTH;
+  return r;
+}
 // host error for a failed realisation's device status (CB_ERR_TIMEOUT or CB_ERR_NONFINITE)
 int status_error(int32_t st);
 int cuda_error(cudaError_t e, const char *what);

@@ -672,6 +672,147 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Full reorthogonalisation (CB_REORTH), after the finalize of step j: the new
+// vector w (basis slot j + 1, unnormalised) is orthogonalised against
+// v_i = scale_i W_i, i = 0..j, by classical Gram-Schmidt,
+//   h_i = v_i . w,   w <- w - sum_i h_i v_i,   beta_j = ||w||,
+// run twice, as the oracle does.  Per pass: partial dots per finalize tile,
+// their ordered sum per realisation, then the update with the norm reduced
+// as in finalize (deterministic throughout).  A step that has stopped
+// (breakdown in finalize or in an earlier pass: scale_{j+1} = 0) is left
+// alone.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool reorth_active(const LArgs &a, uint32_t r, uint32_t j) {
+  return j < a.sc.meff[r] && a.sc.scale[r * a.sc.ms + j + 1] != 0.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) reorth_dot_kernel(LArgs a, uint32_t j, uint32_t fin_off,
+                                                              double *rpart) {
+  __shared__ double s_w[kThreads / 32][CB_MAX_M + 1];
+  const uint32_t t = fin_off + blockIdx.x;
+  const uint32_t r = a.fin_inst[t];
+  if (!reorth_active(a, r, j)) return;
+  const InstDesc &I = a.inst[r];
+  const uint32_t ms = a.sc.ms;
+  const T *Vb = reinterpret_cast<const T *>(a.V);
+  const T *w = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
+  const uint32_t i0 = (t - I.fin_base) * kFinRows + 8 * threadIdx.x;
+  const uint32_t cnt = i0 < I.n ? min(8u, I.n - i0) : 0u;
+  T wv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) wv[q] = T(0);
+  if (cnt == 8) {
+    Vec8<T>::load(w + i0, wv);
+  } else {
+    for (uint32_t q = 0; q < cnt; ++q) wv[q] = w[i0 + q];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t i = 0; i <= j; ++i) {
+    const T *x = Vb + (uint64_t)i * a.vs + I.node_base;
+    T xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) xv[q] = T(0);
+    if (cnt == 8) {
+      Vec8<T>::load(x + i0, xv);
+    } else {
+      for (uint32_t q = 0; q < cnt; ++q) xv[q] = x[i0 + q];
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += xv[q] * wv[q];
+    acc = warp_sum<T>(acc);
+    if (lane == 0) s_w[warp][i] = (double)acc;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i <= j; i += blockDim.x) {
+    double sum = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) sum += s_w[q][i];
+    rpart[(uint64_t)t * ms + i] = a.sc.scale[r * ms + i] * sum;
+  }
+}
+
+__global__ void __launch_bounds__(128) reorth_sum_kernel(LArgs a, uint32_t j, uint32_t r0,
+                                                         const double *rpart, double *rh) {
+  const uint32_t r = r0 + blockIdx.x;
+  if (!reorth_active(a, r, j)) return;
+  const InstDesc &I = a.inst[r];
+  const uint32_t ms = a.sc.ms;
+  for (uint32_t i = threadIdx.x; i <= j; i += blockDim.x) {
+    double sum = 0.0;  // tile order: deterministic
+    for (uint32_t q = 0; q < I.n_fin; ++q) sum += rpart[(uint64_t)(I.fin_base + q) * ms + i];
+    rh[r * ms + i] = sum;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) reorth_update_kernel(LArgs a, uint32_t j,
+                                                                 uint32_t fin_off, const double *rh) {
+  __shared__ double s_red[32];
+  __shared__ T s_c[CB_MAX_M + 1];
+  const uint32_t t = fin_off + blockIdx.x;
+  const uint32_t r = a.fin_inst[t];
+  if (!reorth_active(a, r, j)) return;
+  const InstDesc &I = a.inst[r];
+  const uint32_t ms = a.sc.ms;
+  for (uint32_t i = threadIdx.x; i <= j; i += blockDim.x)
+    s_c[i] = (T)(rh[r * ms + i] * a.sc.scale[r * ms + i]);
+  __syncthreads();
+  T *Vb = reinterpret_cast<T *>(a.V);
+  T *w = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
+  const uint32_t i0 = (t - I.fin_base) * kFinRows + 8 * threadIdx.x;
+  const uint32_t cnt = i0 < I.n ? min(8u, I.n - i0) : 0u;
+  T wv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) wv[q] = T(0);
+  if (cnt == 8) {
+    Vec8<T>::load(w + i0, wv);
+  } else {
+    for (uint32_t q = 0; q < cnt; ++q) wv[q] = w[i0 + q];
+  }
+  for (uint32_t i = 0; i <= j; ++i) {
+    const T *x = Vb + (uint64_t)i * a.vs + I.node_base;
+    const T c = s_c[i];
+    T xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) xv[q] = T(0);
+    if (cnt == 8) {
+      Vec8<T>::load(x + i0, xv);
+    } else {
+      for (uint32_t q = 0; q < cnt; ++q) xv[q] = x[i0 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) wv[q] -= c * xv[q];
+  }
+  T acc = T(0);
+  if (cnt == 8) {
+    Vec8<T>::store(w + i0, wv);
+  } else {
+    for (uint32_t q = 0; q < cnt; ++q) w[i0 + q] = wv[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc += wv[q] * wv[q];  // entries past cnt are 0
+  const double part = block_sum_to_double<T>(acc, s_red);
+  double total;
+  if (arrive_and_reduce(I.fin, t - I.fin_base, r, part, a.red, &total)) {
+    const double beta = sqrt(total);
+    const double alpha = a.sc.alpha[r * ms + j];
+    const double bprev = j > 0 ? a.sc.beta[r * ms + j - 1] : 0.0;
+    a.sc.beta[r * ms + j] = beta;
+    if (!isfinite(beta)) {
+      a.sc.status[r] = CB_ERR_NONFINITE;
+      a.sc.meff[r] = j + 1;
+      a.sc.scale[r * ms + j + 1] = 0.0;
+    } else if (beta <= a.tau * (fabs(alpha) + bprev) || beta == 0.0) {
+      a.sc.meff[r] = j + 1;  // exact breakdown once the lost orthogonality is removed
+      a.sc.scale[r * ms + j + 1] = 0.0;
+    } else {
+      a.sc.scale[r * ms + j + 1] = 1.0 / beta;
+    }
+  }
+}
+
 template <typename T, int G>
 static void launch_spmv(const LArgs &a, uint32_t j, uint32_t chunk_off, uint32_t n_chunks,
                         uint32_t tile_off, uint32_t n_tiles, cudaStream_t s) {
@@ -769,6 +910,12 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
     prof_end(tok, s);
     tok = prof_begin(CB_K_FINALIZE, s);
     if (n_fin) finalize_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off);
+    if (n_fin && h->reorth)
+      for (int pass = 0; pass < 2; ++pass) {
+        reorth_dot_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off, W.rpart);
+        reorth_sum_kernel<<<r1 - r0, 128, 0, s>>>(a, j, r0, W.rpart, W.rh);
+        reorth_update_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off, W.rh);
+      }
     prof_end(tok, s);
   }
   return cuda_error(cudaGetLastError(), "lanczos launch");

@@ -252,8 +252,10 @@ CB_API int cb_ensemble_scores_restarted(cb_graph *h, uint32_t m, uint32_t cycles
     return set_error(CB_ERR_ARG, "cb_ensemble_scores_restarted: need 1 <= m <= CB_MAX_M");
   if (cycles < 1 || cycles > CB_MAX_CYCLES)
     return set_error(CB_ERR_ARG, "cb_ensemble_scores_restarted: need 1 <= cycles <= CB_MAX_CYCLES");
+  const bool reorth = split_prec(prec);
   if (prec != CB_FP32 && prec != CB_FP64)
     return set_error(CB_ERR_ARG, "cb_ensemble_scores_restarted: bad precision");
+  h->reorth = reorth;  // within each cycle
   if (n_out < h->n_max) return set_error(CB_ERR_ARG, "cb_ensemble_scores_restarted: n_out < largest n");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = ensure_workspace(h, h->ws, m, prec, s);

@@ -91,6 +91,7 @@ CB_API int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int pr
     return set_error(CB_ERR_ARG, "cb_subgraph_centrality: null argument");
   if (inst >= h->n_inst) return set_error(CB_ERR_ARG, "cb_subgraph_centrality: realisation out of range");
   if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_subgraph_centrality: need 1 <= m <= CB_MAX_M");
+  const bool reorth = split_prec(prec);
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_subgraph_centrality: bad precision");
   if (k < 1 || k > CB_MAX_SC_NODES)
     return set_error(CB_ERR_ARG, "cb_subgraph_centrality: need 1 <= k <= CB_MAX_SC_NODES");
@@ -126,6 +127,7 @@ CB_API int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int pr
     }
     d_nodes = tmp;
   }
+  v->reorth = reorth;
   rc = ensure_workspace(v, v->ws, m, prec, s);
   if (rc == CB_OK) rc = lanczos_run(v, v->ws, 0, k, m, prec, s, d_nodes, k, true);
   if (rc == CB_OK) {
