@@ -372,6 +372,7 @@ using namespace cb;
 
 CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx,
                               uint32_t k, float *grad, double *log_scale, void *stream) {
+  NvtxRange nvtx_range("cb_scores_backward");
   if (!h || !topk_idx || !grad || !log_scale)
     return set_error(CB_ERR_ARG, "cb_scores_backward: null argument");
   if (m < 1 || m > kMaxAdjM)
@@ -456,6 +457,7 @@ static uint64_t adjoint_bytes(const cb::InstDesc &I, uint64_t nnz, uint32_t m, i
 CB_API int cb_scores_backward_budget(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx,
                                      uint32_t k, float *grad, double *log_scale,
                                      size_t mem_budget, void *stream) {
+  NvtxRange nvtx_range("cb_scores_backward_budget");
   if (!h || !topk_idx || !grad || !log_scale)
     return set_error(CB_ERR_ARG, "cb_scores_backward_budget: null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

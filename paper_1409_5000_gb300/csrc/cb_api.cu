@@ -477,6 +477,7 @@ struct UploadCopies {
 CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
                            const uint32_t *const *row_ptr, const uint32_t *const *col,
                            uint32_t flags, void *stream, cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_upload");
   if (!out) return set_error(CB_ERR_ARG, "cb_graph_upload: out is null");
   *out = nullptr;
   if (n_inst == 0 || !n || !nnz || !row_ptr || !col)
@@ -737,6 +738,7 @@ CB_API uint32_t cb_graph_lanes(const cb_graph *h) { return h ? (uint32_t)h->lane
 // the fastest.  Realisations on the column-blocked kernel are timed too but
 // do not depend on the width.
 CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_out, void *stream) {
+  NvtxRange nvtx_range("cb_graph_tune");
   if (!h) return set_error(CB_ERR_ARG, "cb_graph_tune: null handle");
   split_prec(prec);  // reorthogonalisation does not change the SpMV being tuned
   if (h) h->reorth = false;
@@ -796,6 +798,7 @@ CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_
 }
 
 CB_API int cb_graph_free(cb_graph *h) {
+  NvtxRange nvtx_range("cb_graph_free");
   if (!h) return set_error(CB_ERR_ARG, "cb_graph_free: null handle");
   cudaError_t e = cudaDeviceSynchronize();
   drop_graphs(h);
@@ -841,6 +844,7 @@ static int fill_report(cb_graph *h, uint32_t r0, uint32_t r1, cb_inst_report *re
 
 CB_API int cb_communicability(cb_graph *h, uint32_t inst, uint32_t m, int prec, double *y_scaled,
                               double *log_scale, cb_inst_report *rep, void *stream) {
+  NvtxRange nvtx_range("cb_communicability");
   if (!h || !y_scaled || !log_scale) return set_error(CB_ERR_ARG, "cb_communicability: null argument");
   if (inst >= h->n_inst) return set_error(CB_ERR_ARG, "cb_communicability: realisation index out of range");
   if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_communicability: need 1 <= m <= CB_MAX_M");
@@ -913,6 +917,7 @@ static int ensemble_graph(cb_graph *h, uint32_t m, int prec, uint32_t n_out, dou
 
 CB_API int cb_ensemble_scores(cb_graph *h, uint32_t m, int prec, uint32_t n_out, double *S,
                               double *log_scale, cb_inst_report *rep, void *stream) {
+  NvtxRange nvtx_range("cb_ensemble_scores");
   if (!h || !S || !log_scale) return set_error(CB_ERR_ARG, "cb_ensemble_scores: null argument");
   if (m < 1 || m > CB_MAX_M) return set_error(CB_ERR_ARG, "cb_ensemble_scores: need 1 <= m <= CB_MAX_M");
   const bool reorth = split_prec(prec);

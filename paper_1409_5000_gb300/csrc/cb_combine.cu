@@ -150,6 +150,7 @@ int combine_single(cb_graph *h, uint32_t r, int prec, double *y, double *log_sca
 
 int combine_ensemble(cb_graph *h, int prec, uint32_t n_out, double *S, double *log_scale,
                      cudaStream_t s) {
+  NvtxRange nvtx_range("ensemble combine");
   const size_t shm = (sizeof(double) + sizeof(uint64_t) + sizeof(uint32_t)) * h->n_inst;
   if (shm > 200 * 1024) return set_error(CB_ERR_ARG, "too many realisations for one combine");
   const uint32_t grid = (n_out + 255) / 256;

@@ -341,6 +341,7 @@ using namespace cb;
 CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64_t *m_draws,
                                 uint64_t seed, uint32_t n_tedges, const uint32_t *tedges,
                                 void *stream, cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_generate_er");
   if (!out) return set_error(CB_ERR_ARG, "cb_graph_generate_er: out is null");
   *out = nullptr;
   if (n_inst == 0 || !n || !m_draws || (n_tedges && !tedges))

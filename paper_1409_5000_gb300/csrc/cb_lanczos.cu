@@ -924,6 +924,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
 int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m, int prec,
                 cudaStream_t s, const uint32_t *start_idx, uint32_t k, bool per_inst,
                 const double *restart_scale) {
+  NvtxRange nvtx_range("lanczos");
   return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k, per_inst, restart_scale)
                          : run_t<float>(h, W, r0, r1, m, s, start_idx, k, per_inst, restart_scale);
 }

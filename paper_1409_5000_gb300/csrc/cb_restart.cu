@@ -247,6 +247,7 @@ using namespace cb;
 CB_API int cb_ensemble_scores_restarted(cb_graph *h, uint32_t m, uint32_t cycles, int prec,
                                         uint32_t n_out, double *S, double *log_scale,
                                         cb_inst_report *rep, void *stream) {
+  NvtxRange nvtx_range("cb_ensemble_scores_restarted");
   if (!h || !S || !log_scale) return set_error(CB_ERR_ARG, "cb_ensemble_scores_restarted: null argument");
   if (m < 1 || m > CB_MAX_M)
     return set_error(CB_ERR_ARG, "cb_ensemble_scores_restarted: need 1 <= m <= CB_MAX_M");

@@ -87,6 +87,7 @@ using namespace cb;
 CB_API int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int prec, uint32_t k,
                                   const uint32_t *nodes, double *sc_scaled, double *log_scale,
                                   void *stream) {
+  NvtxRange nvtx_range("cb_subgraph_centrality");
   if (!h || !nodes || !sc_scaled || !log_scale)
     return set_error(CB_ERR_ARG, "cb_subgraph_centrality: null argument");
   if (inst >= h->n_inst) return set_error(CB_ERR_ARG, "cb_subgraph_centrality: realisation out of range");

@@ -207,6 +207,7 @@ size_t topk_scratch_bytes(uint32_t k) {
 
 CB_API int cb_topk(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
                    void *stream) {
+  cb::NvtxRange nvtx_range("cb_topk");
   using namespace cb;
   if (!S || !idx || !val) return set_error(CB_ERR_ARG, "cb_topk: null pointer");
   if (n == 0 || k == 0 || k > n || k > CB_MAX_TOPK)
@@ -273,6 +274,7 @@ int noalloc_scratch(void **out) {
 
 CB_API int cb_topk_noalloc(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
                            void *stream) {
+  cb::NvtxRange nvtx_range("cb_topk_noalloc");
   using namespace cb;
   if (!S || !idx || !val) return set_error(CB_ERR_ARG, "cb_topk_noalloc: null pointer");
   if (n == 0 || k == 0 || k > n)

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(32) tridiag_kernel(Scalars sc, const InstDesc 
 }
 
 int tridiag_run(cb_graph *h, uint32_t r0, uint32_t r1, int /*prec*/, cudaStream_t s) {
+  NvtxRange nvtx_range("tridiagonal exp");
   prefer_shared(tridiag_kernel);
   const int tok = prof_begin(CB_K_TRIDIAG, s);
   tridiag_kernel<<<r1 - r0, 32, 0, s>>>(h->ws.sc, h->d_inst, r0);
