@@ -80,14 +80,14 @@ def workload(name):
 # on the 40-realisation case of the default recipe; reported only while the
 # source that decides its traffic (kernel, epilogue, format builder, blocked
 # constants) still hashes to the captured version.
-_TRAFFIC = {"sources_sha256_16": "e13fcd5a746cf187", "bytes_per_edge": (778.355456e6 + 21.041408e6) / 151654698,
+_TRAFFIC = {"sources_sha256_16": "dd172533242e9175", "bytes_per_edge": (778.158080e6 + 21.209600e6) / 151654698,
             "kernel": "bspmv_kernel", "captured_on": "er-ensemble-40"}
 
 
 def _kernel_sources_hash():
     """Hash of the source that decides the blocked SpMV's memory traffic: the
     kernel and its staging helpers, the row epilogue, the blocked-format
-    builder and the blocked constants."""
+    kernels and the blocked constants."""
     import hashlib
     import re
 
@@ -101,7 +101,8 @@ def _kernel_sources_hash():
     a = lz.index("__device__ __forceinline__ T row_epilogue")
     parts.append(lz[a:lz.index("\n}\n", a)])
     with open(os.path.join(csrc, "cb_blocked.cu")) as f:
-        parts.append(f.read())
+        bl = f.read()  # the count and fill kernels (host code does not change the format)
+    parts.append(bl[bl.index("__global__"):bl.index("size_t fill_smem_bytes")])
     with open(os.path.join(csrc, "cb_internal.cuh")) as f:
         parts += re.findall(r"^constexpr [^\n]*\bk(?:B\w*|Threads|Group)\b[^\n]*$", f.read(), re.M)
     h = hashlib.sha256()
@@ -523,7 +524,7 @@ def main():
                     torch.cuda.current_stream().synchronize()  # this step only
                     g2.close()
 
-        n_pipe = max(3, min(args.steps, 5))
+        n_pipe = 8
         pipelined(2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
