@@ -22,8 +22,8 @@
 //     so they add +0.
 // Rows with more than kBLongDeg entries stay out of the streams; the SpMV
 // sums them from the CSR with whole-CTA global gathers.  Built on the device
-// from the CSR (one count pass, a host prefix over segment lengths, one
-// fill pass), once per upload.
+// from the CSR (one count pass per group of realisations as its copies land,
+// a device prefix over segment lengths, one fill pass), once per upload.
 #include <algorithm>
 #include <cstdlib>
 
@@ -162,6 +162,12 @@ size_t fill_smem_bytes(uint32_t nbmax) {
   return (size_t)nbmax * ((kFillThreads / 32) * 8 + kFillThreads * (4 * 2 + 2 + 4));
 }
 
+// x[i] *= 32: stream offsets in elements from the prefix of per-lane lengths
+__global__ void times32_kernel(uint64_t *x, uint64_t n) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= 32;
+}
+
 template <typename P>
 cudaError_t dalloc(P **p, size_t count) {
   return dev_alloc_n(p, count);
@@ -174,12 +180,13 @@ void free_blocked(cb_graph *h) {
   dev_free(h->d_bseg_base);
   dev_free(h->d_bwstart);
   dev_free(h->d_bwlen);
+  dev_free(h->d_bwscan);
   dev_free(h->d_bcol);
   dev_free(h->d_bslot);
   dev_free(h->d_blong_ptr);
   dev_free(h->d_blong_rows);
   h->d_btile_inst = nullptr;
-  h->d_bseg_base = h->d_bwstart = nullptr;
+  h->d_bseg_base = h->d_bwstart = h->d_bwscan = nullptr;
   h->d_bwlen = nullptr;
   h->d_bcol = nullptr;
   h->d_bslot = nullptr;
@@ -246,8 +253,9 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     const uint64_t nw = nseg * 32;
     chk(dalloc(&h->d_btile_inst, nbt));
     chk(dalloc(&h->d_bseg_base, nbt));
-    chk(dalloc(&h->d_bwstart, nw));
+    chk(dalloc(&h->d_bwstart, nw + 1));
     chk(dalloc(&h->d_bwlen, nw + 1));  // + the sortedness flag of the count pass
+    chk(dalloc(&h->d_bwscan, nw / 4096 + 2));  // prefix scratch
     chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
     chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
     if (e != cudaSuccess) {
@@ -278,20 +286,19 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       r_begin = g.r_end;
     }
     chk(cudaGetLastError());
-    std::vector<uint32_t> len(nw);
+    // stream offsets on the device: bwstart = 32 x the exclusive prefix of
+    // the lengths; only the total and the sortedness flag come back
+    if (e == cudaSuccess) chk(exclusive_scan(h->d_bwlen, nw, h->d_bwstart, h->d_bwscan, s));
+    if (e == cudaSuccess)
+      times32_kernel<<<(uint32_t)((nw + 1 + 255) / 256), 256, 0, s>>>(h->d_bwstart, nw + 1);
+    uint64_t tot = 0;
     uint32_t unsorted = 0;
-    chk(cudaMemcpyAsync(len.data(), h->d_bwlen, nw * 4, cudaMemcpyDeviceToHost, s));
+    chk(cudaMemcpyAsync(&tot, h->d_bwstart + nw, 8, cudaMemcpyDeviceToHost, s));
     chk(cudaMemcpyAsync(&unsorted, d_unsorted, 4, cudaMemcpyDeviceToHost, s));
     chk(cudaStreamSynchronize(s));
     if (e == cudaSuccess && unsorted) {
       free_blocked(h);
       return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
-    }
-    std::vector<uint64_t> start(nw);
-    uint64_t tot = 0;
-    for (uint64_t q = 0; q < nw; ++q) {
-      start[q] = tot;
-      tot += 32ull * len[q];
     }
     const uint64_t alloc = tot + 16;
     chk(dalloc(&h->d_bcol, alloc));
@@ -300,7 +307,6 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       static_assert((kBPadCol >> 8) == (kBPadCol & 0xff), "padding column must be a repeated byte");
       chk(cudaMemsetAsync(h->d_bcol, (int)(kBPadCol & 0xff), alloc * 2, s));  // padding: zero word
       chk(cudaMemsetAsync(h->d_bslot, 0, alloc, s));                          // into slot 0
-      chk(cudaMemcpyAsync(h->d_bwstart, start.data(), nw * 8, cudaMemcpyHostToDevice, s));
       uint32_t nbmax = 1;
       for (uint32_t r = 0; r < h->n_inst; ++r) nbmax = std::max(nbmax, h->inst[r].nb);
       const size_t shm = fill_smem_bytes(nbmax);

@@ -299,6 +299,8 @@ __global__ void scan_add_kernel(uint64_t *out, uint64_t n, const uint64_t *bsum,
   if (i == 0) out[n] = *total;
 }
 
+}  // namespace
+
 cudaError_t exclusive_scan(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *bsum,
                            cudaStream_t s) {
   const uint64_t nb = std::max<uint64_t>((n + kScanBlock - 1) / kScanBlock, 1);
@@ -307,6 +309,8 @@ cudaError_t exclusive_scan(const uint32_t *in, uint64_t n, uint64_t *out, uint64
   scan_add_kernel<<<(uint32_t)((n + 256) / 256), 256, 0, s>>>(out, n, bsum, bsum + nb);
   return cudaGetLastError();
 }
+
+namespace {
 
 __global__ void gather_bounds_kernel(const uint64_t *off2, const uint64_t *node_off,
                                      uint32_t n_inst, uint64_t *bound) {

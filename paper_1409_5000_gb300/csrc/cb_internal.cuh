@@ -149,6 +149,7 @@ struct cb_graph {
   uint32_t *d_btile_inst = nullptr;      // realisation of each blocked tile
   uint64_t *d_bseg_base = nullptr;       // first (tile, column block) segment of each tile
   uint64_t *d_bwstart = nullptr;         // per (segment, warp): first element of its region
+  uint64_t *d_bwscan = nullptr;          // scratch of the prefix that makes d_bwstart
   uint32_t *d_bwlen = nullptr;           // per (segment, warp): longest lane stream
   uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per element (padding: kBPadCol)
   uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane (padding: 0)
@@ -243,6 +244,10 @@ struct CopyGroup {
   uint32_t r_end;
   cudaEvent_t ev;
 };
+// Exclusive prefix of u32 counts into u64 offsets (cb_generate.cu):
+// out[0..n], out[n] = total; bsum holds n / 4096 + 2 u64 of scratch.
+cudaError_t exclusive_scan(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *bsum,
+                           cudaStream_t s);
 int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
                   const std::vector<CopyGroup> &groups);
 void free_blocked(cb_graph *h);
