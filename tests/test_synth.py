@@ -133,3 +133,15 @@ def test_er_generated_degree_and_independence():
     # realisations differ, and their degree variance is Poisson-like
     assert not np.array_equal(g0.col[:1000], g1.col[:1000])
     assert 6.5 < g0.degrees().var() < 9.5
+
+
+def test_ensemble_member_reproduces_the_ensemble():
+    """er_ensemble_member(r) is realisation r of er_ensemble, bit for bit (the
+    full-size parity tests rebuild realisations one by one in oracle workers)."""
+    sizes = synth.er_ensemble_uneven_sizes(5, 1_000, 4_000, 91)
+    ens = synth.er_ensemble_uneven(n_inst=5, n_lo=1_000, n_hi=4_000, config=91)
+    assert [g.n for g in ens.graphs] == sizes
+    for r in range(5):
+        g = synth.er_ensemble_member(sizes, 20.0, 30, 15, 91, r)
+        assert np.array_equal(g.row_ptr, ens.graphs[r].row_ptr)
+        assert np.array_equal(g.col, ens.graphs[r].col)
