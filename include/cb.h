@@ -144,6 +144,45 @@ int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64_t *m_d
                          uint64_t seed, uint32_t n_tedges, const uint32_t *tedges, void *stream,
                          cb_graph **out);
 
+/*
+ * cb_graph_generate_ws -- N Watts-Strogatz small-world backgrounds with one
+ * embedded target, generated on the device into a new handle (the paper's
+ * small-world backgrounds, Table 2 and the single-background scenario).
+ * Model: the ring lattice in which node i links to i + 1 .. i + k/2 (mod n),
+ * every ring edge rewired with probability p to a uniform node.  With the
+ * counter generator of cb_graph_generate_er, realisation r makes draws
+ * t = 0 .. n[r] k/2 - 1, c = r * 2^32 + t; draw t = i k/2 + (d - 1) is the
+ * edge (i, (i + d) mod n[r]), whose second end becomes
+ * (lo32(z) * n[r]) >> 32 when hi32(z) < floor(p * 2^32) (as 64-bit values,
+ * so p = 1 rewires every edge).  Self-loops are dropped and repeated pairs
+ * collapse; the target edges and the output are as cb_graph_generate_er.
+ *   k          even, 2 <= k < n[r] for every r.  p: 0 <= p <= 1.
+ *   other arguments as cb_graph_generate_er; need n[r] k/2 + n_tedges < 2^31.
+ */
+int cb_graph_generate_ws(uint32_t n_inst, const uint32_t *n, uint32_t k, double p, uint64_t seed,
+                         uint32_t n_tedges, const uint32_t *tedges, void *stream, cb_graph **out);
+
+/*
+ * cb_graph_generate_ba -- N Barabasi-Albert scale-free backgrounds with one
+ * embedded target, generated on the device into a new handle (the paper's
+ * scale-free backgrounds, single-background scenario).  Model: preferential
+ * attachment by the endpoint list of Batagelj & Brandes (Phys. Rev. E 71,
+ * 036113, 2005).  Nodes 0..m-1 are seeds; new node m + T (T = 0 .. n-m-1)
+ * adds m edges, edge t = T m + q.  The first new node links to the m seeds.
+ * Edge t of a later node links to the endpoint at position
+ * pos = (lo32(z_t) * 2 m T) >> 32 of the list of all earlier new nodes' edge
+ * endpoints (position 2e holds edge e's new node m + e/m, position 2e + 1
+ * its target), z_t the counter generator's output for c = r * 2^32 + t: a
+ * degree-proportional pick.  An odd position is resolved through the
+ * earlier edge e = pos >> 1 in the same way.  Repeated pairs collapse (a
+ * node that draws one target twice keeps one edge); the target edges and
+ * the output are as cb_graph_generate_er.
+ *   m          m >= 1 and n[r] > m for every r.
+ *   other arguments as cb_graph_generate_er; need m (n[r] - m) + n_tedges < 2^31.
+ */
+int cb_graph_generate_ba(uint32_t n_inst, const uint32_t *n, uint32_t m, uint64_t seed,
+                         uint32_t n_tedges, const uint32_t *tedges, void *stream, cb_graph **out);
+
 /* Number of CSR entries (2 x undirected edges) of realisation r; 0 when r is
  * out of range or h is null. */
 uint64_t cb_graph_num_entries(const cb_graph *h, uint32_t r);

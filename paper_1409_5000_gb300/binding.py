@@ -76,6 +76,11 @@ def lib():
         L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
         L.cb_graph_generate_er.restype = i32
         L.cb_graph_generate_er.argtypes = [u32, vp, vp, u64, u32, vp, vp, ctypes.POINTER(vp)]
+        L.cb_graph_generate_ws.restype = i32
+        L.cb_graph_generate_ws.argtypes = [u32, vp, u32, ctypes.c_double, u64, u32, vp, vp,
+                                           ctypes.POINTER(vp)]
+        L.cb_graph_generate_ba.restype = i32
+        L.cb_graph_generate_ba.argtypes = [u32, vp, u32, u64, u32, vp, vp, ctypes.POINTER(vp)]
         L.cb_scores_backward_budget.restype = i32
         L.cb_scores_backward_budget.argtypes = [vp, u32, i32, vp, u32, vp, vp, ctypes.c_size_t, vp]
         L.cb_graph_tune.restype = i32
@@ -166,6 +171,33 @@ def cb_graph_generate_er(n, m_draws, seed, tedges, stream):
     te_buf = te if len(te) else np.zeros((1, 2), np.uint32)
     out = ctypes.c_void_p()
     _check(lib().cb_graph_generate_er(N, n_arr.ctypes.data, m_arr.ctypes.data, seed & (2**64 - 1),
+                                      len(te), te_buf.ctypes.data, ctypes.c_void_p(stream),
+                                      ctypes.byref(out)))
+    return out.value
+
+
+def _target_buf(tedges):
+    te = np.zeros((0, 2), np.uint32) if tedges is None else np.ascontiguousarray(tedges, dtype=np.uint32).reshape(-1, 2)
+    return te, (te if len(te) else np.zeros((1, 2), np.uint32))
+
+
+def cb_graph_generate_ws(n, k, p, seed, tedges, stream):
+    """Returns the handle (int).  tedges: None or an (E, 2) integer array."""
+    n_arr = np.ascontiguousarray(n, dtype=np.uint32)
+    te, te_buf = _target_buf(tedges)
+    out = ctypes.c_void_p()
+    _check(lib().cb_graph_generate_ws(len(n_arr), n_arr.ctypes.data, int(k), float(p),
+                                      seed & (2**64 - 1), len(te), te_buf.ctypes.data,
+                                      ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
+
+
+def cb_graph_generate_ba(n, m, seed, tedges, stream):
+    """Returns the handle (int).  tedges: None or an (E, 2) integer array."""
+    n_arr = np.ascontiguousarray(n, dtype=np.uint32)
+    te, te_buf = _target_buf(tedges)
+    out = ctypes.c_void_p()
+    _check(lib().cb_graph_generate_ba(len(n_arr), n_arr.ctypes.data, int(m), seed & (2**64 - 1),
                                       len(te), te_buf.ctypes.data, ctypes.c_void_p(stream),
                                       ctypes.byref(out)))
     return out.value
@@ -378,6 +410,32 @@ class GraphSet:
         self.nnz = [cb_graph_num_entries(self.h, r) for r in range(len(n))]
         self.n_max = max(n)
         return self
+
+    @classmethod
+    def _from_handle(cls, h, n):
+        import torch
+
+        self = cls.__new__(cls)
+        self.device = torch.cuda.current_device()
+        self.h = h
+        self.n = [int(x) for x in n]
+        self.nnz = [cb_graph_num_entries(self.h, r) for r in range(len(self.n))]
+        self.n_max = max(self.n)
+        return self
+
+    @classmethod
+    def generate_ws(cls, n, k, p, seed, target_edges=None, stream=None):
+        """N Watts-Strogatz backgrounds generated on the device (cb_graph_generate_ws)."""
+        n = [int(x) for x in n]
+        return cls._from_handle(cb_graph_generate_ws(n, k, p, seed, target_edges,
+                                                     _stream_handle(stream)), n)
+
+    @classmethod
+    def generate_ba(cls, n, m, seed, target_edges=None, stream=None):
+        """N Barabasi-Albert backgrounds generated on the device (cb_graph_generate_ba)."""
+        n = [int(x) for x in n]
+        return cls._from_handle(cb_graph_generate_ba(n, m, seed, target_edges,
+                                                     _stream_handle(stream)), n)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,17 +1,30 @@
-// On-device generation of Erdos-Renyi backgrounds with one embedded target:
-// the N realisations that eq. 5 sums over (paper, "Multiple backgrounds
-// scenario"), built straight into a handle so that they never cross the
-// host-device link.
+// On-device generation of the background realisations, each with one
+// embedded target: the N graphs that eq. 5 sums over (paper, "Multiple
+// backgrounds scenario"), built straight into a handle so that they never
+// cross the host-device link.  Three models, each a reading of the paper's
+// ER / small-world / scale-free backgrounds in which every decision is
+// integer arithmetic on one counter-based generator, so that a CPU statement
+// of the same definition can be compared bit for bit.
 //
-// Model (a fixed-draw G(n, M) reading of the paper's ER backgrounds).
-// SplitMix64 in counter form, output(c) = mix(seed + (c + 1) G) with
-// G = 0x9E3779B97F4A7C15 and mix the generator's output function (Steele,
-// Lea & Flood, OOPSLA 2014).  Realisation r takes draws t = 0 .. M_r - 1 with
-// counter c = r * 2^32 + t; draw t is the pair u = (hi32(z) n_r) >> 32,
-// v = (lo32(z) n_r) >> 32.  Draws with u == v are dropped, repeated pairs
-// collapse, the target's edges are OR-ed into every realisation (those with
-// an endpoint >= n_r are skipped), and rows come out sorted: a simple
-// undirected graph as a symmetric CSR pattern.
+// Generator: SplitMix64 in counter form, output(c) = mix(seed + (c + 1) G)
+// with G = 0x9E3779B97F4A7C15 and mix the generator's output function
+// (Steele, Lea & Flood, OOPSLA 2014).  Realisation r makes draws
+// t = 0 .. D_r - 1 with counter c = r * 2^32 + t; z is the output.
+//  * ER (a fixed-draw G(n, M) reading): D_r = M_r; draw t is the pair
+//    u = (hi32(z) n_r) >> 32, v = (lo32(z) n_r) >> 32.
+//  * WS (Watts & Strogatz): D_r = n_r k/2; draw t = i k/2 + (d - 1) is the
+//    ring edge (i, (i + d) mod n_r), d = 1..k/2, rewired to
+//    v = (lo32(z) n_r) >> 32 when hi32(z) < floor(p 2^32).
+//  * BA (Barabasi & Albert, by the endpoint list of Batagelj & Brandes):
+//    nodes 0..m-1 are seeds; draw t is edge t of new node m + t/m; the first
+//    new node links to the m seeds, and a later one to the endpoint at a
+//    uniform position of the list of all earlier new nodes' edge endpoints,
+//    a degree-proportional pick (see ba_target).
+// In every model self-loops are dropped, repeated pairs collapse (so a WS
+// rewiring onto an existing edge, or a BA node drawing one target twice,
+// leaves fewer edges), the target's edges are OR-ed into every realisation
+// (those with an endpoint >= n_r are skipped), and rows come out sorted: a
+// simple undirected graph as a symmetric CSR pattern.
 //
 // Construction: count the entries of every row (atomics), prefix, scatter
 // (atomic cursors), sort and de-duplicate each row, prefix again, compact.
@@ -19,6 +32,8 @@
 // the result does not depend on their order.  The handle is then built by
 // cb_graph_upload from the device arrays.
 #include <algorithm>
+#include <cmath>
+#include <string>
 #include <vector>
 
 #include "cb_internal.cuh"
@@ -37,16 +52,45 @@ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+enum GenKind : int { kGenER = 0, kGenWS = 1, kGenBA = 2 };
+
 struct GenArgs {
   uint32_t n_inst;
   const uint32_t *n;         // [N] nodes per realisation
   const uint64_t *node_off;  // [N + 1] prefix of n
-  const uint64_t *draw_off;  // [N + 1] prefix of M
+  const uint64_t *draw_off;  // [N + 1] prefix of the draws
   uint64_t seed;
   const uint32_t *tedges;    // [E][2] target edges
   uint32_t n_tedges;
   uint64_t items;            // draws + N * E
+  int kind;
+  uint32_t k_half;           // WS: ring neighbours per side
+  uint64_t p32;              // WS: rewire when hi32(z) < p32 = floor(p 2^32)
+  uint32_t m_ba;             // BA: edges per new node (and seeds)
 };
+
+__device__ __forceinline__ uint64_t gen_z(const GenArgs &a, uint32_t r, uint64_t t) {
+  return sm64_mix(a.seed + ((((uint64_t)r << 32) + t) + 1) * kGolden);
+}
+
+// BA target of edge t of realisation r: edge t belongs to new node
+// m + t / m and points at the endpoint at a uniform position of the
+// endpoint list of the edges of all earlier new nodes (positions
+// [0, 2 m T), T = t / m; even position 2e' holds the new node of edge e',
+// odd position 2e' + 1 its target).  The first new node (T = 0) links to the
+// m seeds.  An odd position is resolved through edge e', an earlier edge, so
+// the walk ends; it takes about two steps on average.
+__device__ __forceinline__ uint32_t ba_target(const GenArgs &a, uint32_t r, uint64_t t) {
+  const uint64_t m = a.m_ba;
+  for (;;) {
+    const uint64_t T = t / m;
+    if (T == 0) return (uint32_t)t;  // seed t
+    const uint64_t z = gen_z(a, r, t);
+    const uint64_t pos = ((z & 0xffffffffull) * (2 * m * T)) >> 32;
+    if (!(pos & 1)) return (uint32_t)(m + (pos >> 1) / m);
+    t = pos >> 1;
+  }
+}
 
 // Work item g -> realisation r and pair (u, v); false when it makes no edge.
 __device__ __forceinline__ bool gen_item(const GenArgs &a, uint64_t g, uint32_t &r, uint32_t &u,
@@ -60,10 +104,21 @@ __device__ __forceinline__ bool gen_item(const GenArgs &a, uint64_t g, uint32_t 
     }
     r = lo;
     const uint64_t t = g - a.draw_off[r];
-    const uint64_t z = sm64_mix(a.seed + ((((uint64_t)r << 32) + t) + 1) * kGolden);
     const uint64_t nr = a.n[r];
-    u = (uint32_t)(((z >> 32) * nr) >> 32);
-    v = (uint32_t)(((z & 0xffffffffull) * nr) >> 32);
+    if (a.kind == kGenER) {
+      const uint64_t z = gen_z(a, r, t);
+      u = (uint32_t)(((z >> 32) * nr) >> 32);
+      v = (uint32_t)(((z & 0xffffffffull) * nr) >> 32);
+    } else if (a.kind == kGenWS) {
+      const uint64_t i = t / a.k_half, d = t % a.k_half + 1;
+      const uint64_t z = gen_z(a, r, t);
+      u = (uint32_t)i;
+      v = (uint32_t)((i + d) % nr);
+      if ((z >> 32) < a.p32) v = (uint32_t)(((z & 0xffffffffull) * nr) >> 32);  // rewired
+    } else {
+      u = (uint32_t)(a.m_ba + t / a.m_ba);
+      v = ba_target(a, r, t);
+    }
   } else {
     const uint64_t q = g - D;
     r = (uint32_t)(q / a.n_tedges);
@@ -121,14 +176,32 @@ __device__ __forceinline__ uint32_t bitonic_cx(uint32_t x, uint32_t y, bool keep
   return keep_min ? min(x, y) : max(x, y);
 }
 
+// Rows of more than 64 raw entries are sorted by whole CTAs in shared memory
+// (gen_sort_block_kernel): up to kSortMid entries by small CTAs, up to
+// kSortBig by large ones; their rows are listed from the two ends of one
+// array.  Rows beyond kSortBig (a degree above 32768 before de-duplication)
+// keep a serial insertion sort.
+constexpr uint32_t kSortMid = 1024, kSortBig = 32768;
+
 __global__ void __launch_bounds__(kGenThreads) gen_sort_kernel(const uint64_t *off, uint32_t *raw,
-                                                               uint32_t *deg, uint64_t rows) {
+                                                               uint32_t *deg, uint64_t rows,
+                                                               uint32_t *long_rows,
+                                                               uint32_t *long_cnt) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < rows;
        i += warps) {
     uint32_t *p = raw + off[i];
     const uint32_t d = (uint32_t)(off[i + 1] - off[i]);
+    if (d > 64 && d <= kSortBig) {  // a CTA sorts it
+      if (lane == 0) {
+        if (d <= kSortMid)
+          long_rows[atomicAdd(&long_cnt[0], 1u)] = (uint32_t)i;
+        else
+          long_rows[rows - 1 - atomicAdd(&long_cnt[1], 1u)] = (uint32_t)i;
+      }
+      continue;
+    }
     if (d > 64) {
       uint32_t w = 0;
       if (lane == 0) {
@@ -324,6 +397,45 @@ uint32_t grid_for(uint64_t work) {
 }
 
 // device buffers of one generation call, freed on every exit path
+// One CTA per listed row: bitonic sort of the row (padded with UINT32_MAX
+// to a power of two) in shared memory, then thread 0 writes the distinct
+// values back and sets the row's degree.  rows_from_end: the row list is
+// read from the end of the array (the large rows).
+template <uint32_t CAP>
+__global__ void gen_sort_block_kernel(const uint64_t *off, uint32_t *raw, uint32_t *deg,
+                                      const uint32_t *long_rows, uint64_t rows,
+                                      bool rows_from_end) {
+  extern __shared__ uint32_t s_row[];
+  const uint32_t i = rows_from_end ? long_rows[rows - 1 - blockIdx.x] : long_rows[blockIdx.x];
+  uint32_t *p = raw + off[i];
+  const uint32_t d = (uint32_t)(off[i + 1] - off[i]);
+  uint32_t P = 1;
+  while (P < d) P <<= 1;
+  for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) s_row[q] = q < d ? p[q] : 0xffffffffu;
+  __syncthreads();
+  for (uint32_t k = 2; k <= P; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
+        const uint32_t u = t ^ j;
+        if (u > t) {
+          const uint32_t a = s_row[t], b = s_row[u];
+          const bool asc = (t & k) == 0;
+          if ((a > b) == asc) {
+            s_row[t] = b;
+            s_row[u] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) {
+    uint32_t w = 0;
+    for (uint32_t q = 0; q < d; ++q)
+      if (q == 0 || s_row[q] != s_row[q - 1]) p[w++] = s_row[q];
+    deg[i] = w;
+  }
+}
+
 struct GenBuffers {
   std::vector<void *> ptrs;
   template <typename P>
@@ -342,27 +454,24 @@ struct GenBuffers {
 
 using namespace cb;
 
-CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64_t *m_draws,
-                                uint64_t seed, uint32_t n_tedges, const uint32_t *tedges,
-                                void *stream, cb_graph **out) {
-  NvtxRange nvtx_range("cb_graph_generate_er");
-  if (!out) return set_error(CB_ERR_ARG, "cb_graph_generate_er: out is null");
-  *out = nullptr;
-  if (n_inst == 0 || !n || !m_draws || (n_tedges && !tedges))
-    return set_error(CB_ERR_ARG, "cb_graph_generate_er: empty input or null array");
+// The construction shared by the three models: per-realisation draw counts
+// in `draws`; the model's parameters in `kp` (kind, k_half, p32, m_ba).
+static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const uint32_t *n,
+                    const std::vector<uint64_t> &draws, uint64_t seed, uint32_t n_tedges,
+                    const uint32_t *tedges, void *stream, cb_graph **out) {
+  auto fail = [&](const char *what) { return set_error(CB_ERR_ARG, std::string(who) + ": " + what); };
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::vector<uint64_t> node_off(n_inst + 1, 0), draw_off(n_inst + 1, 0);
   for (uint32_t r = 0; r < n_inst; ++r) {
-    if (n[r] == 0) return set_error(CB_ERR_ARG, "cb_graph_generate_er: realisation with n = 0");
-    if (m_draws[r] + n_tedges >= (1ull << 31))  // 2 entries per draw, 32-bit cursors
-      return set_error(CB_ERR_ARG, "cb_graph_generate_er: need m_draws + n_tedges < 2^31 per realisation");
+    if (draws[r] + n_tedges >= (1ull << 31))  // 2 entries per draw, 32-bit cursors
+      return fail("need draws + n_tedges < 2^31 per realisation");
     node_off[r + 1] = node_off[r] + n[r];
-    draw_off[r + 1] = draw_off[r] + m_draws[r];
+    draw_off[r + 1] = draw_off[r] + draws[r];
   }
   for (uint32_t e = 0; e < 2 * n_tedges; ++e)
-    if (tedges[e] >= (1u << 31))
-      return set_error(CB_ERR_ARG, "cb_graph_generate_er: target edge endpoint out of range");
+    if (tedges[e] >= (1u << 31)) return fail("target edge endpoint out of range");
   const uint64_t rows = node_off[n_inst];
+  if (rows >= 0xffffffffull) return fail("need fewer than 2^32 nodes over all realisations");
   const uint64_t items = draw_off[n_inst] + (uint64_t)n_inst * n_tedges;
 
   GenBuffers B;
@@ -387,13 +496,24 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   chk(B.alloc(&bsum, (rows + kScanBlock - 1) / kScanBlock + 2));
   chk(B.alloc(&bound, n_inst + 1));
   chk(B.alloc(&ebase, n_inst + 1));
-  if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: allocate");
+  uint32_t *long_rows = nullptr, *long_cnt = nullptr;
+  chk(B.alloc(&long_rows, std::max<uint64_t>(rows, 1)));
+  chk(B.alloc(&long_cnt, 2));
+  if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": allocate").c_str());
   chk(cudaMemcpyAsync(d_n, n, n_inst * 4, cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(d_node_off, node_off.data(), (n_inst + 1) * 8, cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(d_draw_off, draw_off.data(), (n_inst + 1) * 8, cudaMemcpyHostToDevice, s));
   if (n_tedges) chk(cudaMemcpyAsync(d_tedges, tedges, 8ull * n_tedges, cudaMemcpyHostToDevice, s));
   chk(cudaMemsetAsync(deg, 0, rows * 4, s));
-  GenArgs a{n_inst, d_n, d_node_off, d_draw_off, seed, d_tedges, n_tedges, items};
+  GenArgs a = kp;
+  a.n_inst = n_inst;
+  a.n = d_n;
+  a.node_off = d_node_off;
+  a.draw_off = d_draw_off;
+  a.seed = seed;
+  a.tedges = d_tedges;
+  a.n_tedges = n_tedges;
+  a.items = items;
   if (e == cudaSuccess) {
     gen_count_kernel<<<grid_for(items), kGenThreads, 0, s>>>(a, deg);
     chk(cudaGetLastError());
@@ -402,14 +522,29 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   uint64_t entries = 0;
   chk(cudaMemcpyAsync(&entries, off + rows, 8, cudaMemcpyDeviceToHost, s));
   chk(cudaStreamSynchronize(s));
-  if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: count");
+  if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": count").c_str());
   chk(B.alloc(&raw, std::max<uint64_t>(entries, 1)));
-  if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: allocate entries");
+  if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": allocate entries").c_str());
   if (e == cudaSuccess) {
     gather_bounds_kernel<<<(n_inst + 256) / 256, 256, 0, s>>>(off, d_node_off, n_inst, ebase);
     gen_cursor_kernel<<<grid_for(rows), kGenThreads, 0, s>>>(a, off, ebase, cursor, rows);
     gen_fill_kernel<<<grid_for(items), kGenThreads, 0, s>>>(a, ebase, cursor, raw);
-    gen_sort_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(off, raw, deg, rows);
+    chk(cudaMemsetAsync(long_cnt, 0, 8, s));
+    gen_sort_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(off, raw, deg, rows, long_rows,
+                                                                long_cnt);
+    chk(cudaGetLastError());
+    uint32_t nl[2] = {0, 0};
+    chk(cudaMemcpyAsync(nl, long_cnt, 8, cudaMemcpyDeviceToHost, s));
+    chk(cudaStreamSynchronize(s));
+    if (e == cudaSuccess && nl[0])
+      gen_sort_block_kernel<kSortMid><<<nl[0], 256, kSortMid * 4, s>>>(off, raw, deg, long_rows,
+                                                                      rows, false);
+    if (e == cudaSuccess && nl[1]) {
+      chk(cudaFuncSetAttribute(gen_sort_block_kernel<kSortBig>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSortBig * 4)));
+      gen_sort_block_kernel<kSortBig><<<nl[1], 1024, kSortBig * 4, s>>>(off, raw, deg, long_rows,
+                                                                       rows, true);
+    }
     chk(cudaGetLastError());
     chk(exclusive_scan(deg, rows, off2, bsum, s));
     gather_bounds_kernel<<<(n_inst + 256) / 256, 256, 0, s>>>(off2, d_node_off, n_inst, bound);
@@ -418,20 +553,20 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   std::vector<uint64_t> hb(n_inst + 1, 0);
   chk(cudaMemcpyAsync(hb.data(), bound, (n_inst + 1) * 8, cudaMemcpyDeviceToHost, s));
   chk(cudaStreamSynchronize(s));
-  if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: build rows");
+  if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": build rows").c_str());
   std::vector<uint64_t> nnz(n_inst);
   for (uint32_t r = 0; r < n_inst; ++r) {
     nnz[r] = hb[r + 1] - hb[r];
     if (nnz[r] >= 0xffffffffull)
-      return set_error(CB_ERR_ARG, "cb_graph_generate_er: a realisation has >= 2^32 entries");
+      return fail("a realisation has >= 2^32 entries");
   }
   chk(B.alloc(&col, std::max<uint64_t>(hb[n_inst], 1)));
   chk(B.alloc(&rp, rows + n_inst));
-  if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: allocate CSR");
+  if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": allocate CSR").c_str());
   gen_compact_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(a, off, raw, off2, col, rp, rows);
   chk(cudaGetLastError());
   chk(cudaStreamSynchronize(s));  // the upload reads row_ptr back with a plain copy
-  if (e != cudaSuccess) return cuda_error(e, "cb_graph_generate_er: compact");
+  if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": compact").c_str());
   std::vector<const uint32_t *> rpp(n_inst), colp(n_inst);
   for (uint32_t r = 0; r < n_inst; ++r) {
     rpp[r] = rp + node_off[r] + r;
@@ -441,4 +576,69 @@ CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64
   // the temporaries are freed when B goes out of scope
   return cb_graph_upload(n_inst, n, nnz.data(), rpp.data(), colp.data(), CB_DEVICE_PTRS, stream,
                          out);
+}
+
+static int check_common(const char *who, uint32_t n_inst, const uint32_t *n, uint32_t n_tedges,
+                        const uint32_t *tedges, cb_graph **out) {
+  if (!out) return set_error(CB_ERR_ARG, std::string(who) + ": out is null");
+  *out = nullptr;
+  if (n_inst == 0 || !n || (n_tedges && !tedges))
+    return set_error(CB_ERR_ARG, std::string(who) + ": empty input or null array");
+  for (uint32_t r = 0; r < n_inst; ++r)
+    if (n[r] == 0) return set_error(CB_ERR_ARG, std::string(who) + ": realisation with n = 0");
+  return CB_OK;
+}
+
+CB_API int cb_graph_generate_er(uint32_t n_inst, const uint32_t *n, const uint64_t *m_draws,
+                                uint64_t seed, uint32_t n_tedges, const uint32_t *tedges,
+                                void *stream, cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_generate_er");
+  const char *who = "cb_graph_generate_er";
+  int rc = check_common(who, n_inst, n, n_tedges, tedges, out);
+  if (rc != CB_OK) return rc;
+  if (!m_draws) return set_error(CB_ERR_ARG, "cb_graph_generate_er: empty input or null array");
+  GenArgs kp{};
+  kp.kind = kGenER;
+  return generate(kp, who, n_inst, n, std::vector<uint64_t>(m_draws, m_draws + n_inst), seed,
+                  n_tedges, tedges, stream, out);
+}
+
+CB_API int cb_graph_generate_ws(uint32_t n_inst, const uint32_t *n, uint32_t k, double p,
+                                uint64_t seed, uint32_t n_tedges, const uint32_t *tedges,
+                                void *stream, cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_generate_ws");
+  const char *who = "cb_graph_generate_ws";
+  int rc = check_common(who, n_inst, n, n_tedges, tedges, out);
+  if (rc != CB_OK) return rc;
+  if (k < 2 || (k & 1)) return set_error(CB_ERR_ARG, "cb_graph_generate_ws: k must be even and >= 2");
+  if (!(p >= 0.0 && p <= 1.0)) return set_error(CB_ERR_ARG, "cb_graph_generate_ws: need 0 <= p <= 1");
+  std::vector<uint64_t> draws(n_inst);
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    if (k >= n[r]) return set_error(CB_ERR_ARG, "cb_graph_generate_ws: need k < n");
+    draws[r] = (uint64_t)n[r] * (k / 2);
+  }
+  GenArgs kp{};
+  kp.kind = kGenWS;
+  kp.k_half = k / 2;
+  kp.p32 = (uint64_t)std::floor(p * 4294967296.0);  // 2^32 at p = 1: every edge rewired
+  return generate(kp, who, n_inst, n, draws, seed, n_tedges, tedges, stream, out);
+}
+
+CB_API int cb_graph_generate_ba(uint32_t n_inst, const uint32_t *n, uint32_t m, uint64_t seed,
+                                uint32_t n_tedges, const uint32_t *tedges, void *stream,
+                                cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_generate_ba");
+  const char *who = "cb_graph_generate_ba";
+  int rc = check_common(who, n_inst, n, n_tedges, tedges, out);
+  if (rc != CB_OK) return rc;
+  if (m < 1) return set_error(CB_ERR_ARG, "cb_graph_generate_ba: need m >= 1");
+  std::vector<uint64_t> draws(n_inst);
+  for (uint32_t r = 0; r < n_inst; ++r) {
+    if (n[r] <= m) return set_error(CB_ERR_ARG, "cb_graph_generate_ba: need n > m");
+    draws[r] = (uint64_t)m * (n[r] - m);
+  }
+  GenArgs kp{};
+  kp.kind = kGenBA;
+  kp.m_ba = m;
+  return generate(kp, who, n_inst, n, draws, seed, n_tedges, tedges, stream, out);
 }

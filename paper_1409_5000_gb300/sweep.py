@@ -10,16 +10,17 @@ settings are not available, so each column is rebuilt synthetically:
   cb_graph_generate_er) and a sparse 20-node target -- a random tree plus 2
   extra edges, i.e. 21 edges, mean degree 2.1 and density 0.11 as in the
   paper; hub degrees are not controlled.
-* Table 2: N Watts-Strogatz backgrounds (n = 1024, k = 40, rewiring 0.1) and a
-  20-clique.
-* Table 3: one background (ER mean degree 39, WS k = 60, BA m = 10) and a
-  20-clique.
+* Table 2: N Watts-Strogatz backgrounds (n = 1024, k = 40, rewiring 0.1;
+  cb_graph_generate_ws) and a 20-clique.
+* Table 3: one background (ER mean degree 39, WS k = 60, BA m = 10;
+  cb_graph_generate_ba for BA) and a 20-clique.
 * ``--scale``: the single-background clique relaxation at scale -- ER, WS and
   BA backgrounds of mean degree 20, 40 and 60 with n = 1024, 16384 and 1e5.
 
 Per run the target node set is drawn afresh and shared by the run's N
 realisations (eq. 5); the rate of a run is |top-k intersect target| / k.
-Every step of the scoring runs through the library (ensemble scores and
+Every background is generated on the device, and every step of the scoring
+runs through the library (ensemble scores and
 top-k on the GPU).  The numbers are reported, not pinned: they are
 statistical outcomes of synthetic recipes, and the paper's figures are
 context.
@@ -77,11 +78,9 @@ def run_once(B, kind, n, param, N, target, seed, m, prec=None):
     if kind == "er":
         gs = B.GraphSet.generate_er([n] * N, float(param), synth.seed_for(seed, 1), tedges)
     elif kind == "ws":
-        gs = B.GraphSet([synth.ws(n, int(param), WS_REWIRE, synth.seed_for(seed, 2 + r), tedges)
-                         for r in range(N)])
+        gs = B.GraphSet.generate_ws([n] * N, int(param), WS_REWIRE, synth.seed_for(seed, 1), tedges)
     elif kind == "ba":
-        gs = B.GraphSet([synth.ba(n, int(param), synth.seed_for(seed, 2 + r), tedges)
-                         for r in range(N)])
+        gs = B.GraphSet.generate_ba([n] * N, int(param), synth.seed_for(seed, 1), tedges)
     else:
         raise ValueError(kind)
     try:

@@ -22,6 +22,8 @@ import os
 from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 
 SEED_BASE = 14095000
@@ -194,6 +196,83 @@ def er_generated(n: int, m_draws: int, seed: int, r: int, target_edges=None) -> 
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.add.at(row_ptr, rows + 1, 1)
     return Graph(int(n), np.cumsum(row_ptr).astype(np.uint32), (key % n).astype(np.uint32))
+
+
+def _pairs_to_graph(n: int, u, v, target_edges=None) -> Graph:
+    """Symmetric sorted CSR of the pairs (u, v) plus target edges with both
+    ends < n; self-loops dropped, repeats collapsed."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    if target_edges is not None and len(target_edges):
+        te = np.asarray(target_edges, dtype=np.int64).reshape(-1, 2)
+        te = te[(te[:, 0] < n) & (te[:, 1] < n)]
+        u = np.concatenate([u, te[:, 0]])
+        v = np.concatenate([v, te[:, 1]])
+    keep = u != v
+    u, v = u[keep], v[keep]
+    key = np.unique(np.concatenate([u * n + v, v * n + u]))
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, key // n + 1, 1)
+    return Graph(int(n), np.cumsum(row_ptr).astype(np.uint32), (key % n).astype(np.uint32))
+
+
+def ws_threshold(p: float) -> int:
+    """Rewiring threshold floor(p 2^32) (2^32 at p = 1: every edge rewired)."""
+    return int(math.floor(float(p) * 4294967296.0))
+
+
+def ws_generated(n: int, k: int, p: float, seed: int, r: int, target_edges=None) -> Graph:
+    """Realisation r of the counter-based Watts-Strogatz recipe: ring edge
+    (i, (i + d) mod n), d = 1..k/2, as draw t = i k/2 + d - 1, rewired to
+    (lo32(z) n) >> 32 when hi32(z) < floor(p 2^32)."""
+    kh = k // 2
+    t = np.arange(n * kh, dtype=np.uint64)
+    z = sm64_counter(seed, (np.uint64(r) << np.uint64(32)) + t)
+    i = (t // np.uint64(kh)).astype(np.int64)
+    d = (t % np.uint64(kh)).astype(np.int64) + 1
+    v = (i + d) % n
+    with np.errstate(over="ignore"):
+        rew = (z >> np.uint64(32)).astype(np.int64) < ws_threshold(p)
+        nv = (((z & np.uint64(0xFFFFFFFF)) * np.uint64(n)) >> np.uint64(32)).astype(np.int64)
+    v = np.where(rew, nv, v)
+    return _pairs_to_graph(n, i, v, target_edges)
+
+
+def ba_targets(n: int, m: int, seed: int, r: int) -> np.ndarray:
+    """Targets of the m (n - m) edges of the counter-based Batagelj-Brandes
+    recipe: edge t of new node m + t/m picks position
+    (lo32(z_t) 2 m T) >> 32, T = t/m, of the earlier endpoint list (even
+    2e: node m + e/m; odd 2e + 1: the target of edge e); the first new node
+    links to the seeds.  Resolved for all edges at once, step by step."""
+    E = m * (n - m)
+    t0 = np.arange(E, dtype=np.int64)
+    out = np.full(E, -1, dtype=np.int64)
+    cur = t0.copy()  # the edge whose target is still needed
+    live = np.ones(E, dtype=bool)
+    while live.any():
+        idx = np.nonzero(live)[0]
+        e = cur[idx]
+        T = e // m
+        seed_hit = T == 0
+        out[idx[seed_hit]] = e[seed_hit]
+        rest = ~seed_hit
+        idx, e, T = idx[rest], e[rest], T[rest]
+        z = sm64_counter(seed, (np.uint64(r) << np.uint64(32)) + e.astype(np.uint64))
+        with np.errstate(over="ignore"):
+            pos = (((z & np.uint64(0xFFFFFFFF)) * (np.uint64(2 * m) * T.astype(np.uint64)))
+                   >> np.uint64(32)).astype(np.int64)
+        even = (pos & 1) == 0
+        out[idx[even]] = m + (pos[even] >> 1) // m
+        cur[idx[~even]] = pos[~even] >> 1
+        live[:] = False
+        live[idx[~even]] = True
+    return out
+
+
+def ba_generated(n: int, m: int, seed: int, r: int, target_edges=None) -> Graph:
+    """Realisation r of the counter-based Barabasi-Albert recipe."""
+    t = np.arange(m * (n - m), dtype=np.int64)
+    return _pairs_to_graph(n, m + t // m, ba_targets(n, m, seed, r), target_edges)
 
 
 def er(n: int, p: float, seed: int, extra_edges=None) -> Graph:

@@ -3,7 +3,7 @@ graphs (needs a GB300).
 
 The sweep's rate is |top-k of eq. 5 intersect target| / k.  For small
 columns the oracle computes the same quantity from the same graphs (the
-device ER generator's CPU statement, or the host WS generator) in FP64; the
+device generators' CPU statements) in FP64; the
 GPU path in FP64 mode must pick the same top-k set.
 """
 import numpy as np
@@ -32,19 +32,20 @@ def _oracle_rate(kind, n, param, N, target, seed, m):
     nodes = synth.sample_nodes(n, sweep.K, synth.seed_for(seed, 0, salt=11))
     tedges = synth.target_edges(nodes, sweep.SPARSE_EXTRA if target == "sparse" else 0,
                                 target == "clique", synth.seed_for(seed, 0, salt=12))
+    s1 = synth.seed_for(seed, 1)
     if kind == "er":
-        s1 = synth.seed_for(seed, 1)
         graphs = [synth.er_generated(n, synth.er_draw_count(n, param), s1, r, tedges) for r in range(N)]
+    elif kind == "ws":
+        graphs = [synth.ws_generated(n, int(param), sweep.WS_REWIRE, s1, r, tedges) for r in range(N)]
     else:
-        graphs = [synth.ws(n, int(param), sweep.WS_REWIRE, synth.seed_for(seed, 2 + r), tedges)
-                  for r in range(N)]
+        graphs = [synth.ba_generated(n, int(param), s1, r, tedges) for r in range(N)]
     th, S = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], m)
     idx, _ = oc.topk(S, sweep.K)
     return len(set(np.asarray(idx).tolist()) & set(nodes.tolist())) / sweep.K
 
 
 @pytest.mark.parametrize("col", [("er", 600, 2.0, 4, "sparse"), ("er", 1024, 39.0, 1, "clique"),
-                                 ("ws", 500, 20, 2, "clique")])
+                                 ("ws", 500, 20, 2, "clique"), ("ba", 600, 5, 1, "clique")])
 def test_sweep_run_matches_oracle(B, col):
     from paper_1409_5000_gb300 import sweep
 

@@ -145,3 +145,81 @@ def test_ensemble_member_reproduces_the_ensemble():
         g = synth.er_ensemble_member(sizes, 20.0, 30, 15, 91, r)
         assert np.array_equal(g.row_ptr, ens.graphs[r].row_ptr)
         assert np.array_equal(g.col, ens.graphs[r].col)
+
+
+def _sm64(seed, c):
+    """One counter draw, plain Python integers."""
+    M = 2**64 - 1
+    z = (seed + (c + 1) * 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def _edges(g):
+    return {(i, int(j)) for i in range(g.n) for j in g.col[g.row_ptr[i]:g.row_ptr[i + 1]] if i < j}
+
+
+def test_ws_statement_equals_plain_loop():
+    n, k, seed, r = 40, 6, 123, 3
+    for p in (0.0, 0.3, 1.0):
+        thr = synth.ws_threshold(p)
+        want = set()
+        for i in range(n):
+            for d in range(1, k // 2 + 1):
+                z = _sm64(seed, (r << 32) + i * (k // 2) + d - 1)
+                j = (i + d) % n
+                if (z >> 32) < thr:
+                    j = ((z & 0xFFFFFFFF) * n) >> 32
+                if j != i:
+                    want.add((min(i, j), max(i, j)))
+        assert _edges(synth.ws_generated(n, k, p, seed, r)) == want, p
+
+
+def test_ws_without_rewiring_is_the_ring_lattice():
+    n, k = 50, 8
+    g = synth.ws_generated(n, k, 0.0, 9, 0)
+    assert np.all(np.diff(g.row_ptr) == k)
+    assert _edges(g) == {(min(i, (i + d) % n), max(i, (i + d) % n)) for i in range(n) for d in range(1, 5)}
+
+
+def _ba_target_plain(n, m, seed, r, t):
+    while True:
+        T = t // m
+        if T == 0:
+            return t
+        z = _sm64(seed, (r << 32) + t)
+        pos = ((z & 0xFFFFFFFF) * (2 * m * T)) >> 32
+        if pos % 2 == 0:
+            return m + (pos // 2) // m
+        t = pos // 2
+
+
+def test_ba_statement_equals_plain_loop():
+    for n, m in [(60, 1), (80, 3), (50, 5)]:
+        seed, r = 77, 2
+        want = set()
+        for t in range(m * (n - m)):
+            u, v = m + t // m, _ba_target_plain(n, m, seed, r, t)
+            want.add((min(u, v), max(u, v)))
+        assert _edges(synth.ba_generated(n, m, seed, r)) == want, (n, m)
+
+
+def test_ba_structure():
+    # m = 1: each new node links to one earlier node, a tree on n nodes
+    g = synth.ba_generated(500, 1, 5, 0)
+    assert len(_edges(g)) == 499
+    seen, stack = {0}, [0]
+    while stack:
+        i = stack.pop()
+        for j in g.col[g.row_ptr[i]:g.row_ptr[i + 1]]:
+            if int(j) not in seen:
+                seen.add(int(j))
+                stack.append(int(j))
+    assert len(seen) == 500
+    # the first new node links to every seed; degrees are heavy-tailed
+    m = 3
+    g = synth.ba_generated(20_000, m, 6, 0)
+    assert set(int(x) for x in g.col[g.row_ptr[m]:g.row_ptr[m + 1]]) >= set(range(m))
+    deg = np.diff(g.row_ptr.astype(np.int64))
+    assert deg.max() > 20 * deg.mean() and deg.min() >= 1
