@@ -25,6 +25,16 @@ namespace cb {
 
 static thread_local std::string g_err;
 
+// Pinned staging of an upload's small host tables (stage_h2d).  Chunks are
+// kept for the next upload; an upload holds the lock from start to end, and
+// the buffer is recycled once its copies are done.
+struct PinnedArena {
+  std::vector<std::pair<char *, size_t>> chunks;
+  size_t ci = 0, off = 0;
+};
+static std::recursive_mutex g_stage_mu;
+static PinnedArena g_stage;
+
 int set_error(int code, const std::string &msg) {
   g_err = msg;
   return code;
@@ -392,6 +402,12 @@ CB_API int cb_debug_stall_tile(cb_graph *h, uint32_t btile) {
 }
 
 CB_API int cb_release_cached_memory(void) {
+  {
+    std::lock_guard<std::recursive_mutex> lk(g_stage_mu);
+    for (auto &c : g_stage.chunks) cudaFreeHost(c.first);
+    g_stage.chunks.clear();
+    g_stage.ci = g_stage.off = 0;
+  }
   cudaError_t e = cudaDeviceSynchronize();
   std::lock_guard<std::mutex> lk(g_pool_mu);
   for (cudaMemPool_t p : g_pools)
@@ -438,6 +454,17 @@ CB_API uint32_t cb_graph_max_nodes(const cb_graph *h) { return h ? h->n_max : 0;
 // for the copies and releases both.
 namespace {
 constexpr uint64_t kCopyGroups = 8;
+struct StageScope {
+  std::unique_lock<std::recursive_mutex> lk{g_stage_mu};
+  cudaStream_t s;
+  explicit StageScope(cudaStream_t st) : s(st) {}
+  ~StageScope() {
+    cudaStreamSynchronize(s);  // every staged copy has been read
+    g_stage.ci = 0;
+    g_stage.off = 0;
+  }
+};
+
 struct UploadCopies {
   cudaStream_t stream = nullptr;
   std::vector<CopyGroup> groups;
@@ -474,6 +501,28 @@ struct UploadCopies {
 };
 }  // namespace
 
+cudaError_t cb::stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return cudaSuccess;
+  std::lock_guard<std::recursive_mutex> lk(g_stage_mu);
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  while (g_stage.ci < g_stage.chunks.size() && g_stage.off + need > g_stage.chunks[g_stage.ci].second) {
+    ++g_stage.ci;
+    g_stage.off = 0;
+  }
+  if (g_stage.ci == g_stage.chunks.size()) {
+    const size_t sz = std::max<size_t>(need, (size_t)16 << 20);
+    char *p = nullptr;
+    const cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&p), sz);
+    if (e != cudaSuccess) return e;
+    g_stage.chunks.push_back({p, sz});
+    g_stage.off = 0;
+  }
+  char *p = g_stage.chunks[g_stage.ci].first + g_stage.off;
+  g_stage.off += need;
+  std::memcpy(p, src, bytes);
+  return cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, s);
+}
+
 CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
                            const uint32_t *const *row_ptr, const uint32_t *const *col,
                            uint32_t flags, void *stream, cb_graph **out) {
@@ -486,6 +535,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   if (dev && (flags & CB_VALIDATE))
     return set_error(CB_ERR_ARG, "cb_graph_upload: CB_VALIDATE needs host arrays");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  StageScope stage(s);
 
   cb_graph *h = new cb_graph();
   cudaGetDevice(&h->device);
@@ -676,16 +726,12 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     delete h;
     return cuda_error(e, "cb_graph_upload: allocate");
   }
-  chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), n_inst * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(h->d_tile_inst, tile_inst.data(), tile_inst.size() * 4, cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(h->d_tile_rows, tile_rows.data(), tile_rows.size() * sizeof(uint2),
-                      cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(h->d_fin_inst, fin_inst.data(), fin_inst.size() * 4, cudaMemcpyHostToDevice, s));
-  if (!h->heavy.empty())
-    chk(cudaMemcpyAsync(h->d_heavy, h->heavy.data(), h->heavy.size() * sizeof(HeavyRow),
-                        cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(h->d_chunk_heavy, chunk_heavy.data(), chunk_heavy.size() * 4,
-                      cudaMemcpyHostToDevice, s));
+  chk(stage_h2d(h->d_inst, h->inst.data(), n_inst * sizeof(InstDesc), s));
+  chk(stage_h2d(h->d_tile_inst, tile_inst.data(), tile_inst.size() * 4, s));
+  chk(stage_h2d(h->d_tile_rows, tile_rows.data(), tile_rows.size() * sizeof(uint2), s));
+  chk(stage_h2d(h->d_fin_inst, fin_inst.data(), fin_inst.size() * 4, s));
+  if (!h->heavy.empty()) chk(stage_h2d(h->d_heavy, h->heavy.data(), h->heavy.size() * sizeof(HeavyRow), s));
+  chk(stage_h2d(h->d_chunk_heavy, chunk_heavy.data(), chunk_heavy.size() * 4, s));
   if (e != cudaSuccess) {
     cp.finish();
     free_graph_arrays(h);

@@ -262,14 +262,11 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       free_blocked(h);
       return cuda_error(e, "blocked format: allocate");
     }
-    chk(cudaMemcpyAsync(h->d_btile_inst, btile_inst.data(), nbt * 4, cudaMemcpyHostToDevice, s));
-    chk(cudaMemcpyAsync(h->d_bseg_base, bseg_base.data(), nbt * 8, cudaMemcpyHostToDevice, s));
-    chk(cudaMemcpyAsync(h->d_blong_ptr, long_ptr.data(), long_ptr.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!long_rows.empty())
-      chk(cudaMemcpyAsync(h->d_blong_rows, long_rows.data(), long_rows.size() * 4,
-                          cudaMemcpyHostToDevice, s));
-    chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
-                        cudaMemcpyHostToDevice, s));
+    chk(stage_h2d(h->d_btile_inst, btile_inst.data(), nbt * 4, s));
+    chk(stage_h2d(h->d_bseg_base, bseg_base.data(), nbt * 8, s));
+    chk(stage_h2d(h->d_blong_ptr, long_ptr.data(), long_ptr.size() * 4, s));
+    if (!long_rows.empty()) chk(stage_h2d(h->d_blong_rows, long_rows.data(), long_rows.size() * 4, s));
+    chk(stage_h2d(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc), s));
     // no temporary allocation here: a free synchronises the device, which
     // would stall an upload behind another thread's kernels
     uint32_t *d_unsorted = h->d_bwlen + nw;
@@ -319,8 +316,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       chk(cudaStreamSynchronize(s));
     }
   } else {
-    chk(cudaMemcpyAsync(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc),
-                        cudaMemcpyHostToDevice, s));
+    chk(stage_h2d(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc), s));
     chk(cudaStreamSynchronize(s));
   }
   if (e != cudaSuccess) {

@@ -188,6 +188,13 @@ namespace cb {
 // fn(i) for i in [0, n) on the host, spread over the hardware threads
 void parallel_for(uint32_t n, const std::function<void(uint32_t)> &fn);
 
+// Host-to-device copy of a small host table during an upload, staged through
+// a library-owned pinned buffer so that it is truly asynchronous: a copy from
+// pageable memory would wait for the copy engine, which the upload's bulk
+// copies keep busy for the whole transfer, and hold the host thread with it.
+// The staging buffer is recycled when the upload returns (cb_api.cu).
+cudaError_t stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
 // error plumbing (cb_api.cu)
 // Device memory of handles and workspaces.  By default it comes from a
 // library-owned stream-ordered pool per device that keeps freed memory for
