@@ -34,6 +34,35 @@ namespace cb {
 namespace {
 
 constexpr uint32_t kFillThreads = 128;  // lanes of a tile per count / fill CTA
+constexpr uint32_t kFillBatch = 4;      // column loads a lane keeps in flight
+
+// Entry ranges of a lane's kBRowsPerThread rows (first row `row`, stride
+// kBThreads), all loaded before the walk; rows past n and rows longer than
+// kBLongDeg (summed by the SpMV from the CSR) get an empty range.
+__device__ __forceinline__ void row_ranges(const uint32_t *rp, uint32_t row, uint32_t n,
+                                           uint32_t (&e0)[kBRowsPerThread],
+                                           uint32_t (&e1)[kBRowsPerThread]) {
+#pragma unroll
+  for (int k = 0; k < kBRowsPerThread; ++k) {
+    const uint32_t r = row + kBThreads * k;
+    e0[k] = e1[k] = 0;
+    if (r < n) {
+      e0[k] = rp[r];
+      e1[k] = rp[r + 1];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kBRowsPerThread; ++k)
+    if (e1[k] - e0[k] > kBLongDeg) e1[k] = e0[k];
+}
+
+// Columns e .. e + kFillBatch - 1 of a row ending at e1, issued together
+// (entries past e1 are not read).
+__device__ __forceinline__ void load_batch(const uint32_t *cl, uint32_t e, uint32_t e1,
+                                           uint32_t (&cv)[kFillBatch]) {
+#pragma unroll
+  for (uint32_t u = 0; u < kFillBatch; ++u) cv[u] = e + u < e1 ? __ldg(cl + e + u) : 0u;
+}
 
 // Per (segment, warp) stream length: the largest per-lane element count of the
 // warp in that column block, rounded up to a multiple of 4.  CTAs of
@@ -55,18 +84,24 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
   const uint32_t nb = I.nb;
   for (uint32_t b = 0; b < nb; ++b) s_cnt[b][tid] = 0;
   bool bad = false;
+  uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
+  row_ranges(rp, row0 + v, I.n, re0, re1);
+#pragma unroll
   for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t row = row0 + v + kBThreads * k;
-    if (row >= I.n) break;
-    const uint32_t e0 = rp[row], e1 = rp[row + 1];
-    if (e1 - e0 > kBLongDeg) continue;
+    const uint32_t e0 = re0[k], e1 = re1[k];
     uint32_t prev = 0;
-    for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t c = __ldg(cl + e);
-      const uint32_t b = c >> kBColBits;
-      if (b < nb) s_cnt[b][tid]++;  // columns >= n are invalid input: skipped
-      bad |= e > e0 && c < prev;    // the format needs sorted rows
-      prev = c;
+    for (uint32_t e = e0; e < e1; e += kFillBatch) {
+      uint32_t cv[kFillBatch];
+      load_batch(cl, e, e1, cv);
+#pragma unroll
+      for (uint32_t u = 0; u < kFillBatch; ++u) {
+        if (e + u >= e1) break;
+        const uint32_t c = cv[u];
+        const uint32_t b = c >> kBColBits;
+        if (b < nb) s_cnt[b][tid]++;    // columns >= n are invalid input: skipped
+        bad |= e + u > e0 && c < prev;  // the format needs sorted rows
+        prev = c;
+      }
     }
   }
   if (bad) *unsorted = 1u;
@@ -127,21 +162,27 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
     reinterpret_cast<uint2 *>(bcol + st)[32 * stripe + lane] = cv;
     reinterpret_cast<uint32_t *>(bslot + st)[32 * stripe + lane] = sv;
   };
+  uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
+  row_ranges(rp, row0 + v, I.n, re0, re1);
+#pragma unroll
   for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t row = row0 + v + kBThreads * k;
-    if (row >= I.n) break;
-    const uint32_t e0 = rp[row], e1 = rp[row + 1];
-    if (e1 - e0 > kBLongDeg) continue;
-    for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t c = __ldg(cl + e);
-      const uint32_t b = c >> kBColBits;
-      if (b >= nb) continue;  // columns >= n are invalid input: skipped
-      const uint32_t q = s_q[b * kFillThreads + tid];
-      const uint32_t p = q & 3;
-      COL(b, p) = (uint16_t)(c & (kBCol - 1));
-      SLOT(b, p) = (uint8_t)k;
-      s_q[b * kFillThreads + tid] = (uint16_t)(q + 1);
-      if (p == 3) flush(b, q >> 2);
+    const uint32_t e1 = re1[k];
+    for (uint32_t e = re0[k]; e < e1; e += kFillBatch) {
+      uint32_t cv[kFillBatch];
+      load_batch(cl, e, e1, cv);
+#pragma unroll
+      for (uint32_t u = 0; u < kFillBatch; ++u) {
+        if (e + u >= e1) break;
+        const uint32_t c = cv[u];
+        const uint32_t b = c >> kBColBits;
+        if (b >= nb) continue;  // columns >= n are invalid input: skipped
+        const uint32_t q = s_q[b * kFillThreads + tid];
+        const uint32_t p = q & 3;
+        COL(b, p) = (uint16_t)(c & (kBCol - 1));
+        SLOT(b, p) = (uint8_t)k;
+        s_q[b * kFillThreads + tid] = (uint16_t)(q + 1);
+        if (p == 3) flush(b, q >> 2);
+      }
     }
   }
   for (uint32_t b = 0; b < nb; ++b) {

@@ -258,8 +258,16 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
     const bool is_short = valid && (e1 - e0) <= kShort;
     T s = T(0);
     if (is_short) {
-#pragma unroll 4
-      for (uint32_t e = e0 + lane_g; e < e1; e += G) s += ld_vec(x + ld_stream(col + e));
+      // at most kShort / G entries per lane: a fixed, predicated trip count
+      // puts all of the lane's index loads, then all of its gathers, in
+      // flight at once (a counted loop of 2-4 trips runs its remainder
+      // path one load pair at a time); the summation order is unchanged
+      const uint32_t len = e1 - e0;
+#pragma unroll
+      for (uint32_t i = 0; i < kShort / G; ++i) {
+        const uint32_t t = lane_g + i * G;
+        if (t < len) s += ld_vec(x + ld_stream(col + e0 + t));
+      }
     }
     s = group_sum<G, T>(s);
     if (is_short && lane_g == 0) acc += row_epilogue<T>(s, row0 + lr, x, xp, out, sj, bp, has_prev);
