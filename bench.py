@@ -413,7 +413,7 @@ def main():
     spmv_avg = spmv_ms / max(spmv_n, 1)
     peak, peak_kind = measured_peak()
     achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
-    blocked_path = max(g.n for g in ens.graphs) <= 32 * 16384 and not os.environ.get("CB_NO_BLOCKED")
+    blocked_path = max(g.n for g in ens.graphs) <= 32 * 16384
     kname = ("bspmv_kernel (column-blocked Lanczos SpMV step)" if blocked_path
              else "spmv_kernel (tiled-CSR Lanczos SpMV step)")
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,

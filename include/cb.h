@@ -65,6 +65,7 @@ extern "C" {
 /* cb_graph_upload flags */
 #define CB_VALIDATE 1u    /* check CSR invariants on the host before upload */
 #define CB_DEVICE_PTRS 2u /* row_ptr[r] / col[r] are device pointers */
+#define CB_CSR_ONLY 4u    /* no column-blocked format: every FP32 SpMV gathers from the CSR */
 
 /* largest Krylov depth accepted by the compute calls */
 #define CB_MAX_M 128
@@ -101,6 +102,12 @@ typedef struct {
  *              self-loops and the pattern is symmetric (host arrays only;
  *              O(nnz * degree) host time).  Without it, unsorted rows are
  *              still detected on the device (CB_ERR_ARG).
+ *              CB_DEVICE_PTRS: row_ptr[r] and col[r] are device pointers.
+ *              CB_CSR_ONLY: skip the column-blocked format that FP32 calls
+ *              use for realisations with n <= 32 * 16384; they then run the
+ *              tiled-CSR SpMV (same recurrence, FP32 rounding differs), the
+ *              upload is shorter and the handle ~3 B per entry smaller.
+ *              Other bits: CB_ERR_ARG.
  *   stream     used for the copies.  The call synchronises `stream` before
  *              returning, so the input arrays may be freed afterwards.
  *   out        receives the handle.

@@ -403,8 +403,7 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
   // the basis from 1 is the forward pass's when an ensemble pass at this m
   // and precision ran last on the handle (same stream order assumed)
   const bool reuse = rc == CB_OK && h->basis_m == m && h->basis_prec == prec &&
-                     h->basis_reorth == reorth && h->basis_gen == h->ws.gen &&
-                     !std::getenv("CB_NO_REUSE");
+                     h->basis_reorth == reorth && h->basis_gen == h->ws.gen;
   if (rc == CB_OK && !reuse) {
     h->basis_m = 0;
     rc = lanczos_run(h, h->ws, 0, h->n_inst, m, prec, s);

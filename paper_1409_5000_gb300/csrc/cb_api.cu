@@ -116,10 +116,6 @@ void prefer_shared_impl(const void *kernel) {
 }
 
 static int pick_lanes(double avg_deg) {
-  if (const char *env = std::getenv("CB_LANES")) {
-    int v = std::atoi(env);
-    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) return v;
-  }
   if (avg_deg < 3) return 1;
   if (avg_deg < 6) return 2;
   if (avg_deg < 24) return 4;
@@ -531,6 +527,8 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   *out = nullptr;
   if (n_inst == 0 || !n || !nnz || !row_ptr || !col)
     return set_error(CB_ERR_ARG, "cb_graph_upload: empty input or null array");
+  if (flags & ~(CB_VALIDATE | CB_DEVICE_PTRS | CB_CSR_ONLY))
+    return set_error(CB_ERR_ARG, "cb_graph_upload: unknown flag");
   const bool dev = (flags & CB_DEVICE_PTRS) != 0;
   if (dev && (flags & CB_VALIDATE))
     return set_error(CB_ERR_ARG, "cb_graph_upload: CB_VALIDATE needs host arrays");
@@ -539,6 +537,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
 
   cb_graph *h = new cb_graph();
   cudaGetDevice(&h->device);
+  h->csr_only = (flags & CB_CSR_ONLY) != 0;
   h->n_inst = n_inst;
   h->inst.resize(n_inst);
 

@@ -239,7 +239,7 @@ void free_blocked(cb_graph *h) {
 int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
                   const std::vector<CopyGroup> &groups) {
   NvtxRange nvtx_range("column-blocked format");
-  if (std::getenv("CB_NO_BLOCKED")) return CB_OK;
+  if (h->csr_only) return CB_OK;
   // which realisations, their tiles, segments and reduction plans
   uint32_t nbt = 0, slot = 0, group = 0;
   uint64_t nseg = 0;

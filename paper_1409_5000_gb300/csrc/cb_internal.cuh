@@ -123,6 +123,7 @@ struct BackWork {
 
 struct cb_graph {
   int device = 0;
+  bool csr_only = false;  // CB_CSR_ONLY: no column-blocked format
   uint32_t n_inst = 0;
   uint32_t n_max = 0;
   uint64_t total_nodes_padded = 0;  // sum of padded node ranges

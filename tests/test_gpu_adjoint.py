@@ -151,17 +151,16 @@ def test_autograd_function(B):
         assert abs(loss.item() - S[torch.as_tensor(nodes, device="cuda")].sum().item()) <= 1e-12 * abs(loss.item())
 
 
-def test_forward_basis_reuse(B, monkeypatch):
+def test_forward_basis_reuse(B):
     """After an ensemble pass at the same m and precision the adjoint reuses
-    its basis from 1; the gradient must be bit-identical to a recomputation,
-    also when a per-realisation call or another depth came in between."""
+    its basis from 1; the gradient must be bit-identical to a recomputation
+    (the first backward on a fresh handle computes the basis itself), also
+    when a per-realisation call or another depth came in between."""
     ens = synth.er_ensemble_small()
     nodes = [int(x) for x in ens.target]
     with B.GraphSet(ens.graphs) as gs:
-        monkeypatch.setenv("CB_NO_REUSE", "1")
         ls0, g0 = B.scores_backward(gs, 20, nodes)
         g0 = g0.cpu().numpy()
-        monkeypatch.delenv("CB_NO_REUSE")
         for between in (None, "single", "depth"):
             B.ensemble_scores(gs, 20, 0)
             if between == "single":

@@ -30,8 +30,8 @@ def B():
     return binding
 
 
-def _single(B, g, m, prec):
-    with B.GraphSet([g]) as gs:
+def _single(B, g, m, prec, csr_only=False):
+    with B.GraphSet([g], csr_only=csr_only) as gs:
         ls, y, rep = B.communicability(gs, 0, m, PREC[prec], report=True)
         torch.cuda.synchronize()
         return float(ls.item()), y.cpu().numpy(), rep
@@ -270,7 +270,7 @@ def test_argument_errors(B):
         B.GraphSet([bad], validate=True)
 
 
-def test_column_blocked_matches_tiled_csr(B, monkeypatch):
+def test_column_blocked_matches_tiled_csr(B):
     """The FP32 column-blocked SpMV (shared-memory gathers) and the tiled-CSR
     SpMV compute the same recurrence: results agree to FP32 rounding, and
     both agree with the oracle.  n = 70 000 spans 5 column blocks and a
@@ -283,11 +283,7 @@ def test_column_blocked_matches_tiled_csr(B, monkeypatch):
     g = synth.from_edges(n, base + hub)
     res = {}
     for mode in ("blocked", "csr"):
-        if mode == "csr":
-            monkeypatch.setenv("CB_NO_BLOCKED", "1")
-        else:
-            monkeypatch.delenv("CB_NO_BLOCKED", raising=False)
-        res[mode] = _single(B, g, 30, "fp32")
+        res[mode] = _single(B, g, 30, "fp32", csr_only=mode == "csr")
     (tb, yb, _), (tc, yc, _) = res["blocked"], res["csr"]
     e = parity.errors(tb, yb, tc, yc)  # head + normwise: the tail is FP32 noise in both
     assert e["head_rel"] < 1e-5 and e["norm_rel"] < 1e-5, e
