@@ -120,9 +120,24 @@ __global__ void __launch_bounds__(256) combine_sum_kernel(const T *Y, Scalars sc
   const double qnan = __longlong_as_double(0x7ff8000000000000ll);
   if (i == 0) *log_scale = any_bad ? qnan : tmax;
   if (i >= n_out) return;
+  // 8 realisations' loads in flight, then their terms in realisation order;
+  // realisations with n_r <= i are skipped (warp-uniform except at n_r), so
+  // the scarce FP64 pipe only sees real terms
+  constexpr uint32_t kB = 8;
   double sum = 0.0;
-  for (uint32_t r = 0; r < n_inst; ++r)
-    if (i < s_n[r]) sum += s_wt[r] * (double)Y[s_base[r] + i];
+  for (uint32_t r0 = 0; r0 < n_inst; r0 += kB) {
+    T y[kB];
+    bool in[kB];
+#pragma unroll
+    for (uint32_t u = 0; u < kB; ++u) {
+      const uint32_t r = r0 + u;
+      in[u] = r < n_inst && i < s_n[r];
+      y[u] = in[u] ? Y[s_base[r] + i] : T(0);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kB; ++u)
+      if (in[u]) sum += s_wt[r0 + u] * (double)y[u];
+  }
   S[i] = any_bad ? qnan : sum;
 }
 
