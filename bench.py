@@ -325,6 +325,9 @@ def main():
     ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "small", "grad"])
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the e2e, plain-FP64 and CPU-baseline legs")
+    ap.add_argument("--csr-only", action="store_true",
+                    help="upload without the column-blocked format (CB_CSR_ONLY): every FP32 "
+                         "SpMV runs the tiled-CSR kernel")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -355,7 +358,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     units = sum(g.nnz for g in ens.graphs) * m  # edge-Lanczos-steps per step
-    gs = B.GraphSet(ens.graphs)
+    gs = B.GraphSet(ens.graphs, csr_only=args.csr_only)
     S = torch.empty(gs.n_max, dtype=torch.float64, device=dev)
     ls = torch.empty(1, dtype=torch.float64, device=dev)
     idx = torch.empty(k, dtype=torch.int32, device=dev)
@@ -413,7 +416,7 @@ def main():
     spmv_avg = spmv_ms / max(spmv_n, 1)
     peak, peak_kind = measured_peak()
     achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
-    blocked_path = max(g.n for g in ens.graphs) <= 32 * 16384
+    blocked_path = max(g.n for g in ens.graphs) <= 32 * 16384 and not args.csr_only
     kname = ("bspmv_kernel (column-blocked Lanczos SpMV step)" if blocked_path
              else "spmv_kernel (tiled-CSR Lanczos SpMV step)")
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
