@@ -425,12 +425,12 @@ def main():
                 "traffic": traffic_per_launch(ens, blocked_path),
                 "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
                 "kernel_shares": {kname: round(t / tot, 4) for kname, (t, _) in fam.items()}}
-    # init (2) + SpMV and finalize per Lanczos step + tridiag + combine (2) + top-k
-    # (init, 12 radix passes, collect, sort)
-    launches_per_step = 2 + 2 * m + 1 + 2 + 15
+    # init (2) + SpMV, finalize and beta per Lanczos step + tridiag + combine (2)
+    # + top-k (init, 12 radix passes, collect, sort)
+    launches_per_step = 2 + 3 * m + 1 + 2 + 15
     if with_grad:  # the Lanczos run from the indicator (the basis from 1 is the
         # forward pass's) + 3 adjoint kernels
-        launches_per_step += (3 + 2 * m) + 3
+        launches_per_step += (3 + 3 * m) + 3
 
     extra = {}
     if with_grad:

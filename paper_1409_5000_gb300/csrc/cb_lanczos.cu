@@ -662,21 +662,50 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(LArgs a, uint32_t j,
       acc += w * w;
     }
   }
+  // the tile's partial of ||w||^2 goes to its slot; beta_j follows in
+  // finalize_beta_kernel, so no CTA waits on an arrival counter
   const double part = block_sum_to_double<T>(acc, s_red);
-  double total;
-  if (arrive_and_reduce(I.fin, t - I.fin_base, r, part, a.red, &total)) {
-    const double beta = sqrt(total);
-    const double alpha = a.sc.alpha[r * ms + j];
-    const double bprev = j > 0 ? a.sc.beta[r * ms + j - 1] : 0.0;
-    a.sc.beta[r * ms + j] = beta;
-    if (!isfinite(beta)) {
-      a.sc.status[r] = CB_ERR_NONFINITE;
-      a.sc.meff[r] = j + 1;
-    } else if (beta <= a.tau * (fabs(alpha) + bprev) || beta == 0.0) {
-      a.sc.meff[r] = j + 1;  // exact breakdown: K_{j+1}(A,1) is invariant
-    } else {
-      a.sc.scale[r * ms + j + 1] = 1.0 / beta;
-    }
+  if (threadIdx.x == 0) a.red.part[I.fin.slot_base + (t - I.fin_base)] = part;
+}
+
+// beta_j = ||w|| per realisation from the finalize partials, one CTA of
+// kThreads per realisation: group sums over kGroup slots by one warp each,
+// then the sum over groups, in the same order and shapes as the
+// last-arriving reduction of arrive_and_reduce (so beta is bit-identical to
+// it); then the breakdown test and scale_{j+1} = 1 / beta.
+__global__ void __launch_bounds__(kThreads) finalize_beta_kernel(LArgs a, uint32_t j, uint32_t r0) {
+  __shared__ double s_red[kThreads / 32];
+  const uint32_t r = r0 + blockIdx.x;
+  if (j >= a.sc.meff[r]) return;
+  const RedPlan P = a.inst[r].fin;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t g = warp; g < P.n_groups; g += kThreads / 32) {
+    const uint32_t gsize = min((uint32_t)kGroup, P.n_slots - g * kGroup);
+    double v = lane < gsize ? a.red.part[P.slot_base + g * kGroup + lane] : 0.0;
+    v = warp_sum_d(v);
+    if (lane == 0) a.red.gpart[P.group_base + g] = v;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (uint32_t q = threadIdx.x; q < P.n_groups; q += kThreads) acc += a.red.gpart[P.group_base + q];
+  acc = warp_sum_d(acc);
+  if (lane == 0) s_red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double total = 0.0;
+  for (int w = 0; w < kThreads / 32; ++w) total += s_red[w];
+  const uint32_t ms = a.sc.ms;
+  const double beta = sqrt(total);
+  const double alpha = a.sc.alpha[r * ms + j];
+  const double bprev = j > 0 ? a.sc.beta[r * ms + j - 1] : 0.0;
+  a.sc.beta[r * ms + j] = beta;
+  if (!isfinite(beta)) {
+    a.sc.status[r] = CB_ERR_NONFINITE;
+    a.sc.meff[r] = j + 1;
+  } else if (beta <= a.tau * (fabs(alpha) + bprev) || beta == 0.0) {
+    a.sc.meff[r] = j + 1;  // exact breakdown: K_{j+1}(A,1) is invariant
+  } else {
+    a.sc.scale[r * ms + j + 1] = 1.0 / beta;
   }
 }
 
@@ -917,7 +946,10 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
     if (n_btiles) bspmv_kernel<<<n_btiles, kBThreads, kBSmemBytes, s>>>(a, j, btile_off);
     prof_end(tok, s);
     tok = prof_begin(CB_K_FINALIZE, s);
-    if (n_fin) finalize_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off);
+    if (n_fin) {
+      finalize_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off);
+      finalize_beta_kernel<<<r1 - r0, kThreads, 0, s>>>(a, j, r0);
+    }
     if (n_fin && h->reorth)
       for (int pass = 0; pass < 2; ++pass) {
         reorth_dot_kernel<T><<<n_fin, kThreads, 0, s>>>(a, j, fin_off, W.rpart);
