@@ -66,3 +66,17 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_guard_hashes_the_kernel_sources():
+    """roofline.traffic is reported only while the SpMV kernel, its epilogue,
+    the format builder and the blocked constants hash to the captured version;
+    the anchors that cut those regions out of the sources must still exist."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    h = bench._kernel_sources_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    assert bench._TRAFFIC["bytes_per_edge"] > 3.0  # at least the 3 B of an element
