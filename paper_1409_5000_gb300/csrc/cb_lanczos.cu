@@ -12,12 +12,16 @@
 // realisations' node ranges are concatenated with kNodeAlign padding.
 // W_0 = 1, scale_0 = 1/sqrt(n).
 //
-// Step j (0-based), two kernels:
+// Step j (0-based), three kernels:
 //   spmv:     u = scale_j (A W_j) - beta_{j-1} scale_{j-1} W_{j-1}
 //             alpha_j = scale_j (W_j . u);   W_{j+1} <- u
-//   finalize: w = W_{j+1} - alpha_j scale_j W_j;  W_{j+1} <- w
-//             beta_j = ||w||; scale_{j+1} = 1/beta_j, or stop at an exact
+//   finalize: w = W_{j+1} - alpha_j scale_j W_j;  W_{j+1} <- w, and the
+//             per-tile partials of ||w||^2
+//   beta:     beta_j = ||w||; scale_{j+1} = 1/beta_j, or stop at an exact
 //             breakdown beta_j <= tau (|alpha_j| + beta_{j-1}).
+// Deterministic reductions: the SpMV's alpha uses the last CTA to arrive
+// (cb_reduce.cuh); beta sums the finalize partials in the same groups and
+// order in its own kernel, so finalize CTAs retire without waiting.
 // No reorthogonalisation: the Lanczos approximation of f(A)b stays accurate
 // in finite precision after orthogonality is lost (Greenbaum; Musco, Musco &
 // Sidford 2018), which the parity tests check against the FP64 oracle that
