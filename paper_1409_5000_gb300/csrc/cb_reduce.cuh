@@ -5,7 +5,10 @@
 // CTA that completes a group sums that group's slots in a fixed order, and
 // the CTA that completes the last group of a realisation sums the group
 // partials in a fixed order.  Nothing ever waits on another CTA, so there is
-// no spin loop, and the summation order does not depend on scheduling.
+// no spin loop, and the summation order does not depend on scheduling.  The
+// finalize step's norm uses the same slots and groups but no counters: its
+// CTAs only write their partials, and a following kernel (one CTA per
+// realisation) forms the group and realisation sums in the same order.
 #pragma once
 
 #include "cb_internal.cuh"
