@@ -7,7 +7,11 @@ mistake) and raises AssertionError when it disagrees with:
 * the scalar identity sum_ij A_ij G_ij = w^T A e^A 1 (the derivative along
   t -> e^{tA} at t = 1);
 * central finite differences of w^T e^A 1 in the edge weights (FP64);
-* exactness of the Krylov form once m spans the Krylov spaces.
+* exactness of the Krylov form once m spans the Krylov spaces;
+* for the ensemble gradient (eq. 5 restricted to the node set): the dense
+  gradient of every realisation, concatenated, and central differences of
+  the summed loss sum_r w_r^T e^{A_r} 1, on realisations of uneven n and
+  clearly different largest eigenvalues.
 """
 from __future__ import annotations
 
@@ -110,5 +114,68 @@ def check_krylov_fd(adj):
         assert abs(math.exp(th) * fd - ref) < 1e-6 * abs(ref), (e, math.exp(th) * fd, ref)
 
 
+def _ensemble3():
+    """Three realisations of uneven n and spread shifts: a sparse ER(30)
+    (lambda_max ~ 3), a denser ER(45) (~ 11) and a star K_{1,20} beside
+    isolated nodes (sqrt(20) ~ 4.5).  The node set reaches past n for the
+    smaller ones, so each realisation keeps only its own nodes."""
+    g0 = synth.er(30, 0.1, 11)
+    g1 = synth.er(45, 0.25, 12)
+    g2 = synth.from_edges(40, [(5, q) for q in range(20, 40)])
+    nodes = [2, 5, 21, 29, 33, 44]
+    return [(g.n, g.row_ptr, g.col) for g in (g0, g1, g2)], nodes
+
+
+def check_ensemble_grad_dense(adj):
+    """exp(theta*) g equals the dense FP64 gradient of each realisation,
+    concatenated in realisation order, with w_r = 1 on the nodes < n_r
+    (m spans every Krylov space, so the Krylov form is exact)."""
+    graphs, nodes = _ensemble3()
+    theta_s, g = adj.ensemble_edge_grad(graphs, nodes, 50)
+    ref = []
+    for (n, rp, col) in graphs:
+        w = np.zeros(n)
+        w[[x for x in nodes if x < n]] = 1.0
+        ref.append(adj.dense_edge_grad(n, rp, col, w, how="eig"))
+    ref = np.concatenate(ref)
+    assert g.shape == ref.shape, (g.shape, ref.shape)
+    got = math.exp(theta_s) * g
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+    # entry by entry where the value is not tiny against the largest
+    big = np.abs(ref) > 1e-6 * np.max(np.abs(ref))
+    assert rel(got[big], ref[big]) < 1e-8
+    # theta* is the largest shift: some realisation carries weight exp(0) = 1
+    lam = [np.linalg.eigvalsh(oc.dense_adjacency(*gr)).max() for gr in graphs]
+    assert theta_s >= max(lam) - 1e-8
+
+
+def check_ensemble_grad_fd(adj):
+    """Central differences of L = sum_r w_r^T e^{A_r} 1 (dense expm, FP64)
+    on one edge of every realisation equal the ensemble gradient."""
+    graphs, nodes = _ensemble3()
+    theta_s, g = adj.ensemble_edge_grad(graphs, nodes, 50)
+    h = 1e-5
+    off = 0
+    for (n, rp, col) in graphs:
+        w = np.zeros(n)
+        w[[x for x in nodes if x < n]] = 1.0
+        A0 = oc.dense_adjacency(n, rp, col)
+        i, j = adj.edge_list(n, rp, col)
+        e = len(i) // 2
+        vals = []
+        for sgn in (1, -1):
+            A = A0.copy()
+            A[i[e], j[e]] += sgn * h
+            A[j[e], i[e]] += sgn * h
+            # the other realisations' terms do not move
+            vals.append(w @ oc.expm_taylor(A) @ np.ones(n))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        got = math.exp(theta_s) * g[off + e]
+        assert abs(fd - got) < 1e-6 * abs(fd), (off, e, fd, got)
+        off += len(i)
+    assert off == len(g)
+
+
 ADJ_CHECKS = [check_kn_closed_form, check_two_dense_ways, check_scalar_identity,
-              check_finite_differences, check_krylov_exact, check_krylov_fd]
+              check_finite_differences, check_krylov_exact, check_krylov_fd,
+              check_ensemble_grad_dense, check_ensemble_grad_fd]

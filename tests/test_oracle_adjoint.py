@@ -31,6 +31,20 @@ MUTATIONS = [
     ("return Q @ (divided_exp(lam) * C) @ Q.T", "return Q @ (np.exp(lam)[:, None] * C) @ Q.T"),
     # edge gradient misses G_ji
     ("return G[i, j] + G[j, i]", "return 2 * G[i, j]"),
+    # ensemble: the shift applied the wrong way round
+    ("math.exp(t - theta_star) * g for t, g in parts",
+     "math.exp(theta_star - t) * g for t, g in parts"),
+    # ensemble: the last realisation dropped
+    ("np.concatenate([math.exp(t - theta_star) * g for t, g in parts])",
+     "np.concatenate([math.exp(t - theta_star) * g for t, g in parts[:-1]])"),
+    # ensemble: nodes past the realisation's range not filtered out
+    ("sel = np.asarray([x for x in nodes if x < n], dtype=np.int64)",
+     "sel = np.asarray([x for x in nodes], dtype=np.int64)"),
+    # ensemble: nodes past the range wrapped into it instead of dropped
+    ("sel = np.asarray([x for x in nodes if x < n], dtype=np.int64)",
+     "sel = np.asarray([x % n for x in nodes], dtype=np.int64)"),
+    # ensemble: the common shift is the smallest instead of the largest
+    ("theta_star = max(p[0] for p in parts)", "theta_star = min(p[0] for p in parts)"),
 ]
 
 
