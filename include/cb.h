@@ -11,8 +11,8 @@
  *     at linear cost).
  *   - Scores are summed over N background realisations that carry the same
  *     embedded target (eq. 5).
- *   - The k largest summed scores are the recovered target ("the largest
- *     20 EBTC values").
+ *   - The k largest summed scores are the recovered target
+ *     ("Identification algorithm", k = the target size).
  *
  * Conventions shared by every call:
  *   - Return value: CB_OK (0) or one of the CB_ERR_* codes below.  On error
@@ -371,8 +371,9 @@ int cb_ensemble_scores_restarted(cb_graph *h, uint32_t m, uint32_t cycles, int p
                                  cb_inst_report *rep, void *stream);
 
 /*
- * cb_topk -- indices and values of the k largest entries of S ("the
- * largest 20 EBTC values"; the paper sorts, this selects by radix).
+ * cb_topk -- indices and values of the k largest entries of S (the
+ * recovered target of the "Identification algorithm" section; the paper
+ * sorts all scores, this selects by radix).
  *   S    device, double[n], read.
  *   n    1 <= n < 2^32.  k: 1 <= k <= min(n, CB_MAX_TOPK).
  *   idx  device, uint32[k], written; val device, double[k], written.
@@ -394,9 +395,12 @@ int cb_topk(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
  *   Arguments, order and tie rule as cb_topk.  k <= CB_MAX_TOPK (4096);
  *   a larger k is rejected with CB_ERR_ARG and a message naming the limit.
  *   Scratch: one fixed array of about 65 KB in device memory per GPU that
- *   loads the library, held until the process exits.  The first call on a
- *   device looks up that array's device address (cudaGetSymbolAddress), so
- *   make the first call on each device before any stream capture.
+ *   loads the library, held until the process exits.  The first call in a
+ *   CUDA context looks up that array's device address in the context
+ *   (cudaGetSymbolAddress) and caches it under the context's unique id, so
+ *   make the first call on each device before any stream capture.  A
+ *   context created later (after cudaDeviceReset, or another context made
+ *   current) gets its own lookup on its first call.
  *   Every call on a device shares the one array: calls whose work overlaps
  *   on the GPU (different streams, no ordering between them) race and may
  *   return wrong results.  Calls ordered on one stream are safe; each call
@@ -467,6 +471,36 @@ int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_i
 int cb_scores_backward_budget(cb_graph *h, uint32_t m, int prec, const uint32_t *topk_idx,
                               uint32_t k, float *grad, double *log_scale, size_t mem_budget,
                               void *stream);
+
+/*
+ * cb_score_sum -- the summed score of a node set, eq. 5 restricted to it:
+ *   *loss = sum_{q < k, nodes[q] < n} S[nodes[q]]   (FP64, in q order).
+ * With S from cb_ensemble_scores this is the loss that cb_scores_backward
+ * differentiates, in units of exp(log_scale) of that call.
+ *   S      device, double[n], read.   nodes: device, uint32[k], read;
+ *          entries >= n are skipped, a repeated index counts once per entry.
+ *   k      1 <= k <= CB_MAX_TOPK.     loss: device, double[1], written.
+ * Asynchronous; deterministic (one warp, fixed summation order).
+ */
+int cb_score_sum(const double *S, uint32_t n, const uint32_t *nodes, uint32_t k, double *loss,
+                 void *stream);
+
+/*
+ * cb_grad_rescale -- brings a gradient from cb_scores_backward to the units
+ * of another log scale and applies an upstream factor (the vector-Jacobian
+ * product of an autograd backward):
+ *   grad[e] *= exp(*log_scale_grad - *log_scale_ref) * (grad_out ? *grad_out : 1)
+ * for e < count.  The factor is formed once in FP64, applied in FP32.
+ *   grad            device, float[count], read and written.
+ *   log_scale_grad  device, double[1]: the log scale cb_scores_backward wrote.
+ *   log_scale_ref   device, double[1]: the target units (for example the
+ *                   log scale of the cb_ensemble_scores call whose summed
+ *                   scores formed the loss).
+ *   grad_out        device, double[1], or NULL for 1.
+ * Asynchronous.  The paper has no gradient; this serves the adjoint.
+ */
+int cb_grad_rescale(float *grad, uint64_t count, const double *log_scale_grad,
+                    const double *log_scale_ref, const double *grad_out, void *stream);
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *cb_last_error(void);

@@ -11,7 +11,7 @@ Contents (each function cites the passage of the paper it follows):
   (eq. 3, eq. 4 written out), the m-step Lanczos (Krylov) approximation of
   e^A 1 with full reorthogonalisation ("Identification algorithm", the
   Krylov evaluation of e^A 1), the ensemble sum (eq. 5) and the top-k
-  selection by a full sort ("the largest 20 EBTC values").
+  selection by a full sort ("Identification algorithm": the k largest EBTC).
 * :mod:`oracle.adjoint` -- the Frechet derivative of the summed top-k
   score with respect to edge weights (dense, two independent ways, and the
   Krylov form used for checking at scale).  The paper has no gradient;

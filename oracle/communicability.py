@@ -280,7 +280,7 @@ def ensemble_scores(graphs, m, n_out=None):
 
 
 def topk(S, k):
-    """The k largest scores ("the largest 20 EBTC values"), by a full sort.
+    """The k largest scores (section "Identification algorithm"), by a full sort.
 
     Order: score descending, ties to the smaller node index.  Returns
     (idx int64[k], val float64[k]).

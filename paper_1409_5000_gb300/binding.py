@@ -105,6 +105,10 @@ def lib():
         L.cb_debug_stall_tile.argtypes = [vp, u32]
         L.cb_topk_noalloc.restype = i32
         L.cb_topk_noalloc.argtypes = [vp, u32, u32, vp, vp, vp]
+        L.cb_score_sum.restype = i32
+        L.cb_score_sum.argtypes = [vp, u32, vp, u32, vp, vp]
+        L.cb_grad_rescale.restype = i32
+        L.cb_grad_rescale.argtypes = [vp, u64, vp, vp, vp, vp]
         L.cb_profile_enable.restype = i32
         L.cb_profile_enable.argtypes = [i32]
         L.cb_profile_read.restype = i32
@@ -330,6 +334,17 @@ def cb_scores_backward(h, m, prec, topk_idx_ptr, k, grad_ptr, log_scale_ptr, str
                                     ctypes.c_void_p(stream)))
 
 
+def cb_score_sum(S_ptr, n, nodes_ptr, k, loss_ptr, stream):
+    _check(lib().cb_score_sum(ctypes.c_void_p(S_ptr), n, ctypes.c_void_p(nodes_ptr), k,
+                              ctypes.c_void_p(loss_ptr), ctypes.c_void_p(stream)))
+
+
+def cb_grad_rescale(grad_ptr, count, ls_grad_ptr, ls_ref_ptr, grad_out_ptr, stream):
+    _check(lib().cb_grad_rescale(ctypes.c_void_p(grad_ptr), count, ctypes.c_void_p(ls_grad_ptr),
+                                 ctypes.c_void_p(ls_ref_ptr), ctypes.c_void_p(grad_out_ptr),
+                                 ctypes.c_void_p(stream)))
+
+
 def cb_profile_enable(on):
     _check(lib().cb_profile_enable(int(bool(on))))
 
@@ -539,28 +554,40 @@ def _summed_topk_function():
         """Loss = sum_r sum_{i in nodes} EBTC_r(i), scaled by exp(-log_scale),
         as a function of the (unit) edge weights of the handle's pattern.
 
-        forward(edge_weight, gs, m, nodes, prec) -> scaled loss (float64 0-dim)
-        backward gives d loss / d edge_weight from cb_scores_backward (the
-        edge-sensitivity map of the recovered sub-graph).  The store is
-        pattern-only, so edge_weight must be all ones.
+        forward(edge_weight, gs, m, nodes, prec) -> scaled loss (float64 0-dim),
+        the summed scores of the nodes (cb_ensemble_scores + cb_score_sum).
+        backward gives d loss / d edge_weight: cb_scores_backward, brought to
+        the forward's units and multiplied by the upstream gradient by
+        cb_grad_rescale (the edge-sensitivity map of the recovered sub-graph).
+        The store is pattern-only: the scores are those of unit weights, so
+        edge_weight must be all ones (anything else raises ValueError).
         """
 
         @staticmethod
         def forward(ctx, edge_weight, gs, m, nodes, prec=CB_FP32):
             if edge_weight.numel() != sum(gs.nnz):
                 raise ValueError("edge_weight must have one entry per CSR entry of the handle")
+            if not bool(torch.all(edge_weight == 1)):
+                raise ValueError("edge_weight must be all ones: the adjacency store is pattern-only, "
+                                 "so scores and gradients are those of unit weights")
             ls, S = ensemble_scores(gs, m, prec)
-            nodes_t = torch.as_tensor(nodes, dtype=torch.int64, device=S.device)
+            nodes_t = torch.as_tensor(np.asarray(nodes, dtype=np.int64).astype(np.int32),
+                                      device=S.device)
+            loss = torch.empty((), dtype=torch.float64, device=S.device)
+            cb_score_sum(S.data_ptr(), S.numel(), nodes_t.data_ptr(), nodes_t.numel(),
+                         loss.data_ptr(), _stream_handle(None))
             ctx.gs, ctx.m, ctx.nodes, ctx.prec = gs, m, nodes, prec
             ctx.save_for_backward(ls)
-            return S[nodes_t].sum()
+            return loss
 
         @staticmethod
         def backward(ctx, grad_out):
             (ls_fwd,) = ctx.saved_tensors
             ls_bw, grad = scores_backward(ctx.gs, ctx.m, ctx.nodes, ctx.prec)
-            scale = torch.exp(ls_bw - ls_fwd).to(torch.float32)
-            return grad * scale * grad_out.to(torch.float32), None, None, None, None
+            go = grad_out.to(dtype=torch.float64, device=grad.device).contiguous()
+            cb_grad_rescale(grad.data_ptr(), grad.numel(), ls_bw.data_ptr(), ls_fwd.data_ptr(),
+                            go.data_ptr(), _stream_handle(None))
+            return grad, None, None, None, None
 
     return SummedTopkScore
 

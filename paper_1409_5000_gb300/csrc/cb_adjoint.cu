@@ -27,6 +27,7 @@
 #include <cstdlib>
 
 #include "cb_contour.cuh"
+#include "cb_reduce.cuh"
 
 namespace cb {
 
@@ -424,6 +425,33 @@ CB_API int cb_scores_backward(cb_graph *h, uint32_t m, int prec, const uint32_t 
 namespace cb {
 namespace {
 
+// loss = sum over q of S[nodes[q]] for the nodes inside [0, n), FP64: lane l
+// sums q = l, l + 32, ... in order, then a fixed shuffle tree (deterministic).
+__global__ void __launch_bounds__(32) score_sum_kernel(const double *S, uint32_t n,
+                                                       const uint32_t *nodes, uint32_t k,
+                                                       double *out) {
+  double acc = 0.0;
+  for (uint32_t q = threadIdx.x; q < k; q += 32) {
+    const uint32_t i = nodes[q];
+    if (i < n) acc += S[i];
+  }
+  acc = warp_sum_d(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+// grad *= exp(ls_grad - ls_ref) * (grad_out ? *grad_out : 1), the factor
+// formed once in FP64 and applied in FP32.
+__global__ void __launch_bounds__(256) grad_rescale_kernel(float *g, uint64_t n,
+                                                           const double *ls_grad,
+                                                           const double *ls_ref,
+                                                           const double *grad_out) {
+  const double f64 = exp(*ls_grad - *ls_ref) * (grad_out ? *grad_out : 1.0);
+  const float f = (float)f64;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    g[i] *= f;
+}
+
 __global__ void scale_grad_kernel(float *g, uint64_t n, const double *ls_group,
                                   const double *ls_all) {
   const float f = (float)exp(*ls_group - *ls_all);
@@ -520,4 +548,28 @@ CB_API int cb_scores_backward_budget(cb_graph *h, uint32_t m, int prec, const ui
   }
   dev_free(d_ls);
   return rc;
+}
+
+CB_API int cb_score_sum(const double *S, uint32_t n, const uint32_t *nodes, uint32_t k,
+                        double *loss, void *stream) {
+  NvtxRange nvtx_range("cb_score_sum");
+  if (!S || !nodes || !loss) return set_error(CB_ERR_ARG, "cb_score_sum: null argument");
+  if (k < 1 || k > CB_MAX_TOPK)
+    return set_error(CB_ERR_ARG, "cb_score_sum: need 1 <= k <= CB_MAX_TOPK");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  score_sum_kernel<<<1, 32, 0, s>>>(S, n, nodes, k, loss);
+  return cuda_error(cudaGetLastError(), "cb_score_sum");
+}
+
+CB_API int cb_grad_rescale(float *grad, uint64_t count, const double *log_scale_grad,
+                           const double *log_scale_ref, const double *grad_out, void *stream) {
+  NvtxRange nvtx_range("cb_grad_rescale");
+  if (!grad || !log_scale_grad || !log_scale_ref)
+    return set_error(CB_ERR_ARG, "cb_grad_rescale: null argument");
+  if (count == 0) return CB_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t blocks = std::min<uint64_t>((count + 255) / 256, 152ull * 8);
+  grad_rescale_kernel<<<(uint32_t)blocks, 256, 0, s>>>(grad, count, log_scale_grad, log_scale_ref,
+                                                       grad_out);
+  return cuda_error(cudaGetLastError(), "cb_grad_rescale");
 }

@@ -1,4 +1,5 @@
-// Top-k selection of the summed scores ("the largest 20 EBTC values").
+// Top-k selection of the summed scores of eq. 5 (section "Identification
+// algorithm": the recovered target is the k nodes of largest summed EBTC).
 //
 // The paper sorts all n scores (Introsort, O(n log n)).  Only the k largest
 // are needed, so this selects them by most-significant-digit radix select
@@ -245,27 +246,68 @@ constexpr size_t kNoAllocScratchBytes =
 // Shared by every cb_topk_noalloc call on a device; resident until exit.
 __device__ __align__(256) unsigned char g_topk_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// The array's device address belongs to the CUDA context that loaded the
+// module, so it is cached per context: keyed by the context's process-unique
+// id (cuCtxGetId), which a context created after cudaDeviceReset, or another
+// context made current on the same device, does not share.  The driver
+// functions come through the runtime's entry-point query, so the library
+// needs no link against the driver library.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+constexpr int kMaxContexts = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxContexts] = {};
+void *g_noalloc_ptr[kMaxContexts] = {};
+int g_noalloc_used = 0;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
-// Device address of the scratch array on the current device.  The host-side
-// symbol is only a stand-in, so the address is looked up once per device
-// (with that device current) and cached.
+// Device address of the scratch array in the current context.  The host-side
+// symbol is only a stand-in, so the address is looked up (with the context
+// current) the first time a context calls, and cached.
 int noalloc_scratch(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cb_topk_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices)
-    return set_error(CB_ERR_ARG, "cb_topk_noalloc: device index beyond the supported range");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_topk_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_error(e, "cb_topk_noalloc: cudaGetSymbolAddress");
-    g_noalloc_ptr[dev] = p;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&g_ctx_get_current, 12000,
+                                         cudaEnableDefault, &q1);
+    if (e == cudaSuccess)
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&g_ctx_get_id, 12000,
+                                           cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      g_ctx_get_current = nullptr;
+      g_ctx_get_id = nullptr;
+      return set_error(CB_ERR_CUDA, "cb_topk_noalloc: driver context query unavailable");
+    }
   }
-  *out = g_noalloc_ptr[dev];
+  void *ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != 0 || !ctx) {
+    // no context current on this thread yet: make the device's primary
+    // context current (cudaSetDevice initialises it; no allocation)
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_error(e, "cb_topk_noalloc: cudaSetDevice");
+    if (g_ctx_get_current(&ctx) != 0 || !ctx)
+      return set_error(CB_ERR_CUDA, "cb_topk_noalloc: no current CUDA context");
+  }
+  unsigned long long id = 0;
+  if (g_ctx_get_id(ctx, &id) != 0) return set_error(CB_ERR_CUDA, "cb_topk_noalloc: cuCtxGetId failed");
+  for (int q = 0; q < g_noalloc_used; ++q)
+    if (g_noalloc_ctx[q] == id) {
+      *out = g_noalloc_ptr[q];
+      return CB_OK;
+    }
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_topk_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_error(e, "cb_topk_noalloc: cudaGetSymbolAddress");
+  if (g_noalloc_used < kMaxContexts) {  // beyond that many contexts: looked up every call
+    g_noalloc_ctx[g_noalloc_used] = id;
+    g_noalloc_ptr[g_noalloc_used] = p;
+    ++g_noalloc_used;
+  }
+  *out = p;
   return CB_OK;
 }
 

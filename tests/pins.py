@@ -15,7 +15,7 @@ disagrees with:
 * exactness of the Lanczos approximation once m reaches the dimension of
   the Krylov space K(A, 1);
 * linearity of the ensemble sum (eq. 5) and its N = 1 reduction;
-* the top-k rule (a full sort, paper: "the largest 20 EBTC values")
+* the top-k rule (a full sort, the paper's selection in "Identification algorithm")
   against a brute-force Python sort with ties.
 """
 from __future__ import annotations

@@ -149,6 +149,52 @@ def test_autograd_function(B):
         expect = g * torch.exp(ls_b - ls_f).float()
         assert torch.allclose(wgt.grad, expect, rtol=1e-6, atol=0)
         assert abs(loss.item() - S[torch.as_tensor(nodes, device="cuda")].sum().item()) <= 1e-12 * abs(loss.item())
+        # an upstream factor scales the gradient (vector-Jacobian product)
+        wgt.grad = None
+        loss = B.summed_topk_score(wgt, gs, 20, nodes)
+        (3.0 * loss).backward()
+        assert torch.allclose(wgt.grad, 3.0 * expect, rtol=1e-6, atol=0)
+
+
+def test_autograd_rejects_non_unit_weights(B):
+    """The store is pattern-only: weights other than one would silently give
+    unit-weight results, so they are refused."""
+    ens = synth.er_ensemble_small()
+    nodes = [int(x) for x in ens.target]
+    with B.GraphSet(ens.graphs) as gs:
+        wgt = torch.ones(sum(gs.nnz), dtype=torch.float32, device="cuda", requires_grad=True)
+        with torch.no_grad():
+            wgt[7] = 1.5
+        with pytest.raises(ValueError, match="all ones"):
+            B.summed_topk_score(wgt, gs, 20, nodes)
+        with pytest.raises(ValueError, match="one entry per CSR entry"):
+            B.summed_topk_score(wgt[:-1], gs, 20, nodes)
+
+
+def test_score_sum_and_grad_rescale(B):
+    """cb_score_sum against a host sum over the node set (entries >= n
+    skipped); cb_grad_rescale against exp(ls_g - ls_r) * grad_out."""
+    S = torch.rand(1000, dtype=torch.float64, device="cuda")
+    nodes = torch.tensor([5, 999, 1000, 3, 5, 4000], dtype=torch.int32, device="cuda")
+    out = torch.empty((), dtype=torch.float64, device="cuda")
+    B.cb_score_sum(S.data_ptr(), 1000, nodes.data_ptr(), 6, out.data_ptr(),
+                   torch.cuda.current_stream().cuda_stream)
+    Sh = S.cpu().numpy()
+    ref = Sh[5] + Sh[999] + Sh[3] + Sh[5]
+    assert abs(out.item() - ref) <= 1e-15 * ref
+    g = torch.randn(100_003, dtype=torch.float32, device="cuda")
+    g0 = g.clone()
+    lg = torch.tensor([3.25], dtype=torch.float64, device="cuda")
+    lr = torch.tensor([2.0], dtype=torch.float64, device="cuda")
+    go = torch.tensor([-0.5], dtype=torch.float64, device="cuda")
+    B.cb_grad_rescale(g.data_ptr(), g.numel(), lg.data_ptr(), lr.data_ptr(), go.data_ptr(),
+                      torch.cuda.current_stream().cuda_stream)
+    f = math.exp(1.25) * -0.5
+    g1 = g.cpu().numpy()
+    assert np.allclose(g1, g0.cpu().numpy().astype(np.float64) * f, rtol=3e-7, atol=0)
+    B.cb_grad_rescale(g.data_ptr(), g.numel(), lg.data_ptr(), lg.data_ptr(), 0,
+                      torch.cuda.current_stream().cuda_stream)  # factor exactly 1
+    assert np.array_equal(g.cpu().numpy(), g1)
 
 
 def test_forward_basis_reuse(B):
