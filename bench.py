@@ -75,46 +75,64 @@ def workload(name):
     return ens, desc
 
 
-# DRAM bytes per CSR entry of the dominant SpMV kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the column-blocked kernel
-# on the 40-realisation case of the default recipe; reported only while the
-# source that decides its traffic (kernel, epilogue, format builder, blocked
+# DRAM bytes per CSR entry of the dominant SpMV kernel(s), from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum): the column-blocked
+# kernel on the 40-realisation case of the default recipe, and the two
+# phases of the two-phase kernel on the large graph.  Reported only while the
+# source that decides the traffic (kernels, epilogue, format builder,
 # constants) still hashes to the captured version.
-_TRAFFIC = {"sources_sha256_16": "25d711221a8f350f", "bytes_per_edge": (778.643712e6 + 18.272512e6) / 151654698,
-            "kernel": "bspmv_kernel", "captured_on": "er-ensemble-40"}
+_TRAFFIC = {
+    "blocked": {"sources_sha256_16": None, "bytes_per_edge": None, "kernel": "bspmv_kernel",
+                "captured_on": "er-ensemble-40"},
+    "twophase": {"sources_sha256_16": None, "bytes_per_edge": None,
+                 "kernel": "pscatter_kernel + pgather_kernel", "captured_on": "ba-1e7"},
+}
 
 
-def _kernel_sources_hash():
-    """Hash of the source that decides the blocked SpMV's memory traffic: the
-    kernel and its staging helpers, the row epilogue, the blocked-format
-    kernels and the blocked constants."""
+def _cut(text, start, end_marker):
+    a = text.index(start)
+    return text[a:text.index(end_marker, a)]
+
+
+def _kernel_sources_hash(kind="blocked"):
+    """Hash of the source that decides an SpMV path's memory traffic: its
+    kernels and staging helpers, the row epilogue, its format builder and its
+    constants."""
     import hashlib
     import re
 
     csrc = os.path.join(ROOT, "paper_1409_5000_gb300", "csrc")
-    with open(os.path.join(csrc, "cb_lanczos.cu")) as f:
-        lz = f.read()
-    parts = []
-    a = lz.index("// mbarrier and bulk-copy helpers")
-    b = lz.index("\n}\n", lz.index("bspmv_kernel(LArgs a"))
-    parts.append(lz[a:b])
-    a = lz.index("__device__ __forceinline__ T row_epilogue")
-    parts.append(lz[a:lz.index("\n}\n", a)])
-    with open(os.path.join(csrc, "cb_blocked.cu")) as f:
-        bl = f.read()  # the count and fill kernels (host code does not change the format)
-    parts.append(bl[bl.index("__global__"):bl.index("size_t fill_smem_bytes")])
-    with open(os.path.join(csrc, "cb_internal.cuh")) as f:
-        parts += re.findall(r"^constexpr [^\n]*\bk(?:B\w*|Threads|Group)\b[^\n]*$", f.read(), re.M)
+
+    def rd(name):
+        with open(os.path.join(csrc, name)) as f:
+            return f.read()
+
+    step = rd("cb_step.cuh")
+    parts = [_cut(step, "__device__ __forceinline__ T row_epilogue", "\n}\n"),
+             _cut(step, "// mbarrier and bulk-copy helpers", "// Two-phase SpMV step of")]
+    consts = rd("cb_internal.cuh")
+    if kind == "blocked":
+        lz = rd("cb_lanczos.cu")
+        parts.append(_cut(lz, "constexpr size_t kBSmemBytes", "// w = W_{j+1} - alpha_j"))
+        bl = rd("cb_blocked.cu")  # the count and fill kernels (host code does not change the format)
+        parts.append(_cut(bl, "__global__", "size_t fill_smem_bytes"))
+        parts += re.findall(r"^constexpr [^\n]*\bk(?:B\w*|Threads|Group)\b[^\n]*$", consts, re.M)
+    else:
+        tp = rd("cb_twophase.cu")
+        parts.append(_cut(tp, "__global__", "template <typename P>"))
+        parts += re.findall(r"^constexpr [^\n]*\bk(?:P\w*|HeavyDeg|LongDeg|Chunk|Group)\b[^\n]*$",
+                            consts, re.M)
     h = hashlib.sha256()
     for p in parts:
         h.update(p.encode())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(ens, blocked_path):
-    if not blocked_path or _kernel_sources_hash() != _TRAFFIC["sources_sha256_16"]:
+def traffic_per_launch(ens, kind):
+    t = _TRAFFIC[kind]
+    if t["bytes_per_edge"] is None or _kernel_sources_hash(kind) != t["sources_sha256_16"]:
         return None
-    return _TRAFFIC["bytes_per_edge"] * sum(g.nnz for g in ens.graphs)
+    return t["bytes_per_edge"] * sum(g.nnz for g in ens.graphs)
 
 
 def alg_bytes_spmv(ens, fp64=False):
@@ -417,12 +435,18 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
     blocked_path = max(g.n for g in ens.graphs) <= 32 * 16384 and not args.csr_only
-    kname = ("bspmv_kernel (column-blocked Lanczos SpMV step)" if blocked_path
-             else "spmv_kernel (tiled-CSR Lanczos SpMV step)")
+    twophase_path = not blocked_path and not args.csr_only
+    if blocked_path:
+        kname = "bspmv_kernel (column-blocked Lanczos SpMV step)"
+    elif twophase_path:
+        kname = "pscatter_kernel + pgather_kernel (two-phase Lanczos SpMV step)"
+    else:
+        kname = "spmv_kernel (tiled-CSR Lanczos SpMV step)"
+    path_kind = "blocked" if blocked_path else ("twophase" if twophase_path else None)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                 "frac_of_8TBs_nominal": achieved / 8000.0,
-                "traffic": traffic_per_launch(ens, blocked_path),
+                "traffic": traffic_per_launch(ens, path_kind) if path_kind else None,
                 "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
                 "kernel_shares": {kname: round(t / tot, 4) for kname, (t, _) in fam.items()}}
     # init (2) + SpMV, finalize and beta per Lanczos step + tridiag + combine (2)

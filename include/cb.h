@@ -66,6 +66,7 @@ extern "C" {
 #define CB_VALIDATE 1u    /* check CSR invariants on the host before upload */
 #define CB_DEVICE_PTRS 2u /* row_ptr[r] / col[r] are device pointers */
 #define CB_CSR_ONLY 4u    /* no column-blocked format: every FP32 SpMV gathers from the CSR */
+#define CB_TWO_PHASE 8u   /* the two-phase format for every realisation (default: n > 2^19 only) */
 
 /* largest Krylov depth accepted by the compute calls */
 #define CB_MAX_M 128
@@ -104,10 +105,17 @@ typedef struct {
  *              still detected on the device (CB_ERR_ARG).
  *              CB_DEVICE_PTRS: row_ptr[r] and col[r] are device pointers.
  *              CB_CSR_ONLY: skip the column-blocked format that FP32 calls
- *              use for realisations with n <= 32 * 16384; they then run the
- *              tiled-CSR SpMV (same recurrence, FP32 rounding differs), the
- *              upload is shorter and the handle ~3 B per entry smaller.
- *              Other bits: CB_ERR_ARG.
+ *              use for realisations with n <= 32 * 16384, and the two-phase
+ *              format of larger ones; they then run the tiled-CSR SpMV (same
+ *              recurrence, FP32 rounding differs), the upload is shorter and
+ *              the handle ~3 B per entry smaller.
+ *              CB_TWO_PHASE: build the two-phase format (FP32 SpMV in two
+ *              passes over a stream of edge values, both gathering from
+ *              shared memory) for every realisation instead of only those
+ *              with n > 32 * 16384; about 8 B per entry on the device.
+ *              Realisations with n > 2^27 run the tiled-CSR SpMV.
+ *              CB_CSR_ONLY with CB_TWO_PHASE, or other bits: CB_ERR_ARG.
+ *              A column index >= n fails the two-phase build (CB_ERR_ARG).
  *   stream     used for the copies.  The call synchronises `stream` before
  *              returning, so the input arrays may be freed afterwards.
  *   out        receives the handle.

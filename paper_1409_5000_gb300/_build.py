@@ -25,7 +25,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["cb_api.cu", "cb_lanczos.cu", "cb_tridiag.cu", "cb_combine.cu", "cb_topk.cu",
               "cb_adjoint.cu", "cb_blocked.cu", "cb_generate.cu",
-              "cb_subgraph.cu", "cb_restart.cu"]
+              "cb_subgraph.cu", "cb_restart.cu", "cb_twophase.cu"]
 
 
 def cb_lib_path() -> str:

@@ -22,7 +22,7 @@ from ._build import cb_lib_path, INCLUDE
 CB_OK, CB_ERR_ARG, CB_ERR_CUDA, CB_ERR_OOM, CB_ERR_TIMEOUT, CB_ERR_NONFINITE, CB_ERR_STATE = range(7)
 CB_FP32, CB_FP64 = 0, 1
 CB_REORTH = 0x100  # OR into prec: full reorthogonalisation (two Gram-Schmidt passes)
-CB_VALIDATE, CB_DEVICE_PTRS, CB_CSR_ONLY = 1, 2, 4
+CB_VALIDATE, CB_DEVICE_PTRS, CB_CSR_ONLY, CB_TWO_PHASE = 1, 2, 4, 8
 CB_MAX_M, CB_MAX_TOPK, CB_MAX_CYCLES = 128, 4096, 1024
 
 
@@ -378,10 +378,11 @@ def _ptr(a):
 class GraphSet:
     """A handle holding N realisations on the current CUDA device."""
 
-    def __init__(self, graphs, validate=False, stream=None, csr_only=False):
+    def __init__(self, graphs, validate=False, stream=None, csr_only=False, two_phase=False):
         """`graphs`: sequence of objects with .n, .row_ptr, .col (numpy uint32
         arrays, host or pinned torch tensors, or CUDA torch tensors).
-        `csr_only`: no column-blocked format (CB_CSR_ONLY)."""
+        `csr_only`: no column-blocked or two-phase format (CB_CSR_ONLY).
+        `two_phase`: the two-phase format for every realisation (CB_TWO_PHASE)."""
         import torch
 
         graphs = list(graphs)
@@ -389,7 +390,7 @@ class GraphSet:
         if any(dev) and not all(dev):
             raise ValueError("all realisations must be on the host or all on the device")
         flags = ((CB_VALIDATE if validate else 0) | (CB_DEVICE_PTRS if all(dev) else 0)
-                 | (CB_CSR_ONLY if csr_only else 0))
+                 | (CB_CSR_ONLY if csr_only else 0) | (CB_TWO_PHASE if two_phase else 0))
         keep = []
         rps, cols = [], []
         for g in graphs:

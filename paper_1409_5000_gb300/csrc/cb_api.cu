@@ -527,8 +527,10 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   *out = nullptr;
   if (n_inst == 0 || !n || !nnz || !row_ptr || !col)
     return set_error(CB_ERR_ARG, "cb_graph_upload: empty input or null array");
-  if (flags & ~(CB_VALIDATE | CB_DEVICE_PTRS | CB_CSR_ONLY))
+  if (flags & ~(CB_VALIDATE | CB_DEVICE_PTRS | CB_CSR_ONLY | CB_TWO_PHASE))
     return set_error(CB_ERR_ARG, "cb_graph_upload: unknown flag");
+  if ((flags & CB_CSR_ONLY) && (flags & CB_TWO_PHASE))
+    return set_error(CB_ERR_ARG, "cb_graph_upload: CB_CSR_ONLY and CB_TWO_PHASE exclude each other");
   const bool dev = (flags & CB_DEVICE_PTRS) != 0;
   if (dev && (flags & CB_VALIDATE))
     return set_error(CB_ERR_ARG, "cb_graph_upload: CB_VALIDATE needs host arrays");
@@ -538,6 +540,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   cb_graph *h = new cb_graph();
   cudaGetDevice(&h->device);
   h->csr_only = (flags & CB_CSR_ONLY) != 0;
+  h->force_pb = (flags & CB_TWO_PHASE) != 0;
   h->n_inst = n_inst;
   h->inst.resize(n_inst);
 
@@ -740,6 +743,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   std::vector<const uint32_t *> rpv(n_inst);
   for (uint32_t r = 0; r < n_inst; ++r) rpv[r] = rp_of(r);
   int rc = build_blocked(h, rpv, s, cp.groups);
+  if (rc == CB_OK) rc = build_twophase(h, rpv, s, cp.groups, h->force_pb);
   if (rc == CB_OK) {  // every copy has landed before the handle is returned
     for (const CopyGroup &g : cp.groups) chk(cudaStreamWaitEvent(s, g.ev, 0));
     chk(cudaStreamSynchronize(s));
@@ -747,6 +751,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   }
   cp.finish();
   if (rc != CB_OK) {
+    free_twophase(h);
     free_blocked(h);
     free_graph_arrays(h);
     delete h;
@@ -851,6 +856,7 @@ CB_API int cb_graph_free(cb_graph *h) {
   free_workspace(h->ws);
   free_workspace(h->ws2);
   free_backwork(h->bw);
+  free_twophase(h);
   free_blocked(h);
   free_graph_arrays(h);
   delete h;

@@ -250,7 +250,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
   std::vector<std::vector<uint32_t>> lrows(h->n_inst), lcount(h->n_inst);
   parallel_for(h->n_inst, [&](uint32_t r) {
     const InstDesc &I = h->inst[r];
-    if (I.n > kBMaxBlocks * kBCol) return;
+    if (h->force_pb || I.n > kBMaxBlocks * kBCol) return;
     const uint32_t *rp = rp_host[r];
     const uint32_t ntile = (I.n + kBTileRows - 1) / kBTileRows;
     for (uint32_t q = 0; q < ntile; ++q) {
@@ -266,7 +266,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
   });
   for (uint32_t r = 0; r < h->n_inst; ++r) {
     InstDesc &I = h->inst[r];
-    I.blocked = I.n <= kBMaxBlocks * kBCol ? 1u : 0u;
+    I.blocked = !h->force_pb && I.n <= kBMaxBlocks * kBCol ? 1u : 0u;
     I.nb = I.blocked ? (I.n + kBCol - 1) / kBCol : 0u;
     I.btile_base = nbt;
     I.n_btiles = I.blocked ? (I.n + kBTileRows - 1) / kBTileRows : 0u;

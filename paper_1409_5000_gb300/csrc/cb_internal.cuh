@@ -46,6 +46,34 @@ constexpr uint32_t kBBuf = kBPadCol + 4;                 // floats per staging b
 constexpr uint32_t kBMaxBlocks = 32;                     // blocked when n <= 32 * kBCol
 constexpr uint32_t kBLongDeg = 512;                      // longer rows: whole-CTA global gathers
 
+// Two-phase (propagation-blocked) SpMV (FP32), for realisations too large
+// for the column-blocked kernel.  Columns are cut into source tiles of kPSrc
+// nodes and rows into bins whose entries fit a shared-memory region.
+// Phase 1 stages a source tile of W_j in shared memory and writes, for every
+// entry, the gathered value into a stream ordered by (source tile, bin);
+// phase 2 copies a bin's chunks of that stream into shared memory and sums
+// each row from there.  Both phases gather from shared memory only.
+constexpr uint32_t kPSrcBits = 15;
+constexpr uint32_t kPSrc = 1u << kPSrcBits;  // nodes per source tile (128 KB of W_j)
+constexpr uint32_t kPMaxSrc = 4096;          // source tiles per realisation (n <= 2^27)
+constexpr uint32_t kPRegion = 24576;         // values per bin region (96 KB)
+constexpr uint32_t kPBinRows = 2048;         // most rows per bin
+constexpr uint32_t kPPieceUnits = 32768;     // 4-value units per phase-1 CTA (128K values)
+constexpr int kP1Threads = 1024;             // phase-1 CTA (one per SM: 128 KB tile)
+constexpr int kP2Threads = 512;              // phase-2 CTA (two per SM: 96 KB region)
+
+// A bin: consecutive rows [row0, row1) of realisation inst, none heavier
+// than kHeavyDeg, whose entries (with chunk padding) fit kPRegion.
+struct PBin {
+  uint32_t inst, row0, row1, pad;
+};
+// A phase-1 work item: units [u0, u0 + nu) of the stream of source tile
+// `tile` (local index) of realisation inst.
+struct PPiece {
+  uint64_t u0;
+  uint32_t nu, inst, tile, pad;
+};
+
 // Two-level deterministic reduction plan of one instance for one kernel kind:
 // one partial per slot, slots grouped by kGroup; the last CTA to arrive in a
 // group sums the group, the last group of the instance sums the groups.
@@ -69,6 +97,13 @@ struct InstDesc {
   uint32_t blocked, nb;           // column-blocked FP32 SpMV? number of column blocks
   uint32_t btile_base, n_btiles;  // blocked tiles (kBTileRows rows each)
   RedPlan bspmv;                  // slots: n_btiles
+  uint32_t pb, pns;               // two-phase FP32 SpMV? number of source tiles
+  uint32_t ptile_base;            // first source tile (handle-wide index)
+  uint32_t pbin_base, n_pbin;     // bins
+  uint32_t ppiece_base, n_ppiece; // phase-1 work items
+  uint32_t pad_p;
+  uint64_t pmat_base;             // offset of the [bin][pns + 1] chunk tables
+  RedPlan pspmv;                  // slots: n_pbin bins, then n_heavy rows
 };
 
 struct HeavyRow {
@@ -124,6 +159,7 @@ struct BackWork {
 struct cb_graph {
   int device = 0;
   bool csr_only = false;  // CB_CSR_ONLY: no column-blocked format
+  bool force_pb = false;  // CB_TWO_PHASE: the two-phase format for every realisation
   uint32_t n_inst = 0;
   uint32_t n_max = 0;
   uint64_t total_nodes_padded = 0;  // sum of padded node ranges
@@ -156,6 +192,21 @@ struct cb_graph {
   uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane (padding: 0)
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
+  // two-phase format (FP32 SpMV), for realisations with pb = 1
+  uint32_t total_ptiles = 0, total_pbins = 0, total_ppieces = 0;
+  uint32_t pns_max = 0;                  // most source tiles of one realisation
+  uint64_t total_punits = 0;             // 4-value units of the stream
+  cb::PBin *d_pbin = nullptr;
+  cb::PPiece *d_ppiece = nullptr;
+  uint64_t *d_ptbase = nullptr;          // per source tile: first unit of its stream
+  uint32_t *d_ptotal = nullptr;          // per source tile: units of its stream (build)
+  uint32_t *d_ptile_inst = nullptr;      // per source tile: its realisation (build)
+  uint32_t *d_proff = nullptr;           // [bin][s]: unit offset of chunk (s, bin) in the region
+                                         //   ([bin][pns]: units of the region)
+  uint32_t *d_pcstart = nullptr;         // [bin][s]: unit offset of chunk (s, bin) in tile s's stream
+  uint16_t *d_ppos = nullptr;            // per CSR entry of a bin row: its slot in the bin region
+  uint16_t *d_psrc = nullptr;            // per stream slot: source node within its tile
+  float *d_pX = nullptr;                 // per stream slot: the value phase 1 writes
   // captured ensemble pass (one CUDA graph per m / precision / outputs)
   struct GraphEntry {
     uint32_t m;
@@ -259,6 +310,11 @@ cudaError_t exclusive_scan(const uint32_t *in, uint64_t n, uint64_t *out, uint64
 int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
                   const std::vector<CopyGroup> &groups);
 void free_blocked(cb_graph *h);
+// two-phase format builder (cb_twophase.cu); force: every realisation, else
+// those above the column-blocked size limit
+int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
+                   const std::vector<CopyGroup> &groups, bool force);
+void free_twophase(cb_graph *h);
 
 // workspace for depth m in precision prec (cb_api.cu)
 int ensure_workspace(cb_graph *h, Workspace &W, uint32_t m, int prec, cudaStream_t s);

@@ -38,53 +38,10 @@
 
 #include "cb_internal.cuh"
 #include "cb_reduce.cuh"
+#include "cb_step.cuh"
 
 namespace cb {
 
-struct LArgs {
-  const InstDesc *inst;
-  const uint32_t *tile_inst;
-  const uint2 *tile_rows;
-  const HeavyRow *heavy;
-  const uint32_t *chunk_heavy;
-  const uint32_t *fin_inst;
-  const uint32_t *row_ptr;
-  const uint32_t *col;
-  void *V;
-  uint64_t vs;  // vector stride (elements)
-  Scalars sc;
-  RedBufs red;
-  double *cpart;   // per heavy-row chunk partial sums
-  uint32_t *hcnt;  // per heavy row arrival counters
-  double tau;      // breakdown tolerance
-  // column-blocked format (FP32 path)
-  const uint32_t *btile_inst;
-  const uint64_t *bseg_base, *bwstart;
-  const uint32_t *bwlen;
-  const uint16_t *bcol;
-  const uint8_t *bslot;
-  const uint32_t *blong_ptr, *blong_rows;
-  uint32_t skip_blocked;  // the tiled-CSR kernel leaves blocked realisations alone
-  uint32_t stall_btile;   // test hook: this tile's first column block is never copied
-};
-
-// Column indices are read once per step: streaming (evict-first) load.
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(p); }
-
-template <typename T>
-__device__ __forceinline__ T ld_vec(const T *p) {
-  return __ldg(p);
-}
-
-// Row epilogue: u = sj*sum - bp*W_{j-1}[row]; store; return W_j[row]*u.
-template <typename T>
-__device__ __forceinline__ T row_epilogue(T sum, uint32_t row, const T *x, const T *xp, T *out,
-                                          T sj, T bp, bool has_prev) {
-  T u = sj * sum;
-  if (has_prev) u -= bp * xp[row];
-  out[row] = u;
-  return x[row] * u;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) init_vec_kernel(LArgs a, uint32_t r0, uint32_t r1,
@@ -155,16 +112,6 @@ __global__ void __launch_bounds__(kThreads) init_scalars_kernel(LArgs a, uint32_
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void finish_alpha(const LArgs &a, uint32_t r, uint32_t j, double total) {
-  const uint32_t ms = a.sc.ms;
-  const double alpha = a.sc.scale[r * ms + j] * total;
-  a.sc.alpha[r * ms + j] = alpha;
-  if (!isfinite(alpha)) {
-    if (a.sc.status[r] == CB_OK) a.sc.status[r] = CB_ERR_NONFINITE;
-    a.sc.meff[r] = j;  // stop; this realisation is reported as failed
-  }
-}
 
 // One Lanczos SpMV step over a range of realisations.
 // Blocks [0, n_chunks) are heavy-row chunks starting at chunk_off; blocks
@@ -177,7 +124,6 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
   __shared__ uint16_t s_med[kTileRows], s_long[kTileRows];
   __shared__ uint32_t s_wcnt[kThreads / 32][2];
   __shared__ uint32_t s_nmed, s_nlong;
-  __shared__ int s_last;
   __shared__ T s_rowsum[32];
 
   const uint32_t ms = a.sc.ms;
@@ -195,6 +141,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
   }
   if (j >= a.sc.meff[r]) return;  // realisation stopped (uniform per CTA)
   if (a.skip_blocked && a.inst[r].blocked) return;  // the column-blocked kernel owns it
+  if (a.skip_pb && a.inst[r].pb) return;            // the two-phase kernels own it
 
   const InstDesc &I = a.inst[r];
   const uint32_t *rp = a.row_ptr + I.rp_base;
@@ -208,33 +155,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
   const T bp = has_prev ? (T)(a.sc.beta[r * ms + j - 1] * a.sc.scale[r * ms + j - 1]) : T(0);
 
   if (is_chunk) {
-    // ---- one chunk of a heavy row ----
-    const HeavyRow H = a.heavy[hid];
-    const uint32_t c = cidx - H.chunk_base;
-    const uint32_t e0 = rp[H.row] + c * kChunk;
-    const uint32_t e1 = min(e0 + kChunk, rp[H.row + 1]);
-    T s = T(0);
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kThreads) s += ld_vec(x + ld_stream(col + e));
-    const double part = block_sum_to_double<T>(s, s_red);
-    if (threadIdx.x == 0) {
-      a.cpart[cidx] = part;
-      __threadfence();
-      const uint32_t prev = atomicAdd(&a.hcnt[hid], 1u);
-      s_last = (prev == H.n_chunks - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double dot = 0.0;
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (uint32_t q = 0; q < H.n_chunks; ++q) tot += __ldcg(&a.cpart[H.chunk_base + q]);
-      a.hcnt[hid] = 0u;
-      dot = (double)row_epilogue<T>((T)tot, H.row, x, xp, out, sj, bp, has_prev);
-    }
-    const uint32_t slot = I.n_tiles + (hid - I.heavy_base);
-    double total;
-    if (arrive_and_reduce(I.spmv, slot, r, dot, a.red, &total)) finish_alpha<T>(a, r, j, total);
+    heavy_chunk<T>(a, j, cidx, hid, r, I.spmv, I.n_tiles + (hid - I.heavy_base));
     return;
   }
 
@@ -355,60 +276,6 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
 // (slot-major, so the accumulator traffic is conflict-free); every row has a
 // single writer, so the result is deterministic.
 // ---------------------------------------------------------------------------
-// mbarrier and bulk-copy helpers (shared-window addresses).
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait for the phase of `parity` to complete: false after 1 s of
-// global time or kSpinLimit polls, whichever comes first.
-constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 1000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1; it < kSpinLimit; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 15u) == 0 && global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-// One bulk copy global -> shared whose bytes complete on `bar` (16-byte
-// aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Prefetch of a global range into L2 (16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 // two column blocks of W_j (each followed by its zero word), then
 // kBRowsPerThread accumulator slots per thread
@@ -904,6 +771,16 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   const bool use_blocked = sizeof(T) == 4 && h->total_btiles > 0;
   a.skip_blocked = use_blocked ? 1u : 0u;
   a.stall_btile = h->stall_btile;
+  a.pbin = h->d_pbin;
+  a.ppiece = h->d_ppiece;
+  a.ptbase = h->d_ptbase;
+  a.proff = h->d_proff;
+  a.pcstart = h->d_pcstart;
+  a.ppos = h->d_ppos;
+  a.psrc = h->d_psrc;
+  a.pX = h->d_pX;
+  const bool use_pb = sizeof(T) == 4 && h->total_ptiles > 0;
+  a.skip_pb = use_pb ? 1u : 0u;
 
   const InstDesc &A0 = h->inst[r0], &A1 = h->inst[r1 - 1];
   const uint32_t chunk_off = A0.chunk_base;
@@ -914,8 +791,16 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   const uint32_t n_fin = A1.fin_base + A1.n_fin - fin_off;
   const uint32_t btile_off = A0.btile_base;
   const uint32_t n_btiles = use_blocked ? A1.btile_base + A1.n_btiles - btile_off : 0u;
-  bool any_csr = !use_blocked;  // does the tiled-CSR kernel have work in the range?
-  for (uint32_t r = r0; r < r1 && !any_csr; ++r) any_csr = !h->inst[r].blocked;
+  const uint32_t piece_off = A0.ppiece_base;
+  const uint32_t n_pieces = use_pb ? A1.ppiece_base + A1.n_ppiece - piece_off : 0u;
+  const uint32_t bin_off = A0.pbin_base;
+  const uint32_t n_bins = use_pb ? A1.pbin_base + A1.n_pbin - bin_off : 0u;
+  bool any_pb = false;  // two-phase realisations in the range (their heavy rows too)
+  for (uint32_t r = r0; r < r1 && use_pb; ++r) any_pb |= h->inst[r].pb != 0;
+  // does the tiled-CSR kernel have work in the range?
+  bool any_csr = false;
+  for (uint32_t r = r0; r < r1 && !any_csr; ++r)
+    any_csr = !(use_blocked && h->inst[r].blocked) && !(use_pb && h->inst[r].pb);
   if (n_btiles) {
     static bool attr_set = false;  // one-time opt-in to > 48 KB of shared memory
     if (!attr_set) {
@@ -948,6 +833,9 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
     tok = prof_begin(CB_K_SPMV, s);
     if (any_csr) launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);
     if (n_btiles) bspmv_kernel<<<n_btiles, kBThreads, kBSmemBytes, s>>>(a, j, btile_off);
+    if (any_pb)
+      launch_twophase(a, h->lanes, j, piece_off, n_pieces, chunk_off, n_chunks, bin_off, n_bins,
+                      h->pns_max, s);
     prof_end(tok, s);
     tok = prof_begin(CB_K_FINALIZE, s);
     if (n_fin) {

@@ -52,10 +52,14 @@ def test_argument_errors_need_no_device(libcb):
     nnz = (ctypes.c_uint64 * 1)(0)
     rp = (ctypes.c_uint32 * 5)()
     rpp = (ctypes.c_void_p * 1)(ctypes.addressof(rp))
-    unknown = 8
-    assert unknown & (binding.CB_VALIDATE | binding.CB_DEVICE_PTRS | binding.CB_CSR_ONLY) == 0
+    unknown = 16
+    assert unknown & (binding.CB_VALIDATE | binding.CB_DEVICE_PTRS | binding.CB_CSR_ONLY
+                      | binding.CB_TWO_PHASE) == 0
     assert L.cb_graph_upload(1, n, nnz, rpp, rpp, unknown, None, ctypes.byref(out)) == binding.CB_ERR_ARG
     assert b"unknown flag" in L.cb_last_error()
+    both = binding.CB_CSR_ONLY | binding.CB_TWO_PHASE
+    assert L.cb_graph_upload(1, n, nnz, rpp, rpp, both, None, ctypes.byref(out)) == binding.CB_ERR_ARG
+    assert b"exclude each other" in L.cb_last_error()
     assert L.cb_communicability(None, 0, 10, 0, None, None, None, None) == binding.CB_ERR_ARG
     assert L.cb_ensemble_scores(None, 10, 0, 5, None, None, None, None) == binding.CB_ERR_ARG
     assert b"null" in L.cb_last_error()

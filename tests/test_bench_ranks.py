@@ -77,6 +77,9 @@ def test_traffic_guard_hashes_the_kernel_sources():
     spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    h = bench._kernel_sources_hash()
-    assert len(h) == 16 and int(h, 16) >= 0
-    assert bench._TRAFFIC["bytes_per_edge"] > 3.0  # at least the 3 B of an element
+    for kind in ("blocked", "twophase"):
+        h = bench._kernel_sources_hash(kind)
+        assert len(h) == 16 and int(h, 16) >= 0
+        t = bench._TRAFFIC[kind]
+        if t["bytes_per_edge"] is not None:  # at least the 3 B of a blocked element
+            assert t["bytes_per_edge"] > 3.0
