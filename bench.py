@@ -61,6 +61,12 @@ def workload(name):
         ens = synth.ba_clique_large()
         desc = dict(workload="ba-1e7-m8-clique20-m40", n_inst=1, n=10_000_000, ba_m=8,
                     target="clique20", m=40, k=20)
+    elif name == "large2m":
+        # the same recipe at n = 2e6 (3.2e7 entries, value array ~0.13 GB, larger
+        # than L2): the small case for ncu captures of the two-phase kernels
+        ens = synth.ba_clique_large(n=2_000_000)
+        desc = dict(workload="ba-2e6-m8-clique20-m40", n_inst=1, n=2_000_000, ba_m=8,
+                    target="clique20", m=40, k=20)
     elif name == "grad":
         ens = synth.er_ensemble_grad()
         desc = dict(workload="er-ensemble-64x1e5-d16-m30-fwd+bwd", n_inst=64, n=100_000, dbar=16,
@@ -340,7 +346,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "small", "grad"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "large2m", "small", "grad"])
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the e2e, plain-FP64 and CPU-baseline legs")
     ap.add_argument("--csr-only", action="store_true",

@@ -456,9 +456,10 @@ class GraphSet:
                                                      _stream_handle(stream)), n)
 
     def close(self):
-        if getattr(self, "h", None):
-            cb_graph_free(self.h)
-            self.h = None
+        h = getattr(self, "h", None)
+        if h:
+            self.h = None  # the handle is gone even if the free reports an error
+            cb_graph_free(h)
 
     def __del__(self):
         try:

@@ -50,28 +50,22 @@ constexpr uint32_t kBLongDeg = 512;                      // longer rows: whole-C
 // for the column-blocked kernel.  Columns are cut into source tiles of kPSrc
 // nodes and rows into bins whose entries fit a shared-memory region.
 // Phase 1 stages a source tile of W_j in shared memory and writes, for every
-// entry, the gathered value into a stream ordered by (source tile, bin);
-// phase 2 copies a bin's chunks of that stream into shared memory and sums
-// each row from there.  Both phases gather from shared memory only.
+// entry, the gathered value into its bin's region of a value array; phase 2
+// copies a bin's region into shared memory and sums each row from there.
+// Both phases gather from shared memory only.
 constexpr uint32_t kPSrcBits = 15;
 constexpr uint32_t kPSrc = 1u << kPSrcBits;  // nodes per source tile (128 KB of W_j)
 constexpr uint32_t kPMaxSrc = 4096;          // source tiles per realisation (n <= 2^27)
-constexpr uint32_t kPRegion = 24576;         // values per bin region (96 KB)
-constexpr uint32_t kPBinRows = 2048;         // most rows per bin
-constexpr uint32_t kPPieceUnits = 32768;     // 4-value units per phase-1 CTA (128K values)
+constexpr uint32_t kPGroup = 8;              // slots per group: one 32-byte sector of values
+constexpr uint32_t kPRegion = 16384;         // slots per bin region (64 KB)
+constexpr uint32_t kPBinRows = 1024;         // most rows per bin
 constexpr int kP1Threads = 1024;             // phase-1 CTA (one per SM: 128 KB tile)
-constexpr int kP2Threads = 512;              // phase-2 CTA (two per SM: 96 KB region)
+constexpr int kP2Threads = 512;              // phase-2 CTA (two per SM: ~115 KB each)
 
 // A bin: consecutive rows [row0, row1) of realisation inst, none heavier
-// than kHeavyDeg, whose entries (with chunk padding) fit kPRegion.
+// than kHeavyDeg, whose entries (with chunk padding) fit kPRegion slots.
 struct PBin {
   uint32_t inst, row0, row1, pad;
-};
-// A phase-1 work item: units [u0, u0 + nu) of the stream of source tile
-// `tile` (local index) of realisation inst.
-struct PPiece {
-  uint64_t u0;
-  uint32_t nu, inst, tile, pad;
 };
 
 // Two-level deterministic reduction plan of one instance for one kernel kind:
@@ -100,8 +94,7 @@ struct InstDesc {
   uint32_t pb, pns;               // two-phase FP32 SpMV? number of source tiles
   uint32_t ptile_base;            // first source tile (handle-wide index)
   uint32_t pbin_base, n_pbin;     // bins
-  uint32_t ppiece_base, n_ppiece; // phase-1 work items
-  uint32_t pad_p;
+  uint32_t pad_p[3];
   uint64_t pmat_base;             // offset of the [bin][pns + 1] chunk tables
   RedPlan pspmv;                  // slots: n_pbin bins, then n_heavy rows
 };
@@ -193,20 +186,27 @@ struct cb_graph {
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
   // two-phase format (FP32 SpMV), for realisations with pb = 1
-  uint32_t total_ptiles = 0, total_pbins = 0, total_ppieces = 0;
+  uint32_t total_ptiles = 0, total_pbins = 0;
   uint32_t pns_max = 0;                  // most source tiles of one realisation
-  uint64_t total_punits = 0;             // 4-value units of the stream
+  uint64_t total_pgroups = 0;            // groups of kPGroup slots (stream and value array)
   cb::PBin *d_pbin = nullptr;
-  cb::PPiece *d_ppiece = nullptr;
-  uint64_t *d_ptbase = nullptr;          // per source tile: first unit of its stream
-  uint32_t *d_ptotal = nullptr;          // per source tile: units of its stream (build)
-  uint32_t *d_ptile_inst = nullptr;      // per source tile: its realisation (build)
-  uint32_t *d_proff = nullptr;           // [bin][s]: unit offset of chunk (s, bin) in the region
-                                         //   ([bin][pns]: units of the region)
-  uint32_t *d_pcstart = nullptr;         // [bin][s]: unit offset of chunk (s, bin) in tile s's stream
-  uint16_t *d_ppos = nullptr;            // per CSR entry of a bin row: its slot in the bin region
+  std::vector<uint64_t> ptbase;          // host copy of d_ptbase
+  uint64_t *d_ptbase = nullptr;          // per source tile: first group of its stream (+ total)
+  uint32_t *d_ptotal = nullptr;          // per source tile: groups of its stream (build)
+  uint32_t *d_ptile_inst = nullptr;      // per source tile: its realisation
+  uint32_t *d_proff = nullptr;           // [bin][s]: group offset of chunk (s, bin) in the
+                                         //   bin region ([bin][pns]: groups of the region)
+  uint32_t *d_pcstart = nullptr;         // [bin][s]: group offset of chunk (s, bin) in
+                                         //   tile s's stream
+  uint32_t *d_prtot = nullptr;           // per bin: groups of its region (build)
+  uint64_t *d_pxbase = nullptr;          // per bin: first group of its region (+ total)
+  uint64_t *d_pxscan = nullptr;          // scratch of the prefix that makes d_pxbase
+  uint16_t *d_ppos = nullptr;            // per CSR entry of a bin row: its slot in the region
   uint16_t *d_psrc = nullptr;            // per stream slot: source node within its tile
-  float *d_pX = nullptr;                 // per stream slot: the value phase 1 writes
+  uint32_t *d_pgdst = nullptr;           // per stream group: its group in the value array
+  float *d_pX = nullptr;                 // value array: bin regions, phase 1 writes them
+  uint32_t *d_pplan = nullptr;           // per (bin, phase-2 thread): merge-path start row | entry << 16
+  uint32_t *d_pplan_end = nullptr;       // per bin: nrows | entries << 16
   // captured ensemble pass (one CUDA graph per m / precision / outputs)
   struct GraphEntry {
     uint32_t m;

@@ -772,13 +772,15 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.skip_blocked = use_blocked ? 1u : 0u;
   a.stall_btile = h->stall_btile;
   a.pbin = h->d_pbin;
-  a.ppiece = h->d_ppiece;
   a.ptbase = h->d_ptbase;
-  a.proff = h->d_proff;
-  a.pcstart = h->d_pcstart;
+  a.ptile_inst = h->d_ptile_inst;
+  a.pxbase = h->d_pxbase;
   a.ppos = h->d_ppos;
   a.psrc = h->d_psrc;
+  a.pgdst = h->d_pgdst;
   a.pX = h->d_pX;
+  a.pplan = h->d_pplan;
+  a.pplan_end = h->d_pplan_end;
   const bool use_pb = sizeof(T) == 4 && h->total_ptiles > 0;
   a.skip_pb = use_pb ? 1u : 0u;
 
@@ -791,8 +793,8 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   const uint32_t n_fin = A1.fin_base + A1.n_fin - fin_off;
   const uint32_t btile_off = A0.btile_base;
   const uint32_t n_btiles = use_blocked ? A1.btile_base + A1.n_btiles - btile_off : 0u;
-  const uint32_t piece_off = A0.ppiece_base;
-  const uint32_t n_pieces = use_pb ? A1.ppiece_base + A1.n_ppiece - piece_off : 0u;
+  const uint32_t ptile_lo = A0.ptile_base, ptile_hi = A1.ptile_base + A1.pns;
+  const uint64_t pg_lo = use_pb ? h->ptbase[ptile_lo] : 0, pg_hi = use_pb ? h->ptbase[ptile_hi] : 0;
   const uint32_t bin_off = A0.pbin_base;
   const uint32_t n_bins = use_pb ? A1.pbin_base + A1.n_pbin - bin_off : 0u;
   bool any_pb = false;  // two-phase realisations in the range (their heavy rows too)
@@ -834,8 +836,8 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
     if (any_csr) launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);
     if (n_btiles) bspmv_kernel<<<n_btiles, kBThreads, kBSmemBytes, s>>>(a, j, btile_off);
     if (any_pb)
-      launch_twophase(a, h->lanes, j, piece_off, n_pieces, chunk_off, n_chunks, bin_off, n_bins,
-                      h->pns_max, s);
+      launch_twophase(a, h->lanes, j, ptile_lo, ptile_hi, pg_lo, pg_hi, chunk_off, n_chunks,
+                      bin_off, n_bins, s);
     prof_end(tok, s);
     tok = prof_begin(CB_K_FINALIZE, s);
     if (n_fin) {

@@ -116,4 +116,42 @@ __device__ __forceinline__ bool arrive_and_reduce(const RedPlan &P, uint32_t slo
   return false;
 }
 
+// arrive_and_reduce run by one full warp (the other warps of the CTA may
+// have exited): the same slots, groups and counters, the group sum over its
+// kGroup slots by the warp's lanes, the realisation sum over the groups by
+// lane-strided partial sums and a shuffle tree.  Returns true (in every
+// lane) in the warp that completes the realisation; *total then holds its
+// sum.
+__device__ __forceinline__ bool warp_arrive_and_reduce(const RedPlan &P, uint32_t slot_local,
+                                                       uint32_t inst, double val, const RedBufs &B,
+                                                       double *total) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t g = slot_local / kGroup;
+  const uint32_t gsize = min((uint32_t)kGroup, P.n_slots - g * kGroup);
+  uint32_t last = 0;
+  if (lane == 0) {
+    B.part[P.slot_base + slot_local] = val;
+    __threadfence();
+    last = atomicAdd(&B.gcnt[P.group_base + g], 1u) == gsize - 1;
+  }
+  if (!__shfl_sync(0xffffffffu, last, 0)) return false;
+  __threadfence();
+  double v = lane < gsize ? __ldcg(&B.part[P.slot_base + g * kGroup + lane]) : 0.0;
+  v = warp_sum_d(v);
+  if (lane == 0) {
+    B.gpart[P.group_base + g] = v;
+    B.gcnt[P.group_base + g] = 0u;
+    __threadfence();
+    last = atomicAdd(&B.icnt[inst], 1u) == P.n_groups - 1;
+  }
+  if (!__shfl_sync(0xffffffffu, last, 0)) return false;
+  __threadfence();
+  double acc = 0.0;
+  for (uint32_t q = lane; q < P.n_groups; q += 32) acc += __ldcg(&B.gpart[P.group_base + q]);
+  acc = warp_sum_d(acc);
+  if (lane == 0) B.icnt[inst] = 0u;
+  *total = acc;
+  return true;
+}
+
 }  // namespace cb

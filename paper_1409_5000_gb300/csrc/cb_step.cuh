@@ -35,11 +35,13 @@ struct LArgs {
   uint32_t stall_btile;   // test hook: this tile's first column block is never copied
   // two-phase format (FP32 path)
   const PBin *pbin;
-  const PPiece *ppiece;
   const uint64_t *ptbase;
-  const uint32_t *proff, *pcstart;
+  const uint32_t *ptile_inst;
+  const uint64_t *pxbase;
   const uint16_t *ppos, *psrc;
+  const uint32_t *pgdst;
   float *pX;
+  const uint32_t *pplan, *pplan_end;
   uint32_t skip_pb;  // the tiled-CSR kernel leaves two-phase realisations alone
 };
 
@@ -75,8 +77,11 @@ __device__ __forceinline__ void finish_alpha(const LArgs &a, uint32_t r, uint32_
 // One chunk of kChunk entries of a heavy row (degree > kHeavyDeg), summed by
 // the whole CTA (any width) with global gathers; the last chunk of the row to
 // finish sums the chunk partials in chunk order, applies the row epilogue and
-// enters the row's alpha term as slot `slot` of `plan`.
-template <typename T>
+// enters the row's alpha term as slot `slot` of `plan` -- by the CTA
+// (arrive_and_reduce) or, with WarpArrive, by its first warp
+// (warp_arrive_and_reduce), whichever the plan's other slots use, so that
+// the realisation's sum takes one order whichever CTA arrives last.
+template <typename T, bool WarpArrive = false>
 __device__ __forceinline__ void heavy_chunk(const LArgs &a, uint32_t j, uint32_t cidx, uint32_t hid,
                                             uint32_t r, const RedPlan &plan, uint32_t slot) {
   __shared__ double s_hred[32];
@@ -116,7 +121,15 @@ __device__ __forceinline__ void heavy_chunk(const LArgs &a, uint32_t j, uint32_t
     dot = (double)row_epilogue<T>((T)tot, H.row, x, xp, out, sj, bp, has_prev);
   }
   double total;
-  if (arrive_and_reduce(plan, slot, r, dot, a.red, &total)) finish_alpha<T>(a, r, j, total);
+  if (WarpArrive) {
+    if (threadIdx.x < 32) {
+      dot = __shfl_sync(0xffffffffu, dot, 0);
+      if (warp_arrive_and_reduce(plan, slot, r, dot, a.red, &total) && threadIdx.x == 0)
+        finish_alpha<T>(a, r, j, total);
+    }
+  } else if (arrive_and_reduce(plan, slot, r, dot, a.red, &total)) {
+    finish_alpha<T>(a, r, j, total);
+  }
 }
 
 // mbarrier and bulk-copy helpers (shared-window addresses).
@@ -159,6 +172,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   }
   return false;
 }
+// Bounded wait as mbar_wait, but each poll may suspend the thread until the
+// phase completes (up to 0.1 ms), so a waiting warp takes almost no issue
+// slots from the warps that compute.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait_sleep(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < kSpinLimit; ++it) {
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
 // One bulk copy global -> shared whose bytes complete on `bar` (16-byte
 // aligned addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -183,11 +218,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Two-phase SpMV step of the realisations in the given ranges (cb_twophase.cu):
-// phase-1 pieces [piece_off, +n_pieces), then phase 2 over heavy-row chunks
-// [chunk_off, +n_chunks) (those of two-phase realisations) and bins
-// [bin_off, +n_bins).
-void launch_twophase(const LArgs &a, int lanes, uint32_t j, uint32_t piece_off, uint32_t n_pieces,
-                     uint32_t chunk_off, uint32_t n_chunks, uint32_t bin_off, uint32_t n_bins,
-                     uint32_t pns_max, cudaStream_t s);
+// phase 1 over the streams of source tiles [tile_lo, tile_hi) (groups
+// [g_lo, g_hi)), then phase 2 over heavy-row chunks [chunk_off, +n_chunks)
+// (those of two-phase realisations) and bins [bin_off, +n_bins).
+void launch_twophase(const LArgs &a, int lanes, uint32_t j, uint32_t tile_lo, uint32_t tile_hi,
+                     uint64_t g_lo, uint64_t g_hi, uint32_t chunk_off, uint32_t n_chunks,
+                     uint32_t bin_off, uint32_t n_bins, cudaStream_t s);
 
 }  // namespace cb
