@@ -67,6 +67,12 @@ def workload(name):
         ens = synth.ba_clique_large(n=2_000_000)
         desc = dict(workload="ba-2e6-m8-clique20-m40", n_inst=1, n=2_000_000, ba_m=8,
                     target="clique20", m=40, k=20)
+    elif name in ("c2er", "c2ba", "c2ws"):
+        kind = name[2:]
+        ens = synth.single_clique_100k(kind)
+        desc = dict(workload=f"{kind}-1e5-clique12-m30", n_inst=1, n=100_000, target="clique12",
+                    m=30, k=12, background={"er": "ER d=10", "ba": "BA m0=m=5",
+                                            "ws": "WS k=10 p=0.1"}[kind])
     elif name == "grad":
         ens = synth.er_ensemble_grad()
         desc = dict(workload="er-ensemble-64x1e5-d16-m30-fwd+bwd", n_inst=64, n=100_000, dbar=16,
@@ -340,13 +346,168 @@ def run_reference(args, ens, desc, rank, world):
     print(json.dumps(line), flush=True)
 
 
+_FAMILIES = ["spmv", "finalize", "tridiag", "combine", "topk", "init", "backward"]
+
+
+def kernel_families(B, step, steps):
+    """Per-family device time (ms) and launch count over `steps` steps, from
+    the library's CUDA events recorded on the launching stream."""
+    import torch
+
+    B.cb_profile_enable(1)
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    kid = {"spmv": B.CB_K_SPMV, "finalize": B.CB_K_FINALIZE, "tridiag": B.CB_K_TRIDIAG,
+           "combine": B.CB_K_COMBINE, "topk": B.CB_K_TOPK, "init": B.CB_K_INIT,
+           "backward": B.CB_K_BACKWARD}
+    fam = {name: B.cb_profile_read(kid[name]) for name in _FAMILIES}
+    B.cb_profile_enable(0)
+    return fam
+
+
+def spmv_path(ens, csr_only=False):
+    """Which FP32 SpMV the workload runs under the automatic path: 'twophase'
+    (a realisation above 2^19 nodes), 'blocked' (otherwise, when the handle
+    has at least one 16384-row blocked tile per SM) or 'csr' (fewer tiles,
+    or CB_CSR_ONLY)."""
+    if csr_only:
+        return "csr"
+    if max(g.n for g in ens.graphs) > 32 * 16384:
+        return "twophase"
+    import torch
+
+    tiles = sum((g.n + 16383) // 16384 for g in ens.graphs)
+    return "blocked" if tiles >= torch.cuda.get_device_properties(0).multi_processor_count else "csr"
+
+
+_KERNEL_NAMES = {"blocked": "bspmv_kernel (column-blocked Lanczos SpMV step)",
+                 "twophase": "pscatter_kernel + pgather_kernel (two-phase Lanczos SpMV step)",
+                 "csr": "spmv_kernel (tiled-CSR Lanczos SpMV step)"}
+
+
+def roofline_for(ens, fam, path):
+    """The roofline object of the SpMV family: algorithmic bytes of one
+    launch over its average event-timed duration, against the measured HBM
+    copy bandwidth."""
+    tot = sum(t for t, _ in fam.values())
+    spmv_ms, spmv_n = fam["spmv"]
+    spmv_avg = spmv_ms / max(spmv_n, 1)
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": _KERNEL_NAMES[path], "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "frac_of_8TBs_nominal": achieved / 8000.0,
+            "traffic": traffic_per_launch(ens, path) if path != "csr" else None,
+            "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
+            "kernel_shares": {k: round(t / tot, 4) for k, (t, _) in fam.items()}}
+
+
+def launches_for(m, path, with_grad=False):
+    """Kernel launches of one step: init (2) + per Lanczos step the SpMV
+    (two kernels on the two-phase path), finalize and beta + tridiag +
+    combine (2) + top-k (init, 12 radix passes, collect, sort)."""
+    per_step = (2 if path == "twophase" else 1) + 2
+    n = 2 + per_step * m + 1 + 2 + 15
+    if with_grad:  # the Lanczos run from the indicator (the basis from 1 is the
+        # forward pass's) + 3 adjoint kernels
+        n += (3 + per_step * m) + 3
+    return n
+
+
+def tuned_choice(B, gs, prec=0):
+    """cb_graph_tune on a handle: the width and path it keeps and the ms of
+    each candidate (widths 1..32 on the tiled-CSR path, then the format path)."""
+    import torch
+
+    lanes, ms = B.cb_graph_tune(gs.h, prec, torch.cuda.current_stream().cuda_stream)
+    names = {B.CB_PATH_AUTO: "auto", B.CB_PATH_FORMATS: "formats", B.CB_PATH_CSR: "csr"}
+    return {"lanes": lanes, "path": names.get(B.cb_graph_path(gs.h), "?"),
+            "ms_per_3_step_run": {"csr_lanes_" + str(w): m for w, m in zip((1, 2, 4, 8, 16, 32), ms)} |
+            {"formats": ms[6]}}
+
+
+def extra_leg(B, name, steps, warmup, dev, csr_only=False, precs=(0,), built=None, tune=False):
+    """One more workload timed the way the main line is (warm-up, CUDA
+    events around `steps` steps of ensemble scores + top-k (+ the edge
+    gradient for 'grad'), then a profiled pass for the SpMV family).
+    `built`: the (ensemble, description) pair when already generated."""
+    import torch
+
+    ens, desc = built if built is not None else workload(name)
+    m, k = desc["m"], desc["k"]
+    with_grad = name == "grad"
+    stream = torch.cuda.current_stream()
+    out = {"config": desc}
+    u0 = time.perf_counter()
+    gs = B.GraphSet(ens.graphs, csr_only=csr_only)
+    out["upload_ms"] = 1e3 * (time.perf_counter() - u0)
+    try:
+        for prec in precs:
+            S = torch.empty(gs.n_max, dtype=torch.float64, device=dev)
+            ls = torch.empty(1, dtype=torch.float64, device=dev)
+            idx = torch.empty(k, dtype=torch.int32, device=dev)
+            val = torch.empty(k, dtype=torch.float64, device=dev)
+            if with_grad:
+                grad = torch.empty(sum(gs.nnz), dtype=torch.float32, device=dev)
+                gls = torch.empty(1, dtype=torch.float64, device=dev)
+
+            def step():
+                B.ensemble_scores(gs, m, prec, out=(S, ls))
+                B.topk(S, k, out=(idx, val))
+                if with_grad:
+                    B.cb_scores_backward(gs.h, m, prec, idx.data_ptr(), k, grad.data_ptr(),
+                                         gls.data_ptr(), stream.cuda_stream)
+
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            units = sum(g.nnz for g in ens.graphs) * m
+            fam = kernel_families(B, step, steps)
+            path = "csr" if (csr_only or prec == 1) else spmv_path(ens)
+            leg = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
+                   "dtype": "f64" if prec == 1 else "f32", "roofline": roofline_for(ens, fam, path),
+                   "gpu_launches_per_step": launches_for(m, path, with_grad)}
+            if prec == 1:  # FP64 bytes: 8-byte vector elements
+                leg["roofline"]["alg_bytes_per_launch"] = alg_bytes_spmv(ens, fp64=True)
+                a = alg_bytes_spmv(ens, fp64=True) / (leg["roofline"]["avg_launch_ms"] * 1e-3) / 1e9
+                leg["roofline"].update(achieved=a, frac=a / leg["roofline"]["peak"],
+                                       frac_of_8TBs_nominal=a / 8000.0)
+            if with_grad:
+                leg["backward_share"] = round(fam["backward"][0] / sum(t for t, _ in fam.values()), 4)
+            leg["scores"] = (float(ls.item()), S.cpu().numpy())
+            out["f64" if prec == 1 else "f32"] = leg
+        if tune:
+            out["tuned"] = tuned_choice(B, gs)
+    finally:
+        gs.close()
+    if "f32" in out and "f64" in out:  # FP32 against FP64, the S10 reading (head and 2-norm)
+        (la, a), (lb, b) = out["f32"]["scores"], out["f64"]["scores"]
+        a = a * math.exp(la - lb)
+        head = b >= 1e-3 * b.max()
+        out["f32_vs_f64"] = {"head_max_rel": float(np.max(np.abs(a - b)[head] / b[head])),
+                             "norm_rel": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+    for p in ("f32", "f64"):
+        if p in out:
+            del out[p]["scores"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "large2m", "small", "grad"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "ensemble40", "large", "large2m", "small", "grad", "c2er", "c2ba", "c2ws"])
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the e2e, plain-FP64 and CPU-baseline legs")
     ap.add_argument("--csr-only", action="store_true",
@@ -424,43 +585,10 @@ def main():
     ms, value = combine_ranks(ms, units, dist, dev)
 
     # per-kernel times (CUDA events around each launch, same stream), separate pass
-    B.cb_profile_enable(1)
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    fam = {}
-    for name, kid in [("spmv", B.CB_K_SPMV), ("finalize", B.CB_K_FINALIZE), ("tridiag", B.CB_K_TRIDIAG),
-                      ("combine", B.CB_K_COMBINE), ("topk", B.CB_K_TOPK), ("init", B.CB_K_INIT),
-                      ("backward", B.CB_K_BACKWARD)]:
-        t, c = B.cb_profile_read(kid)
-        fam[name] = (t, c)
-    B.cb_profile_enable(0)
-    tot = sum(t for t, _ in fam.values())
-    spmv_ms, spmv_n = fam["spmv"]
-    spmv_avg = spmv_ms / max(spmv_n, 1)
-    peak, peak_kind = measured_peak()
-    achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
-    blocked_path = max(g.n for g in ens.graphs) <= 32 * 16384 and not args.csr_only
-    twophase_path = not blocked_path and not args.csr_only
-    if blocked_path:
-        kname = "bspmv_kernel (column-blocked Lanczos SpMV step)"
-    elif twophase_path:
-        kname = "pscatter_kernel + pgather_kernel (two-phase Lanczos SpMV step)"
-    else:
-        kname = "spmv_kernel (tiled-CSR Lanczos SpMV step)"
-    path_kind = "blocked" if blocked_path else ("twophase" if twophase_path else None)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                "frac_of_8TBs_nominal": achieved / 8000.0,
-                "traffic": traffic_per_launch(ens, path_kind) if path_kind else None,
-                "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
-                "kernel_shares": {kname: round(t / tot, 4) for kname, (t, _) in fam.items()}}
-    # init (2) + SpMV, finalize and beta per Lanczos step + tridiag + combine (2)
-    # + top-k (init, 12 radix passes, collect, sort)
-    launches_per_step = 2 + 3 * m + 1 + 2 + 15
-    if with_grad:  # the Lanczos run from the indicator (the basis from 1 is the
-        # forward pass's) + 3 adjoint kernels
-        launches_per_step += (3 + 3 * m) + 3
+    fam = kernel_families(B, step, args.steps)
+    path_kind = spmv_path(ens, args.csr_only)
+    roofline = roofline_for(ens, fam, path_kind)
+    launches_per_step = launches_for(m, path_kind, with_grad)
 
     extra = {}
     if with_grad:
@@ -667,6 +795,27 @@ def main():
         extra["reorth"] = {"ms": q0.elapsed_time(q1),
                            "head_max_rel_vs_plain": float(np.max(np.abs(a - b)[head] / b[head])),
                            "api": "cb_ensemble_scores(CB_FP32 | CB_REORTH), graph replay"}
+
+    if rank == 0 and not args.skip_extra and args.workload == "ensemble":
+        # the other configurations, each timed the same way: the 10M-node BA
+        # graph (two-phase SpMV; the tiled-CSR kernel beside it), the three
+        # 1e5-node single backgrounds in FP32 and FP64, and forward + adjoint
+        legs = {}
+        big = workload("large")
+        legs["large"] = extra_leg(B, "large", 5, 3, dev, built=big, tune=True)
+        csr = extra_leg(B, "large", 3, 2, dev, csr_only=True, built=big)
+        legs["large"]["csr_only"] = {"ms_per_step": csr["f32"]["ms_per_step"],
+                                     "spmv_avg_ms": csr["f32"]["roofline"]["avg_launch_ms"],
+                                     "frac": csr["f32"]["roofline"]["frac"]}
+        del big
+        legs["single_1e5"] = {kind: extra_leg(B, "c2" + kind, 10, 3, dev, precs=(0, 1))
+                              for kind in ("er", "ba", "ws")}
+        legs["grad"] = extra_leg(B, "grad", 5, 3, dev)
+        # the measured choice of SpMV width and path on the default workload
+        # (after its timing; the autotuner's cache stores the same)
+        legs["ensemble_tuned"] = tuned_choice(B, gs)
+        B.cb_graph_set_path(gs.h, B.CB_PATH_AUTO)
+        extra["configs"] = legs
 
     cpu = None
     if rank == 0 and not args.skip_extra and world == 1:

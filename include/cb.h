@@ -68,6 +68,12 @@ extern "C" {
 #define CB_CSR_ONLY 4u    /* no column-blocked format: every FP32 SpMV gathers from the CSR */
 #define CB_TWO_PHASE 8u   /* the two-phase format for every realisation (default: n > 2^19 only) */
 
+/* FP32 SpMV path of a handle (cb_graph_set_path) */
+#define CB_PATH_AUTO 0    /* column-blocked kernel when the handle has >= one blocked tile per SM,
+                             two-phase kernels where built, else tiled CSR */
+#define CB_PATH_FORMATS 1 /* column-blocked and two-phase kernels wherever their format was built */
+#define CB_PATH_CSR 2     /* the tiled-CSR kernel for every realisation */
+
 /* largest Krylov depth accepted by the compute calls */
 #define CB_MAX_M 128
 /* largest k accepted by cb_topk */
@@ -238,21 +244,32 @@ int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int prec, uin
                            void *stream);
 
 /*
- * cb_graph_tune -- pick the group width of the tiled-CSR SpMV (rows of up to
- * 8 * lanes entries share `lanes` lanes of a warp; longer rows go to a warp,
- * a CTA, or several CTAs) for this handle by measurement.  The tiled-CSR
- * kernel serves FP64 mode and FP32 realisations above the column-blocked
- * kernel's size limit (n > 32 * 16384).  Each candidate 1, 2, 4, 8, 16, 32 is
- * timed on a 3-step Lanczos run over all realisations (CUDA events, two
- * repetitions after a warm-up, on a workspace of its own) and the fastest is
- * kept.  Without a realisation on the tiled-CSR kernel at `prec` nothing is
- * timed and the current width is reported.  The upload's default comes from
- * the mean degree.  Results do not depend on the width beyond FP summation
- * order.  Synchronises `stream`.
+ * cb_graph_tune -- pick, by measurement, the SpMV configuration of this
+ * handle at precision `prec`: the group width of the tiled-CSR SpMV (rows of
+ * up to 8 * lanes entries share `lanes` lanes of a warp; longer rows go to a
+ * warp, a CTA, or several CTAs) and, in FP32, the path -- the specialised
+ * formats built at upload (column-blocked kernel for n <= 32 * 16384,
+ * two-phase kernels above) or the tiled-CSR kernel for every realisation.
+ * Candidates: the six widths 1, 2, 4, 8, 16, 32 on the tiled-CSR path, then
+ * (FP32, when the handle has a blocked or two-phase format) the format path.
+ * Each is timed on a 3-step Lanczos run over all realisations (CUDA events,
+ * two repetitions after a warm-up, on a workspace of its own); the fastest
+ * is kept (cb_graph_set_lanes / cb_graph_set_path).  FP64 always runs the
+ * tiled-CSR kernel, so only the width is tuned there.  Results do not depend
+ * on the choice beyond FP summation order.  Synchronises `stream`.
  *   lanes_out  optional host uint32[1]: the width kept.
- *   ms_out     optional host double[6]: ms per run for each candidate (-1 when not timed).
+ *   ms_out     optional host double[7]: ms per run for each width, then for
+ *              the format path (-1 when not timed).
+ *   The path kept is read back with cb_graph_path.
  */
 int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_out, void *stream);
+
+/* Set / read the FP32 SpMV path (CB_PATH_AUTO, CB_PATH_FORMATS, CB_PATH_CSR),
+ * e.g. from a cached tuning result.  A path whose format was not built
+ * (CB_CSR_ONLY, or no realisation in its size range) falls back to the
+ * tiled-CSR kernel.  Setting drops the handle's captured passes. */
+int cb_graph_set_path(cb_graph *h, int path);
+int cb_graph_path(const cb_graph *h);
 
 /* Set / read the tiled-CSR group width (1, 2, 4, 8, 16 or 32), e.g. from a
  * cached tuning result.  Setting drops the handle's captured passes. */

@@ -24,6 +24,7 @@ CB_FP32, CB_FP64 = 0, 1
 CB_REORTH = 0x100  # OR into prec: full reorthogonalisation (two Gram-Schmidt passes)
 CB_VALIDATE, CB_DEVICE_PTRS, CB_CSR_ONLY, CB_TWO_PHASE = 1, 2, 4, 8
 CB_MAX_M, CB_MAX_TOPK, CB_MAX_CYCLES = 128, 4096, 1024
+CB_PATH_AUTO, CB_PATH_FORMATS, CB_PATH_CSR = 0, 1, 2
 
 
 class CBError(RuntimeError):
@@ -89,6 +90,10 @@ def lib():
         L.cb_graph_set_lanes.argtypes = [vp, u32]
         L.cb_graph_lanes.restype = u32
         L.cb_graph_lanes.argtypes = [vp]
+        L.cb_graph_set_path.restype = i32
+        L.cb_graph_set_path.argtypes = [vp, i32]
+        L.cb_graph_path.restype = i32
+        L.cb_graph_path.argtypes = [vp]
         L.cb_subgraph_centrality.restype = i32
         L.cb_subgraph_centrality.argtypes = [vp, u32, u32, i32, u32, vp, vp, vp, vp]
         L.cb_graph_read.restype = i32
@@ -216,9 +221,11 @@ def cb_scores_backward_budget(h, m, prec, topk_idx_ptr, k, grad_ptr, log_scale_p
 
 
 def cb_graph_tune(h, prec, stream):
-    """Returns (lanes kept, [ms per candidate 1, 2, 4, 8, 16, 32; -1 = not timed])."""
+    """Returns (lanes kept, [ms per candidate: widths 1, 2, 4, 8, 16, 32 on the
+    tiled-CSR path, then the format path; -1 = not timed]).  The path kept is
+    cb_graph_path(h)."""
     lanes = ctypes.c_uint32()
-    ms = (ctypes.c_double * 6)()
+    ms = (ctypes.c_double * 7)()
     _check(lib().cb_graph_tune(ctypes.c_void_p(h), prec, ctypes.byref(lanes), ms,
                                ctypes.c_void_p(stream)))
     return int(lanes.value), list(ms)
@@ -230,6 +237,14 @@ def cb_graph_set_lanes(h, lanes):
 
 def cb_graph_lanes(h):
     return int(lib().cb_graph_lanes(ctypes.c_void_p(h)))
+
+
+def cb_graph_set_path(h, path):
+    _check(lib().cb_graph_set_path(ctypes.c_void_p(h), path))
+
+
+def cb_graph_path(h):
+    return int(lib().cb_graph_path(ctypes.c_void_p(h)))
 
 
 def cb_subgraph_centrality(h, inst, m, prec, k, nodes_ptr, sc_ptr, log_scale_ptr, stream):
@@ -378,11 +393,13 @@ def _ptr(a):
 class GraphSet:
     """A handle holding N realisations on the current CUDA device."""
 
-    def __init__(self, graphs, validate=False, stream=None, csr_only=False, two_phase=False):
+    def __init__(self, graphs, validate=False, stream=None, csr_only=False, two_phase=False,
+                 path=None):
         """`graphs`: sequence of objects with .n, .row_ptr, .col (numpy uint32
         arrays, host or pinned torch tensors, or CUDA torch tensors).
         `csr_only`: no column-blocked or two-phase format (CB_CSR_ONLY).
-        `two_phase`: the two-phase format for every realisation (CB_TWO_PHASE)."""
+        `two_phase`: the two-phase format for every realisation (CB_TWO_PHASE).
+        `path`: FP32 SpMV path (CB_PATH_*; default CB_PATH_AUTO)."""
         import torch
 
         graphs = list(graphs)
@@ -410,6 +427,8 @@ class GraphSet:
         self.n_max = max(n)
         self.device = torch.cuda.current_device()
         self.h = cb_graph_upload(n, nnz, rps, cols, flags, _stream_handle(stream))
+        if path is not None:
+            cb_graph_set_path(self.h, path)
 
     @classmethod
     def generate_er(cls, n, dbar, seed, target_edges=None, stream=None):

@@ -438,7 +438,7 @@ CB_API int cb_profile_read(int kernel, double *total_ms, uint64_t *launches) {
   *launches = c;
   return CB_OK;
 }
-CB_API uint32_t cb_version(void) { return (1u << 16) | 0u; }
+CB_API uint32_t cb_version(void) { return (1u << 16) | 1u; }
 
 CB_API uint32_t cb_graph_num_instances(const cb_graph *h) { return h ? h->n_inst : 0; }
 CB_API uint32_t cb_graph_num_nodes(const cb_graph *h, uint32_t r) {
@@ -698,6 +698,11 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   uint64_t nsum = 0;
   for (uint32_t r = 0; r < n_inst; ++r) nsum += n[r];
   h->lanes = pick_lanes((double)edge_off / (double)nsum);
+  {
+    int sm = 0;
+    if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && sm > 0)
+      h->n_sm = (uint32_t)sm;
+  }
 
   // per-tile instance tables
   std::vector<uint32_t> tile_inst(std::max<uint32_t>(tile_off, 1)), fin_inst(std::max<uint32_t>(fin_off, 1));
@@ -783,6 +788,19 @@ CB_API int cb_graph_set_lanes(cb_graph *h, uint32_t lanes) {
 
 CB_API uint32_t cb_graph_lanes(const cb_graph *h) { return h ? (uint32_t)h->lanes : 0u; }
 
+CB_API int cb_graph_set_path(cb_graph *h, int path) {
+  if (!h) return set_error(CB_ERR_ARG, "cb_graph_set_path: null handle");
+  if (path != CB_PATH_AUTO && path != CB_PATH_FORMATS && path != CB_PATH_CSR)
+    return set_error(CB_ERR_ARG, "cb_graph_set_path: unknown path");
+  if (h->path != path) {
+    h->path = path;
+    drop_graphs(h);  // captured passes hold the old kernel choice
+  }
+  return CB_OK;
+}
+
+CB_API int cb_graph_path(const cb_graph *h) { return h ? h->path : -1; }
+
 // Times a short Lanczos run (kProbe steps over all realisations, twice, on a
 // workspace of its own) for every group width of the tiled-CSR SpMV and keeps
 // the fastest.  Realisations on the column-blocked kernel are timed too but
@@ -791,16 +809,12 @@ CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_
   NvtxRange nvtx_range("cb_graph_tune");
   if (!h) return set_error(CB_ERR_ARG, "cb_graph_tune: null handle");
   split_prec(prec);  // reorthogonalisation does not change the SpMV being tuned
-  if (h) h->reorth = false;
+  h->reorth = false;
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_graph_tune: bad precision");
   static const uint32_t kCand[6] = {1, 2, 4, 8, 16, 32};
-  for (int c = 0; ms_out && c < 6; ++c) ms_out[c] = -1.0;
-  bool any_csr = prec == CB_FP64 || h->total_btiles == 0;
-  for (uint32_t r = 0; r < h->n_inst && !any_csr; ++r) any_csr = !h->inst[r].blocked;
-  if (!any_csr) {  // every realisation runs the column-blocked kernel: nothing to choose
-    if (lanes_out) *lanes_out = (uint32_t)h->lanes;
-    return CB_OK;
-  }
+  for (int c = 0; ms_out && c < 7; ++c) ms_out[c] = -1.0;
+  // the format path is a candidate in FP32 when a format was built
+  const bool formats = prec == CB_FP32 && (h->total_btiles > 0 || h->total_ptiles > 0);
   constexpr uint32_t kProbe = 3;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Workspace W;
@@ -809,11 +823,12 @@ CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int keep = h->lanes;
-  int best = keep;
+  const int keep_lanes = h->lanes, keep_path = h->path;
+  int best_lanes = keep_lanes, best_path = keep_path;
   double best_ms = 1e300;
-  for (int c = 0; c < 6 && e == cudaSuccess && rc == CB_OK; ++c) {
-    h->lanes = (int)kCand[c];
+  auto time_one = [&](int lanes, int path, int slot) {
+    h->lanes = lanes;
+    h->path = path;
     rc = lanczos_run(h, W, 0, h->n_inst, kProbe, prec, s);  // warm-up
     if (rc == CB_OK) e = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 2 && rc == CB_OK && e == cudaSuccess; ++rep)
@@ -823,27 +838,30 @@ CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_
     float ms = 0.f;
     if (rc == CB_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (rc == CB_OK && e == cudaSuccess) {
-      if (ms_out) ms_out[c] = ms / 2.0;
+      if (ms_out) ms_out[slot] = ms / 2.0;
       if (ms < best_ms) {
         best_ms = ms;
-        best = (int)kCand[c];
+        best_lanes = lanes;
+        best_path = path;
       }
     }
-  }
-  h->lanes = best;
-  if (best != keep) drop_graphs(h);
+  };
+  for (int c = 0; c < 6 && e == cudaSuccess && rc == CB_OK; ++c) time_one((int)kCand[c], CB_PATH_CSR, c);
+  // the format path, with the best width for any tiled-CSR realisations left
+  if (formats && e == cudaSuccess && rc == CB_OK) time_one(best_lanes, CB_PATH_FORMATS, 6);
+  if (prec == CB_FP64) best_path = keep_path;  // FP64 does not depend on the path
+  h->lanes = best_lanes;
+  h->path = best_path;
+  if (best_lanes != keep_lanes || best_path != keep_path) drop_graphs(h);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   free_workspace(W);
-  if (rc != CB_OK) {
-    h->lanes = keep;
-    return rc;
+  if (rc != CB_OK || e != cudaSuccess) {
+    h->lanes = keep_lanes;
+    h->path = keep_path;
+    return rc != CB_OK ? rc : cuda_error(e, "cb_graph_tune");
   }
-  if (e != cudaSuccess) {
-    h->lanes = keep;
-    return cuda_error(e, "cb_graph_tune");
-  }
-  if (lanes_out) *lanes_out = (uint32_t)best;
+  if (lanes_out) *lanes_out = (uint32_t)best_lanes;
   return CB_OK;
 }
 

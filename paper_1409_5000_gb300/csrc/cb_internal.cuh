@@ -160,6 +160,8 @@ struct cb_graph {
   uint32_t total_tiles = 0, total_heavy = 0, total_chunks = 0, total_fin = 0;
   uint32_t total_slots = 0, total_groups = 0;
   int lanes = 8;  // lanes per row for short rows (1, 2, 4, 8, 16, 32)
+  int path = CB_PATH_AUTO;  // FP32 SpMV path (cb_graph_set_path)
+  uint32_t n_sm = 1;        // SMs of the handle's device
   std::vector<cb::InstDesc> inst;        // host copy
   std::vector<cb::HeavyRow> heavy;       // host copy
   // device arrays

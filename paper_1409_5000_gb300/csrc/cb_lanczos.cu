@@ -768,7 +768,12 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.bslot = h->d_bslot;
   a.blong_ptr = h->d_blong_ptr;
   a.blong_rows = h->d_blong_rows;
-  const bool use_blocked = sizeof(T) == 4 && h->total_btiles > 0;
+  // FP32 path: the column-blocked kernel needs about one 16384-row tile per
+  // SM to fill the GPU (a single 1e5-node graph has 7), so the automatic
+  // choice takes it only from one tile per SM on; the test hook forces it
+  const bool blocked_auto = h->total_btiles >= h->n_sm || h->stall_btile != UINT32_MAX;
+  const bool use_blocked = sizeof(T) == 4 && h->total_btiles > 0 && h->path != CB_PATH_CSR &&
+                           (h->path == CB_PATH_FORMATS || blocked_auto);
   a.skip_blocked = use_blocked ? 1u : 0u;
   a.stall_btile = h->stall_btile;
   a.pbin = h->d_pbin;
@@ -781,7 +786,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.pX = h->d_pX;
   a.pplan = h->d_pplan;
   a.pplan_end = h->d_pplan_end;
-  const bool use_pb = sizeof(T) == 4 && h->total_ptiles > 0;
+  const bool use_pb = sizeof(T) == 4 && h->total_ptiles > 0 && h->path != CB_PATH_CSR;
   a.skip_pb = use_pb ? 1u : 0u;
 
   const InstDesc &A0 = h->inst[r0], &A1 = h->inst[r1 - 1];

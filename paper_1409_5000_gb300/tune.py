@@ -1,8 +1,9 @@
-"""Tiled-CSR group width for a handle: measured once per graph shape, then cached.
+"""SpMV configuration of a handle: measured once per graph shape, then cached.
 
 ``cb_graph_tune`` times every group width (1, 2, 4, 8, 16, 32 lanes per short
-row) of the tiled-CSR SpMV on a short Lanczos run over the handle and keeps
-the fastest.  This module keys the result by the shape of the input -- the
+row) of the tiled-CSR SpMV and, in FP32, the path through the formats built
+at upload (column-blocked or two-phase kernels) on a short Lanczos run over
+the handle, and keeps the fastest width and path.  This module keys the result by the shape of the input -- the
 precision, the number of realisations, the largest n, the mean degree and
 the coefficient of variation of the degrees, each bucketed -- and keeps a
 JSON cache so that later handles of the same shape take the width without
@@ -61,10 +62,10 @@ def load_cache(path=None) -> dict:
         return {}
 
 
-def store(key: str, lanes: int, ms, path=None) -> None:
+def store(key: str, lanes: int, ms, path=None, spmv_path: int = 0) -> None:
     path = path or cache_path()
     data = load_cache(path)
-    data[key] = {"lanes": int(lanes), "ms": [float(x) for x in ms]}
+    data[key] = {"lanes": int(lanes), "path": int(spmv_path), "ms": [float(x) for x in ms]}
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     tmp = path + ".tmp"
     with open(tmp, "w") as f:
@@ -73,10 +74,11 @@ def store(key: str, lanes: int, ms, path=None) -> None:
 
 
 def autotune(gs, prec: int = 0, graphs=None, path=None, stream=None):
-    """Set the handle's group width from the cache, or measure and cache it.
+    """Set the handle's group width and SpMV path from the cache, or measure
+    and cache them.
 
-    Returns (lanes, from_cache).  `graphs` (the host realisations) adds the
-    degree CV to the key."""
+    Returns (lanes, from_cache); the path is cb_graph_path(gs.h).  `graphs`
+    (the host realisations) adds the degree CV to the key."""
     from . import binding as B
 
     cv = degree_cv(graphs) if graphs is not None else None
@@ -84,8 +86,9 @@ def autotune(gs, prec: int = 0, graphs=None, path=None, stream=None):
     hit = load_cache(path).get(key)
     if hit is not None and int(hit.get("lanes", 0)) in (1, 2, 4, 8, 16, 32):
         B.cb_graph_set_lanes(gs.h, int(hit["lanes"]))
+        B.cb_graph_set_path(gs.h, int(hit.get("path", B.CB_PATH_AUTO)))
         return int(hit["lanes"]), True
     lanes, ms = B.cb_graph_tune(gs.h, prec, B._stream_handle(stream))
     if any(x >= 0 for x in ms):  # only measured shapes are worth remembering
-        store(key, lanes, ms, path)
+        store(key, lanes, ms, path, B.cb_graph_path(gs.h))
     return lanes, False

@@ -18,6 +18,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 PREC = {"fp32": 0, "fp64": 1}
+# The FP32 cases here run the specialised formats wherever they are built
+# (CB_PATH_FORMATS): the automatic choice would give these small handles to
+# the tiled-CSR kernel, which the tune and CSR-only cases cover.
+FORMATS = 1
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +35,7 @@ def B():
 
 
 def _single(B, g, m, prec, csr_only=False):
-    with B.GraphSet([g], csr_only=csr_only) as gs:
+    with B.GraphSet([g], csr_only=csr_only, path=None if csr_only else FORMATS) as gs:
         ls, y, rep = B.communicability(gs, 0, m, PREC[prec], report=True)
         torch.cuda.synchronize()
         return float(ls.item()), y.cpu().numpy(), rep
@@ -72,7 +76,7 @@ def test_er_ensemble_small(B, prec):
     m, k = ens.meta["m"], ens.meta["k"]
     gs_o = [(g.n, g.row_ptr, g.col) for g in ens.graphs]
     theta_o, S_o = oc.ensemble_scores(gs_o, m)
-    with B.GraphSet(ens.graphs) as gs:
+    with B.GraphSet(ens.graphs, path=FORMATS) as gs:
         ls, S, rep = B.ensemble_scores(gs, m, PREC[prec], report=True)
         idx, val = B.topk(S, k)
         torch.cuda.synchronize()
@@ -81,7 +85,7 @@ def test_er_ensemble_small(B, prec):
         parity.assert_topk(idx.cpu().numpy(), val.cpu().numpy(), S_o, k, tol)
         assert all(r.m_eff == m and r.status == 0 for r in rep)
     # each realisation alone through the plain per-graph call
-    with B.GraphSet(ens.graphs) as gs:
+    with B.GraphSet(ens.graphs, path=FORMATS) as gs:
         for r in (0, 9):
             ls, y = B.communicability(gs, r, m, PREC[prec])
             th_o, y_o, _ = oc.krylov_expv(*gs_o[r], m)
@@ -96,7 +100,7 @@ def test_uneven_ensemble(B, prec):
     m = ens.meta["m"]
     gs_o = [(g.n, g.row_ptr, g.col) for g in ens.graphs]
     theta_o, S_o = oc.ensemble_scores(gs_o, m)
-    with B.GraphSet(ens.graphs) as gs:
+    with B.GraphSet(ens.graphs, path=FORMATS) as gs:
         ls, S = B.ensemble_scores(gs, m, PREC[prec], n_out=ens.n_max + 37)
         S = S.cpu().numpy()
         assert np.all(S[ens.n_max:] == 0.0)
@@ -118,7 +122,7 @@ def test_single_background_clique(B, kind, prec):
     theta, y, rep = _single(B, g, m, prec)
     parity.assert_scores(theta, y, th_o, y_o, prec)
     tol = parity.TOL_FP64 if prec == "fp64" else parity.TOL_FP32
-    with B.GraphSet([g]) as gs:
+    with B.GraphSet([g], path=FORMATS) as gs:
         ls, yy = B.communicability(gs, 0, m, PREC[prec])
         idx, val = B.topk(yy, 12)
         parity.assert_topk(idx.cpu().numpy(), val.cpu().numpy(), y_o, 12, tol)
@@ -190,7 +194,7 @@ def test_topk_distinct_values(B):
 
 def test_deterministic(B):
     ens = synth.er_ensemble_uneven(n_inst=6, n_lo=5_000, n_hi=60_000, config=304)
-    with B.GraphSet(ens.graphs) as gs:
+    with B.GraphSet(ens.graphs, path=FORMATS) as gs:
         a = B.ensemble_scores(gs, 25, 0)[1].cpu().numpy()
         b = B.ensemble_scores(gs, 25, 0)[1].cpu().numpy()
     assert np.array_equal(a, b)
@@ -202,7 +206,7 @@ def test_graph_replay(B, monkeypatch):
     bit-identical to direct launches, also after the workspace grows (a
     per-realisation call at larger m) and for a second output buffer."""
     ens = synth.er_ensemble_uneven(n_inst=5, n_lo=5_000, n_hi=40_000, config=305)
-    with B.GraphSet(ens.graphs) as gs:
+    with B.GraphSet(ens.graphs, path=FORMATS) as gs:
         monkeypatch.setenv("CB_NO_GRAPH", "1")
         ref = {m: B.ensemble_scores(gs, m, 0) for m in (12, 30)}
         ref = {m: (float(l.item()), S.cpu().numpy()) for m, (l, S) in ref.items()}
@@ -228,11 +232,11 @@ def test_memory_pool_reuse_and_release(B):
     reuses it and computes the same scores; cb_release_cached_memory hands
     it back to the driver."""
     g = synth.er(200_000, 20.0 / 200_000, 5)
-    with B.GraphSet([g]) as gs:
+    with B.GraphSet([g], path=FORMATS) as gs:
         ref = B.ensemble_scores(gs, 10, 0)[1].cpu().numpy()
     torch.cuda.synchronize()
     held, _ = torch.cuda.mem_get_info()
-    with B.GraphSet([g]) as gs:
+    with B.GraphSet([g], path=FORMATS) as gs:
         again = B.ensemble_scores(gs, 10, 0)[1].cpu().numpy()
     assert np.array_equal(ref, again)
     torch.cuda.synchronize()
@@ -251,7 +255,7 @@ def test_max_depth(B):
 
 def test_argument_errors(B):
     g = synth.er(100, 0.05, 1)
-    with B.GraphSet([g]) as gs:
+    with B.GraphSet([g], path=FORMATS) as gs:
         y = torch.empty(100, dtype=torch.float64, device="cuda")
         ls = torch.empty(1, dtype=torch.float64, device="cuda")
         with pytest.raises(B.CBError):  # realisation out of range
@@ -299,7 +303,7 @@ def test_column_block_boundaries(B, n):
     Ensemble of the boundary size with a smaller realisation, FP32 vs oracle."""
     graphs = [synth.er(n, 10.0 / n, 60 + n % 97), synth.er(5_000, 0.002, 61)]
     th_o, S_o = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], 20)
-    with B.GraphSet(graphs) as gs:
+    with B.GraphSet(graphs, path=FORMATS) as gs:
         ls, S = B.ensemble_scores(gs, 20, B.CB_FP32)
         parity.assert_scores(float(ls.item()), S.cpu().numpy(), th_o, S_o, "fp32")
 
@@ -324,13 +328,13 @@ def test_upload_concurrent_with_compute(B):
 
     ens_a = synth.er_ensemble_uneven(n_inst=6, n_lo=20_000, n_hi=120_000, config=311)
     ens_b = synth.er_ensemble_uneven(n_inst=5, n_lo=10_000, n_hi=90_000, config=312)
-    with B.GraphSet(ens_a.graphs) as ga:
+    with B.GraphSet(ens_a.graphs, path=FORMATS) as ga:
         ref_a = B.ensemble_scores(ga, 25, B.CB_FP32)[1].cpu().numpy()
-    with B.GraphSet(ens_b.graphs) as gb:
+    with B.GraphSet(ens_b.graphs, path=FORMATS) as gb:
         ref_b = B.ensemble_scores(gb, 25, B.CB_FP32)[1].cpu().numpy()
     up = torch.cuda.Stream()
-    with B.GraphSet(ens_a.graphs) as ga, ThreadPoolExecutor(1) as ex:
-        fut = ex.submit(lambda: B.GraphSet(ens_b.graphs, stream=up))
+    with B.GraphSet(ens_a.graphs, path=FORMATS) as ga, ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(lambda: B.GraphSet(ens_b.graphs, stream=up, path=FORMATS))
         for _ in range(3):
             got_a = B.ensemble_scores(ga, 25, B.CB_FP32)[1]
         torch.cuda.current_stream().synchronize()

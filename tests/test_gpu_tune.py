@@ -38,15 +38,40 @@ def test_tuner_keeps_fastest(B):
         lanes, ms = B.cb_graph_tune(gs.h, B.CB_FP64, 0)
         assert lanes in (1, 2, 4, 8, 16, 32) and B.cb_graph_lanes(gs.h) == lanes
         timed = [x for x in ms if x >= 0]
-        assert len(timed) == 6
+        assert len(timed) == 6 and ms[6] == -1.0  # FP64: the width only
         assert ms[[1, 2, 4, 8, 16, 32].index(lanes)] == min(timed)
 
 
-def test_tuner_noop_when_all_blocked(B):
-    with B.GraphSet([synth.er(5_000, 0.002, 5)]) as gs:
-        before = B.cb_graph_lanes(gs.h)
+def test_tuner_fp32_picks_width_and_path(B):
+    """FP32 on a handle with the column-blocked format: the six widths on the
+    tiled-CSR path and the format path are all timed, and the fastest is kept."""
+    with B.GraphSet([synth.er(60_000, 10.0 / 60_000, 5)]) as gs:
         lanes, ms = B.cb_graph_tune(gs.h, B.CB_FP32, 0)
-        assert lanes == before and all(x == -1.0 for x in ms)
+        assert len(ms) == 7 and all(x >= 0 for x in ms)
+        path = B.cb_graph_path(gs.h)
+        kept = 6 if path == B.CB_PATH_FORMATS else [1, 2, 4, 8, 16, 32].index(lanes)
+        assert path in (B.CB_PATH_FORMATS, B.CB_PATH_CSR)
+        assert ms[kept] == min(ms)
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("two_phase", [False, True])
+def test_every_path_matches_oracle(B, path, two_phase):
+    """Every FP32 path (automatic, formats, tiled CSR) on the column-blocked
+    and on the two-phase format, against the oracle."""
+    graphs = [synth.ba(40_000, 6, 61), synth.er(25_000, 12.0 / 25_000, 62)]
+    th_o, S_o = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], 20)
+    with B.GraphSet(graphs, two_phase=two_phase) as gs:
+        B.cb_graph_set_path(gs.h, path)
+        assert B.cb_graph_path(gs.h) == path
+        ls, S = B.ensemble_scores(gs, 20, B.CB_FP32)
+        parity.assert_scores(float(ls.item()), S.cpu().numpy(), th_o, S_o, "fp32")
+
+
+def test_path_errors(B):
+    with B.GraphSet([synth.er(100, 0.05, 1)]) as gs:
+        with pytest.raises(B.CBError):
+            B.cb_graph_set_path(gs.h, 3)
 
 
 def test_autotune_cache(B, tmp_path):
