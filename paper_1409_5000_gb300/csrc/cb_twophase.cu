@@ -439,9 +439,9 @@ static_assert((kPRegion * 4) % 16 == 0 && (kP2PosElems * 2) % 16 == 0 && (kP2RpW
 constexpr size_t kP2SmemBytes = (size_t)kPRegion * sizeof(float) + kP2PosElems * sizeof(uint16_t) +
                                 kP2RpWords * sizeof(uint32_t) + 2 * kP2XWords * sizeof(float) +
                                 kPBinRows * sizeof(float);
-// two CTAs per SM: 228 KB per SM, 1 KB reserved per CTA, < 512 B of static
+// two CTAs per SM: 228 KB per SM, 1 KB reserved per CTA, < 640 B of static
 // shared memory (ptxas -v reports it)
-static_assert(2 * (kP2SmemBytes + 1024 + 512) <= 228 * 1024, "two phase-2 CTAs per SM");
+static_assert(2 * (kP2SmemBytes + 1024 + 640) <= 228 * 1024, "two phase-2 CTAs per SM");
 
 __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_t j, uint32_t chunk_off,
                                                                 uint32_t n_chunks, uint32_t bin_off) {
@@ -530,21 +530,25 @@ __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_
     uint32_t re_i = ri < nrows ? s_rp[ri + 1] - e_first : E;  // end of row ri (bin-relative entries)
     float sum = 0.f, head = 0.f;
     bool head_done = false;
+    // one step per iteration, without divergence: every step gathers (entry
+    // k, clamped to the bin; its slot clamped to the region), and a row end
+    // only selects what it keeps, so the lanes of a warp never run two paths
+    const uint32_t elast = E ? E - 1 : 0;
     for (uint32_t d = 0; d < nsteps; ++d) {
-      if (k < re_i) {  // the next entry of row ri
-        sum += reg[pos[k]];
-        ++k;
-      } else {  // row ri ends
-        if (ri == i_first) {
-          head = sum;  // may continue an earlier lane's row: completed below
-          head_done = true;
-        } else {
-          s_sum[ri] = sum;
-        }
-        sum = 0.f;
-        ++ri;
-        re_i = ri < nrows ? s_rp[ri + 1] - e_first : E;
-      }
+      const bool ent = k < re_i;  // the next entry of row ri, or row ri ends
+      // the slot clamped to the region: a bin without entries copies no pos,
+      // and the value of a row-end step is never added
+      const float v = reg[min((uint32_t)pos[min(k, elast)], kPRegion - 1)];
+      const bool first = !ent && ri == i_first;
+      if (!ent && !first) s_sum[ri] = sum;
+      head = first ? sum : head;  // may continue an earlier lane's row: completed below
+      head_done = head_done || first;
+      sum = ent ? sum + v : 0.f;
+      k += ent ? 1u : 0u;
+      const uint32_t rn = ri + 1;
+      const uint32_t ren = rn < nrows ? s_rp[min(rn + 1, nrows)] - e_first : E;
+      re_i = ent ? re_i : ren;
+      ri = ent ? ri : rn;
     }
     // carries: the lane's unfinished row and its partial sum; an inclusive
     // segmented scan (rows are non-decreasing over lanes) in lane order
