@@ -96,10 +96,10 @@ def workload(name):
 _TRAFFIC = {
     "blocked": {"sources_sha256_16": "93b7b04521a0dccc", "bytes_per_edge": (778.72e6 + 21.19e6) / 151654698,
                 "kernel": "bspmv_kernel", "captured_on": "er-ensemble-40"},
-    # one launch of each phase on the 10M-node graph: phase 1 492.29 MB read +
-    # 660.68 MB written, phase 2 1.17 GB read + 34.22 MB written
-    "twophase": {"sources_sha256_16": "130ce3f2d5cc1a3c",
-                 "bytes_per_edge": (492.29e6 + 660.68e6 + 1.17e9 + 34.22e6) / 160000252,
+    # one launch of each phase on the 10M-node graph: phase 1 492.13 MB read +
+    # 664.68 MB written, phase 2 1.17 GB read + 34.36 MB written
+    "twophase": {"sources_sha256_16": "03028aa62d3c3036",
+                 "bytes_per_edge": (492.13e6 + 664.68e6 + 1.17e9 + 34.36e6) / 160000252,
                  "kernel": "pscatter_kernel + pgather_kernel", "captured_on": "ba-1e7"},
 }
 
