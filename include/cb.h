@@ -527,6 +527,28 @@ int cb_score_sum(const double *S, uint32_t n, const uint32_t *nodes, uint32_t k,
 int cb_grad_rescale(float *grad, uint64_t count, const double *log_scale_grad,
                     const double *log_scale_ref, const double *grad_out, void *stream);
 
+/*
+ * Bounds-checked debug build.  A library compiled with -DCB_DEBUG
+ * (libcb_debug.so, built beside libcb.so) checks, on the device, every
+ * column-blocked stream element (column < 16384 or the padding column, row
+ * slot < 16) and stream write position, every CSR column the SpMV kernels
+ * gather through (< n), the two-phase kernels' source offsets (< the tile's
+ * nodes), group places (< the value array) and region slots (< the bin's
+ * region), and the adjoint's edge columns (< n).  A failed check counts a
+ * violation, records the first one as (site << 48) | index (sites 1-7 in the
+ * order above: blocked element, blocked fill, CSR column, two-phase source,
+ * two-phase place, two-phase slot, adjoint column) and skips the access;
+ * nothing traps.
+ * cb_debug_build: 1 in the debug build, 0 in the release build.
+ * cb_debug_violations: the count since the last reset and the first record
+ *   (host outputs; both 0 in the release build); reset != 0 clears them.
+ *   The debug build synchronizes the device first; the release build
+ *   touches no device.  Library service; no counterpart in
+ *   the paper.
+ */
+uint32_t cb_debug_build(void);
+int cb_debug_violations(uint32_t *count, uint64_t *first, int reset);
+
 /* Message describing the last error on this host thread ("" if none). */
 const char *cb_last_error(void);
 

@@ -3,6 +3,10 @@
 * ``_lib/libcb.so``      -- the C-ABI library (CUDA, sm_103a only), built
   with nvcc from ``csrc/*.cu``; one object per translation unit, compiled
   in parallel, then linked with ``-shared``.
+* ``_lib/libcb_debug.so`` -- the same sources with ``-DCB_DEBUG``: every
+  indexed access of the SpMV kernels checked on the device (a violation is
+  counted and skipped, never trapped); loaded instead of libcb.so when the
+  environment sets ``CB_DEBUG=1``.
 * ``_lib/libcbsynth.so`` -- the seeded input generators (plain C, gcc).
 
 Outputs are written to a temporary name and renamed, so that concurrent
@@ -28,8 +32,8 @@ CU_SOURCES = ["cb_api.cu", "cb_lanczos.cu", "cb_tridiag.cu", "cb_combine.cu", "c
               "cb_subgraph.cu", "cb_restart.cu", "cb_twophase.cu"]
 
 
-def cb_lib_path() -> str:
-    return os.path.join(LIBDIR, "libcb.so")
+def cb_lib_path(debug: bool = False) -> str:
+    return os.path.join(LIBDIR, "libcb_debug.so" if debug else "libcb.so")
 
 
 def synth_lib_path() -> str:
@@ -70,9 +74,12 @@ def nvcc_flags(extra=()):
             + ARCH + list(extra))
 
 
-def build_cb(verbose: bool = False, extra_flags=()) -> str:
-    """Compile every CUDA translation unit for sm_103a and link libcb.so."""
+def build_cb(verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Compile every CUDA translation unit for sm_103a and link libcb.so
+    (libcb_debug.so with ``debug``)."""
     os.makedirs(LIBDIR, exist_ok=True)
+    if debug:
+        extra_flags = list(extra_flags) + ["-DCB_DEBUG"]
     objdir = tempfile.mkdtemp(prefix="obj_", dir=LIBDIR)
     try:
         nvcc = _nvcc()
@@ -93,12 +100,13 @@ def build_cb(verbose: bool = False, extra_flags=()) -> str:
         os.close(fd)
         _run([nvcc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH
              + ["-Xcompiler", "-fPIC", "-cudart", "static"])
-        _atomic_move(tmp, cb_lib_path())
+        _atomic_move(tmp, cb_lib_path(debug))
     finally:
         shutil.rmtree(objdir, ignore_errors=True)
-    return cb_lib_path()
+    return cb_lib_path(debug)
 
 
 def build_all(verbose: bool = False) -> None:
     build_synth()
     build_cb(verbose=verbose)
+    build_cb(debug=True)

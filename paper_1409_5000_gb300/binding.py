@@ -42,12 +42,14 @@ _LIB = None
 
 
 def lib():
-    """The loaded libcb (ctypes.CDLL)."""
+    """The loaded libcb (ctypes.CDLL): the bounds-checked libcb_debug.so when
+    the environment sets CB_DEBUG=1, else libcb.so."""
     global _LIB
     if _LIB is None:
-        path = cb_lib_path()
+        path = cb_lib_path(os.environ.get("CB_DEBUG", "0") == "1")
         if not os.path.exists(path):
-            raise RuntimeError(f"libcb.so not built ({path}); run __graft_entry__.build()")
+            raise RuntimeError(f"{os.path.basename(path)} not built ({path}); "
+                               "run __graft_entry__.build()")
         L = ctypes.CDLL(path)
         vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
         pp = ctypes.POINTER(ctypes.c_void_p)
@@ -73,6 +75,10 @@ def lib():
         L.cb_last_error.argtypes = []
         L.cb_version.restype = u32
         L.cb_version.argtypes = []
+        L.cb_debug_build.restype = u32
+        L.cb_debug_build.argtypes = []
+        L.cb_debug_violations.restype = i32
+        L.cb_debug_violations.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u64), i32]
         L.cb_scores_backward.restype = i32
         L.cb_scores_backward.argtypes = [vp, u32, i32, vp, u32, vp, vp, vp]
         L.cb_graph_generate_er.restype = i32
@@ -378,6 +384,19 @@ def cb_last_error():
 
 def cb_version():
     return int(lib().cb_version())
+
+
+def cb_debug_build():
+    """1 if the loaded library is the bounds-checked build, else 0."""
+    return int(lib().cb_debug_build())
+
+
+def cb_debug_violations(reset=False):
+    """(count, first) of the debug build's failed device checks since the
+    last reset; ``first`` = (site << 48) | index of the first one."""
+    c, f = ctypes.c_uint32(), ctypes.c_uint64()
+    _check(lib().cb_debug_violations(ctypes.byref(c), ctypes.byref(f), 1 if reset else 0))
+    return int(c.value), int(f.value)
 
 
 # ---------------------------------------------------------------------------

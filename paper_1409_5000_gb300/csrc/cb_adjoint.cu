@@ -31,6 +31,8 @@
 
 namespace cb {
 
+CB_DEBUG_STATE()
+
 constexpr uint32_t kMaxAdjM = 64;  // adjoint depth limit (shared-memory staging)
 
 void free_backwork(BackWork &B) {
@@ -233,6 +235,10 @@ __global__ void __launch_bounds__(256) bw_mirror_kernel(const InstDesc *inst,
       if (s_rp[mid] <= e) lo = mid; else hi = mid;
     }
     const uint32_t i = row0 + lo, j = __ldg(cl + e);
+    if (!CB_DCHECK(j < I.n, kDbgAdjointCol, j)) {
+      mirror[I.edge_base + e] = e;
+      continue;
+    }
     uint32_t a = rp[j], b = rp[j + 1];  // first position in row j with col >= i
     while (a < b) {
       const uint32_t mid = (a + b) >> 1;
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(256) bw_edge_kernel(const T *P, const T *U, ui
         if (s_up[mid] <= u) lo = mid; else hi = mid;
       }
       e = s_first[lo] + (u - s_up[lo]);
-      if (active) {
+      if (active && CB_DCHECK(__ldg(cl + e) < I.n, kDbgAdjointCol, __ldg(cl + e))) {
         const uint64_t i = I.node_base + row0 + lo;
         const uint64_t j = I.node_base + __ldg(cl + e);
         const T *Pi = P + i * mpad, *Ui = U + i * mpad, *Pj = P + j * mpad, *Uj = U + j * mpad;
@@ -366,6 +372,8 @@ static int backward_t(cb_graph *h, uint32_t m, const uint32_t *idx, uint32_t k, 
   (void)k;
   return cuda_error(cudaGetLastError(), "adjoint launch");
 }
+
+CB_DEBUG_READER(adjoint)
 
 }  // namespace cb
 

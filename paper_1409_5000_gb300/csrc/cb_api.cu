@@ -440,6 +440,32 @@ CB_API int cb_profile_read(int kernel, double *total_ms, uint64_t *launches) {
 }
 CB_API uint32_t cb_version(void) { return (1u << 16) | 1u; }
 
+CB_API uint32_t cb_debug_build(void) {
+#ifdef CB_DEBUG
+  return 1u;
+#else
+  return 0u;
+#endif
+}
+
+CB_API int cb_debug_violations(uint32_t *count, uint64_t *first, int reset) {
+  if (!count || !first) return set_error(CB_ERR_ARG, "cb_debug_violations: null argument");
+  *count = 0;
+  *first = 0;
+  if (cb_debug_build() && cudaDeviceSynchronize() != cudaSuccess)
+    return set_error(CB_ERR_CUDA, "cb_debug_violations: device synchronize");
+  int (*readers[4])(uint32_t *, uint64_t *, bool) = {dbg_read_lanczos, dbg_read_blocked,
+                                                     dbg_read_twophase, dbg_read_adjoint};
+  for (auto rd : readers) {
+    uint32_t c = 0;
+    uint64_t f = 0;
+    if (rd(&c, &f, reset != 0) != 0) return set_error(CB_ERR_CUDA, "cb_debug_violations: read");
+    if (c && !*count) *first = f;
+    *count += c;
+  }
+  return CB_OK;
+}
+
 CB_API uint32_t cb_graph_num_instances(const cb_graph *h) { return h ? h->n_inst : 0; }
 CB_API uint32_t cb_graph_num_nodes(const cb_graph *h, uint32_t r) {
   return (h && r < h->n_inst) ? h->inst[r].n : 0;

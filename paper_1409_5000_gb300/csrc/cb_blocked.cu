@@ -31,6 +31,8 @@
 
 namespace cb {
 
+CB_DEBUG_STATE()
+
 namespace {
 
 constexpr uint32_t kFillThreads = 128;  // lanes of a tile per count / fill CTA
@@ -159,6 +161,13 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
     const uint32_t sv = (uint32_t)SLOT(b, 0) | ((uint32_t)SLOT(b, 1) << 8) |
                         ((uint32_t)SLOT(b, 2) << 16) | ((uint32_t)SLOT(b, 3) << 24);
     const uint64_t st = s_start[b * (kFillThreads / 32) + wl];
+#ifdef CB_DEBUG
+    // the stripe lies inside this (segment, warp) stream: before the next one starts
+    const uint64_t wi = (bseg_base[t] + b) * 32 + blockIdx.y * (kFillThreads / 32) + wl;
+    if (!CB_DCHECK(st + 128ull * stripe + 4 * lane + 3 < bwstart[wi + 1], kDbgBlockedFill,
+                   st + 128ull * stripe + 4 * lane))
+      return;
+#endif
     reinterpret_cast<uint2 *>(bcol + st)[32 * stripe + lane] = cv;
     reinterpret_cast<uint32_t *>(bslot + st)[32 * stripe + lane] = sv;
   };
@@ -366,5 +375,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
   }
   return CB_OK;
 }
+
+CB_DEBUG_READER(blocked)
 
 }  // namespace cb

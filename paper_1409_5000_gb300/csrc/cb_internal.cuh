@@ -239,6 +239,64 @@ struct cb_graph {
 };
 
 namespace cb {
+// ---------------------------------------------------------------------------
+// Bounds checks of the debug build (compiled with -DCB_DEBUG; nothing in the
+// release build).  A failed check counts a violation, records the site and
+// index of the first one, and the caller skips the access: no check traps or
+// faults.  Each translation unit keeps its own record (device variables are
+// per unit without relocatable device code) and exports a reader that
+// cb_debug_violations sums.
+// ---------------------------------------------------------------------------
+enum DebugSite : uint32_t {
+  kDbgBlockedElem = 1,   // column-blocked SpMV: stream element (column, row slot)
+  kDbgBlockedFill = 2,   // column-blocked format: stream write position
+  kDbgCsrCol = 3,        // CSR gathers of the SpMV kernels: column index
+  kDbgTwoPhaseSrc = 4,   // two-phase phase 1: source offset within the tile
+  kDbgTwoPhaseDst = 5,   // two-phase phase 1: group place in the value array
+  kDbgTwoPhasePos = 6,   // two-phase phase 2: slot in the bin region
+  kDbgAdjointCol = 7,    // adjoint mirror and edge kernels: column index
+};
+#ifdef CB_DEBUG
+#define CB_DEBUG_STATE()                                                                    \
+  static __device__ unsigned int g_dbg_count = 0;                                          \
+  static __device__ unsigned long long g_dbg_first = 0;                                    \
+  static __device__ __forceinline__ bool dbg_ok(bool ok, uint32_t site, uint64_t idx) {    \
+    if (!ok && atomicAdd(&g_dbg_count, 1u) == 0)                                            \
+      g_dbg_first = ((unsigned long long)site << 48) | (idx & 0xffffffffffffull);           \
+    return ok;                                                                              \
+  }
+#define CB_DEBUG_READER(name)                                                               \
+  int dbg_read_##name(uint32_t *count, uint64_t *first, bool reset) {                       \
+    unsigned int c = 0;                                                                     \
+    unsigned long long f = 0;                                                               \
+    cudaError_t e = cudaMemcpyFromSymbol(&c, g_dbg_count, sizeof c);                        \
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&f, g_dbg_first, sizeof f);              \
+    if (e == cudaSuccess && reset) {                                                        \
+      const unsigned int z = 0;                                                             \
+      const unsigned long long zf = 0;                                                      \
+      e = cudaMemcpyToSymbol(g_dbg_count, &z, sizeof z);                                    \
+      if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_first, &zf, sizeof zf);            \
+    }                                                                                       \
+    *count = c;                                                                             \
+    *first = f;                                                                             \
+    return e == cudaSuccess ? 0 : 1;                                                        \
+  }
+#define CB_DCHECK(cond, site, idx) dbg_ok((cond), (site), (idx))
+#else
+#define CB_DEBUG_STATE()
+#define CB_DEBUG_READER(name)                                                               \
+  int dbg_read_##name(uint32_t *count, uint64_t *first, bool) {                             \
+    *count = 0;                                                                             \
+    *first = 0;                                                                             \
+    return 0;                                                                               \
+  }
+#define CB_DCHECK(cond, site, idx) true
+#endif
+int dbg_read_lanczos(uint32_t *count, uint64_t *first, bool reset);
+int dbg_read_blocked(uint32_t *count, uint64_t *first, bool reset);
+int dbg_read_twophase(uint32_t *count, uint64_t *first, bool reset);
+int dbg_read_adjoint(uint32_t *count, uint64_t *first, bool reset);
+
 // fn(i) for i in [0, n) on the host, spread over the hardware threads
 void parallel_for(uint32_t n, const std::function<void(uint32_t)> &fn);
 

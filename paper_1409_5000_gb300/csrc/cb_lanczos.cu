@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
 #pragma unroll
       for (uint32_t i = 0; i < kShort / G; ++i) {
         const uint32_t t = lane_g + i * G;
-        if (t < len) s += ld_vec(x + ld_stream(col + e0 + t));
+        if (t < len) {
+          const uint32_t c = ld_stream(col + e0 + t);
+          if (CB_DCHECK(c < I.n, kDbgCsrCol, c)) s += ld_vec(x + c);
+        }
       }
     }
     s = group_sum<G, T>(s);
@@ -233,7 +236,10 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
       const uint32_t e0 = s_rp[lr], e1 = s_rp[lr + 1];
       T s = T(0);
 #pragma unroll 4
-      for (uint32_t e = e0 + lane; e < e1; e += 32) s += ld_vec(x + ld_stream(col + e));
+      for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        const uint32_t c = ld_stream(col + e);
+        if (CB_DCHECK(c < I.n, kDbgCsrCol, c)) s += ld_vec(x + c);
+      }
       s = warp_sum<T>(s);
       if (lane == 0) acc += row_epilogue<T>(s, row0 + lr, x, xp, out, sj, bp, has_prev);
     }
@@ -246,7 +252,10 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
     const uint32_t e0 = s_rp[lr], e1 = s_rp[lr + 1];
     T s = T(0);
 #pragma unroll 4
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kThreads) s += ld_vec(x + ld_stream(col + e));
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+      const uint32_t c = ld_stream(col + e);
+      if (CB_DCHECK(c < I.n, kDbgCsrCol, c)) s += ld_vec(x + c);
+    }
     s = warp_sum<T>(s);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) s_rowsum[warp] = s;
@@ -419,7 +428,10 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
             for (int e = 0; e < 4; ++e) {
               const uint32_t col = ((e < 2 ? cvA[u].x : cvA[u].y) >> (16 * (e & 1))) & 0xffffu;
               const uint32_t k = (svA[u] >> (8 * e)) & 0xffu;
-              mine[k * kBThreads] += cur[col];  // padding: cur[kBPadCol] = 0 into slot 0
+              // padding: cur[kBPadCol] = 0 into slot 0
+              if (CB_DCHECK((col < kBCol || col == kBPadCol) && k < (uint32_t)kBRowsPerThread,
+                            kDbgBlockedElem, col | (k << 16)))
+                mine[k * kBThreads] += cur[col];
             }
           }
       }
@@ -467,7 +479,10 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
     const uint32_t row = row0 + a.blong_rows[q];
     const uint32_t e0 = rp[row], e1 = rp[row + 1];
     float sum = 0.f;
-    for (uint32_t e = e0 + tid; e < e1; e += kBThreads) sum += __ldg(x + ld_stream(col + e));
+    for (uint32_t e = e0 + tid; e < e1; e += kBThreads) {
+      const uint32_t c = ld_stream(col + e);
+      if (CB_DCHECK(c < I.n, kDbgCsrCol, c)) sum += __ldg(x + c);
+    }
     sum = warp_sum<float>(sum);
     if ((tid & 31) == 0) s_rowsum[tid >> 5] = sum;
     __syncthreads();
@@ -786,6 +801,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.pX = h->d_pX;
   a.pplan = h->d_pplan;
   a.pplan_end = h->d_pplan_end;
+  a.pgroups = h->total_pgroups;
   const bool use_pb = sizeof(T) == 4 && h->total_ptiles > 0 && h->path != CB_PATH_CSR;
   a.skip_pb = use_pb ? 1u : 0u;
 
@@ -867,5 +883,7 @@ int lanczos_run(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m,
   return prec == CB_FP64 ? run_t<double>(h, W, r0, r1, m, s, start_idx, k, per_inst, restart_scale)
                          : run_t<float>(h, W, r0, r1, m, s, start_idx, k, per_inst, restart_scale);
 }
+
+CB_DEBUG_READER(lanczos)
 
 }  // namespace cb

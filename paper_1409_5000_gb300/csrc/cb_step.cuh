@@ -8,6 +8,9 @@
 
 namespace cb {
 
+// debug-build violation record of the translation unit (see cb_internal.cuh)
+CB_DEBUG_STATE()
+
 struct LArgs {
   const InstDesc *inst;
   const uint32_t *tile_inst;
@@ -42,6 +45,7 @@ struct LArgs {
   const uint32_t *pgdst;
   float *pX;
   const uint32_t *pplan, *pplan_end;
+  uint64_t pgroups;  // groups of the value array (bounds of the debug build)
   uint32_t skip_pb;  // the tiled-CSR kernel leaves two-phase realisations alone
 };
 
@@ -102,7 +106,10 @@ __device__ __forceinline__ void heavy_chunk(const LArgs &a, uint32_t j, uint32_t
   const uint32_t e0 = rp[H.row] + c * kChunk;
   const uint32_t e1 = min(e0 + kChunk, rp[H.row + 1]);
   T s = T(0);
-  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) s += ld_vec(x + ld_stream(col + e));
+  for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const uint32_t cl = ld_stream(col + e);
+    if (CB_DCHECK(cl < I.n, kDbgCsrCol, cl)) s += ld_vec(x + cl);
+  }
   const double part = block_sum_to_double<T>(s, s_hred);
   if (threadIdx.x == 0) {
     a.cpart[cidx] = part;

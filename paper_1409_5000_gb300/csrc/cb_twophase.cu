@@ -362,6 +362,13 @@ __global__ void __launch_bounds__(kP1Threads, 1) pscatter_kernel(LArgs a, uint32
             if (g >= gb && g < se) {
               const uint2 sv = sb2[2 * gi + half];
               const uint32_t d = dbuf[b * kP1Block + gi];
+#ifdef CB_DEBUG
+              const uint32_t nn = min(kPSrc, I.n - ((t - I.ptile_base) << kPSrcBits));
+              const uint32_t smax = max(max(sv.x & 0xffffu, sv.x >> 16), max(sv.y & 0xffffu, sv.y >> 16));
+              if (!CB_DCHECK(smax < nn, kDbgTwoPhaseSrc, smax) ||
+                  !CB_DCHECK(d < a.pgroups, kDbgTwoPhaseDst, d))
+                continue;
+#endif
               float4 o;
               o.x = vt[sv.x & 0xffffu];
               o.y = vt[sv.x >> 16];
@@ -534,11 +541,19 @@ __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_
     // k, clamped to the bin; its slot clamped to the region), and a row end
     // only selects what it keeps, so the lanes of a warp never run two paths
     const uint32_t elast = E ? E - 1 : 0;
+#ifdef CB_DEBUG
+    const uint32_t rslots = (uint32_t)(a.pxbase[bin + 1] - a.pxbase[bin]) * kPGroup;
+#endif
     for (uint32_t d = 0; d < nsteps; ++d) {
       const bool ent = k < re_i;  // the next entry of row ri, or row ri ends
       // the slot clamped to the region: a bin without entries copies no pos,
       // and the value of a row-end step is never added
       const float v = reg[min((uint32_t)pos[min(k, elast)], kPRegion - 1)];
+#ifdef CB_DEBUG
+      // an entry's slot lies inside the bin's region (the clamp above only
+      // guards the look of a row-end step)
+      CB_DCHECK(!ent || pos[min(k, elast)] < rslots, kDbgTwoPhasePos, pos[min(k, elast)]);
+#endif
       const bool first = !ent && ri == i_first;
       if (!ent && !first) s_sum[ri] = sum;
       head = first ? sum : head;  // may continue an earlier lane's row: completed below
@@ -824,5 +839,7 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
   if (e != cudaSuccess) return fail(CB_ERR_CUDA, "two-phase format: fill");
   return CB_OK;
 }
+
+CB_DEBUG_READER(twophase)
 
 }  // namespace cb

@@ -63,3 +63,22 @@ def test_argument_errors_need_no_device(libcb):
     assert L.cb_communicability(None, 0, 10, 0, None, None, None, None) == binding.CB_ERR_ARG
     assert L.cb_ensemble_scores(None, 10, 0, 5, None, None, None, None) == binding.CB_ERR_ARG
     assert b"null" in L.cb_last_error()
+
+
+def test_debug_library_exports_the_same_symbols():
+    """libcb_debug.so (-DCB_DEBUG) exports every declared function and says
+    which build it is; the release build says 0 and reports no violations
+    without touching a device."""
+    path = _build.cb_lib_path(debug=True)
+    if not os.path.exists(path):
+        _build.build_cb(debug=True)
+    dbg = ctypes.CDLL(path)
+    missing = [n for n in binding.declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+    dbg.cb_debug_build.restype = ctypes.c_uint32
+    assert dbg.cb_debug_build() == 1
+    L = binding.lib()
+    assert binding.cb_debug_build() == (1 if os.environ.get("CB_DEBUG") == "1" else 0)
+    if not binding.cb_debug_build():
+        assert binding.cb_debug_violations() == (0, 0)
+    assert L.cb_debug_violations(None, None, 0) == binding.CB_ERR_ARG
