@@ -60,13 +60,32 @@ constexpr uint32_t kPGroup = 8;              // slots per group: one 32-byte sec
 constexpr uint32_t kPRegion = 16384;         // slots per bin region (64 KB)
 constexpr uint32_t kPBinRows = 1024;         // most rows per bin
 constexpr int kP1Threads = 1024;             // phase-1 CTA (one per SM: 128 KB tile)
-constexpr int kP2Threads = 512;              // phase-2 CTA (two per SM: ~115 KB each)
+constexpr int kP2Threads = 512;              // phase-2 CTA (persistent, one per SM)
+// Phase 2 sums rows in pieces of at most kPPiece entries, 32 pieces (one per
+// lane) at a time; a bin has at most kPMaxPieces pieces, and bins are closed
+// so that their slot array (the pieces' region slots, padded) stays within
+// kPSlotsMax u16 words: 32 kPPiece + the sum over rows of deg + (deg & 1)
+// bounds it.
+constexpr uint32_t kPPiece = 16;
+constexpr uint32_t kPMaxPieces = kPBinRows + kPRegion / kPPiece;
+constexpr uint32_t kPMaxSlices = kPMaxPieces / 32;
+constexpr uint32_t kPSlotsMax = 17408;
 
 // A bin: consecutive rows [row0, row1) of realisation inst, none heavier
 // than kHeavyDeg, whose entries (with chunk padding) fit kPRegion slots.
 struct PBin {
   uint32_t inst, row0, row1, pad;
 };
+
+// What a phase-2 CTA needs to start on a bin: its region (first group of the
+// value array, bytes), its plan (first u16 word, bytes of the part copied to
+// shared memory, word offset of the rows' piece offsets), its rows (vector
+// offset of the first, count), its realisation and its alpha-term slot.
+struct P2Desc {
+  uint64_t xg0, plan, node;
+  uint32_t reg_bytes, head_bytes, pf, inst, nrows, slot;
+};
+static_assert(sizeof(P2Desc) == 48, "P2Desc is three 16-byte units");
 
 // Two-level deterministic reduction plan of one instance for one kernel kind:
 // one partial per slot, slots grouped by kGroup; the last CTA to arrive in a
@@ -207,8 +226,9 @@ struct cb_graph {
   uint16_t *d_psrc = nullptr;            // per stream slot: source node within its tile
   uint32_t *d_pgdst = nullptr;           // per stream group: its group in the value array
   float *d_pX = nullptr;                 // value array: bin regions, phase 1 writes them
-  uint32_t *d_pplan = nullptr;           // per (bin, phase-2 thread): merge-path start row | entry << 16
-  uint32_t *d_pplan_end = nullptr;       // per bin: nrows | entries << 16
+  uint16_t *d_psl = nullptr;             // per bin: the phase-2 plan (sliced rows), u16 words
+  uint64_t *d_psloff = nullptr;          // per bin: first word of its plan (+ total)
+  cb::P2Desc *d_pdesc = nullptr;         // per bin: its phase-2 copies
   // captured ensemble pass (one CUDA graph per m / precision / outputs)
   struct GraphEntry {
     uint32_t m;

@@ -799,8 +799,8 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.psrc = h->d_psrc;
   a.pgdst = h->d_pgdst;
   a.pX = h->d_pX;
-  a.pplan = h->d_pplan;
-  a.pplan_end = h->d_pplan_end;
+  a.psl = h->d_psl;
+  a.pdesc = h->d_pdesc;
   a.pgroups = h->total_pgroups;
   const bool use_pb = sizeof(T) == 4 && h->total_ptiles > 0 && h->path != CB_PATH_CSR;
   a.skip_pb = use_pb ? 1u : 0u;

@@ -44,7 +44,8 @@ struct LArgs {
   const uint16_t *ppos, *psrc;
   const uint32_t *pgdst;
   float *pX;
-  const uint32_t *pplan, *pplan_end;
+  const uint16_t *psl;      // phase-2 plans (sliced rows)
+  const P2Desc *pdesc;      // per bin: its phase-2 copies
   uint64_t pgroups;  // groups of the value array (bounds of the debug build)
   uint32_t skip_pb;  // the tiled-CSR kernel leaves two-phase realisations alone
 };

@@ -20,26 +20,29 @@
 //     in bin order -- a group at a time: 8 u16 source offsets and the
 //     group's place in X in, 8 gathers from shared memory, and two float4
 //     stores that fill one sector of X exactly;
-//   * phase 2 (pgather_kernel) brings its bin's region, the entries' region
-//     slots (pos: u16 per CSR entry) and the row offsets into shared memory
-//     with three bulk copies, then sums each row as the tiled-CSR kernel does
-//     -- G-lane groups for short rows, a warp for medium ones, the CTA for
-//     long ones -- gathering region[pos[e]] instead of W_j[col[e]], and
-//     applies the same row epilogue and alpha partial.  Heavy rows are summed
-//     in chunks from the CSR as in the tiled-CSR kernel.
+//   * phase 2 (pgather_kernel, one bin per CTA) brings its bin's region and
+//     the head of the bin's plan into shared memory with two bulk copies and
+//     sums the rows from there: rows are cut into pieces of at most kPPiece
+//     entries, the pieces sorted by length and dealt 32 at a time (one per
+//     lane) into slices, so a lane walks its piece's region slots with no
+//     branch and no search; each row then adds its pieces in order and takes
+//     the same row epilogue and alpha partial as the other kernels.  Heavy
+//     rows are summed in chunks from the CSR as in the tiled-CSR kernel.
 //
 // DRAM bytes per entry: 2 (source offset) + 0.5 (group place) + 4 (value
-// write) in phase 1, 4 (value read) + 2 (pos) in phase 2, plus the chunk
-// padding, against the 4 of one u32 column index; in exchange every access
-// is sequential or a whole sector, and every random one hits shared memory.
+// write) in phase 1, 4 (value read) + ~2.1 (slot, with the slices' padding)
+// in phase 2, plus the chunk padding, against the 4 of one u32 column index;
+// in exchange every access is sequential or a whole sector, and every random
+// one hits shared memory.
 //
 // The format is built on the device at upload: a count pass per bin (chunk
 // sizes, region offsets), a prefix over the bins' region sizes, a pass per
-// source tile (chunk offsets within the tile's stream), and a fill pass per
-// bin that gives every entry a slot and every stream group its place.  The
-// slot of an entry inside its chunk comes from a shared-memory atomic, so
-// the layout may differ between uploads, but the sums cannot: phase 2 adds
-// each row's entries in CSR order wherever they sit.
+// source tile (chunk offsets within the tile's stream), a fill pass per bin
+// that gives every entry a slot and every stream group its place, and a pass
+// per bin that builds its phase-2 plan.  The slot of an entry inside its
+// chunk comes from a shared-memory atomic, so the layout may differ between
+// uploads, but the sums cannot: phase 2 adds each piece's entries in CSR
+// order and each row's pieces in order, wherever the entries sit.
 #include <algorithm>
 
 #include "cb_internal.cuh"
@@ -200,50 +203,201 @@ __global__ void __launch_bounds__(kBuildThreads) pfill_kernel(const InstDesc *in
   }
 }
 
-// Per bin: the phase-2 work plan.  The bin's rows are split among the
-// kP2Threads / 32 warps by entry count (warp w owns the rows that start in
-// [E w / W, E (w + 1) / W)), and each lane of a warp gets an equal share of
-// the warp's merge path -- the merged sequence of its entries and row ends --
-// whose start (row, entry), both bin-relative, is stored as row | entry << 16;
-// plan_end[bin] = nrows | E << 16 ends the last lane's share.
-__global__ void __launch_bounds__(kP2Threads) pplan_kernel(const InstDesc *inst, const PBin *bins,
-                                                           const uint32_t *row_ptr, uint32_t *plan,
-                                                           uint32_t *plan_end) {
+// Per bin: the phase-2 plan (sliced rows).  Every row of the bin is cut into
+// pieces of at most kPPiece entries, in entry order; the pieces, sorted by
+// length (longest first, ties in piece order), are dealt 32 at a time into
+// slices, one piece per lane; a slice runs as many steps as its first piece
+// is long, rounded up to an even number, and a lane past its piece's end
+// reads the region's zero slot.  The slices go to the warps longest first,
+// each to the warp with the least work so far (ties: the lower warp).  The
+// plan (u16 words, every part a multiple of 8 words) is:
+//   [0, 17)      ws: warp w runs slices [ws[w], ws[w+1]) (warp-major order)
+//   [24, 58)     wo: the slot-array offset of warp w's first slice (u32 as
+//                two words, low first); wo[16] is the array's length
+//   [64, ...)    slen[ns]: steps of each slice
+//                pid[ns][32]: the piece of each lane (0xffff: none)
+//                slots: per slice, [step / 2][lane] pairs of u16 region slots
+//                pf[nrows + 1]: first piece of each row (pf[nrows] = pieces)
+// Phase 2 copies everything before pf to shared memory; this kernel also
+// writes the bin's P2Desc.  The host sized each plan from the same piece
+// lengths (slice_plan_words); a size that disagrees fails the upload.
+__global__ void __launch_bounds__(kP2Threads) pslice_kernel(const InstDesc *inst, const PBin *bins,
+                                                            const uint32_t *row_ptr,
+                                                            const uint16_t *ppos,
+                                                            const uint64_t *psloff,
+                                                            const uint64_t *pxbase, uint16_t *psl,
+                                                            P2Desc *pdesc, uint32_t *bad) {
   constexpr uint32_t W = kP2Threads / 32;
-  __shared__ uint32_t s_rp[kPBinRows + 1];
-  __shared__ uint32_t s_wrow[W + 1];
+  __shared__ uint32_t s_rp[kPBinRows + 1];           // bin-relative row offsets
+  __shared__ uint16_t s_pf[kPBinRows + 2];           // first piece of each row
+  __shared__ uint16_t s_prow[kPMaxPieces];           // row of each piece
+  __shared__ uint8_t s_plen[kPMaxPieces];            // entries of each piece
+  __shared__ uint16_t s_order[kPMaxPieces];          // sorted position -> piece
+  __shared__ uint32_t s_base[kPPiece + 1], s_carry[kPPiece + 1];
+  __shared__ uint32_t s_wc[W][kPPiece + 1];
+  __shared__ uint16_t s_perm[kPMaxSlices], s_ulen[kPMaxSlices];
+  __shared__ uint32_t s_uoff[kPMaxSlices + 1];
+  __shared__ uint32_t s_ws[W + 1], s_wo[W + 1];
+  __shared__ uint32_t s_w[33];
   const PBin B = bins[blockIdx.x];
   const InstDesc I = inst[B.inst];
   const uint32_t *rp = row_ptr + I.rp_base + B.row0;
   const uint32_t nrows = B.row1 - B.row0;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint32_t q = tid; q <= nrows; q += blockDim.x) s_rp[q] = rp[q] - rp[0];
+  if (tid <= kPPiece) s_base[tid] = 0u;
   __syncthreads();
-  const uint32_t E = s_rp[nrows];
-  auto lower_bound = [&](uint32_t t) -> uint32_t {  // least lr with s_rp[lr] >= t
-    uint32_t lo = 0, hi = nrows;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (s_rp[mid] < t) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+  // pieces per row and their prefix (each thread two consecutive rows)
+  auto npieces = [&](uint32_t q) -> uint32_t {
+    return q < nrows ? (s_rp[q + 1] - s_rp[q] + kPPiece - 1) / kPPiece : 0u;
   };
-  if (tid < W) s_wrow[tid] = lower_bound((uint32_t)((uint64_t)E * tid / W));
-  if (tid == 0) s_wrow[W] = nrows;
-  __syncthreads();
-  const uint32_t w = tid >> 5, l = tid & 31;
-  const uint32_t rb = s_wrow[w], re = s_wrow[w + 1];
-  const uint32_t k0 = s_rp[rb], nr = re - rb, ne = s_rp[re] - k0;
-  const uint32_t d0 = (uint32_t)((uint64_t)(nr + ne) * l / 32);
-  // rows of the warp completed before step d0: row i ends at step
-  // (s_rp[rb + i + 1] - k0) + i
-  uint32_t lo = 0, hi = nr;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (s_rp[rb + mid + 1] - k0 + mid < d0) lo = mid + 1; else hi = mid;
+  const uint32_t n0 = npieces(2 * tid), n1 = npieces(2 * tid + 1);
+  uint32_t NP;
+  const uint32_t ex = block_excl_scan(n0 + n1, s_w, &NP);
+  if (NP > kPMaxPieces) {  // cannot happen within the bin limits; fails the upload
+    if (tid == 0) atomicExch(bad, 1u);
+    return;
   }
-  plan[(uint64_t)blockIdx.x * kP2Threads + tid] = (rb + lo) | ((k0 + d0 - lo) << 16);
-  if (tid == 0) plan_end[blockIdx.x] = nrows | (E << 16);
+  if (2 * tid < nrows) s_pf[2 * tid] = (uint16_t)ex;
+  if (2 * tid + 1 < nrows) s_pf[2 * tid + 1] = (uint16_t)(ex + n0);
+  if (tid == 0) s_pf[nrows] = (uint16_t)NP;
+  __syncthreads();
+  // each piece's row and length; the length histogram (key = kPPiece - len)
+  for (uint32_t p = tid; p < NP; p += blockDim.x) {
+    uint32_t lo = 0, hi = nrows;  // s_pf[lo] <= p < s_pf[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_pf[mid] <= p) lo = mid; else hi = mid;
+    }
+    const uint32_t k = p - s_pf[lo], deg = s_rp[lo + 1] - s_rp[lo];
+    const uint32_t len = min(kPPiece, deg - k * kPPiece);
+    s_prow[p] = (uint16_t)lo;
+    s_plen[p] = (uint8_t)len;
+    atomicAdd(&s_base[kPPiece - len], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (uint32_t key = 0; key <= kPPiece; ++key) {
+      const uint32_t c = s_base[key];
+      s_base[key] = run;
+      s_carry[key] = 0u;
+      run += c;
+    }
+  }
+  // stable placement, 512 pieces at a time: the rank of a piece among the
+  // equal keys of its warp, after those of the lower warps and earlier chunks
+  for (uint32_t c0 = 0; c0 < NP; c0 += blockDim.x) {
+    for (uint32_t q = tid; q < W * (kPPiece + 1); q += blockDim.x) (&s_wc[0][0])[q] = 0u;
+    __syncthreads();
+    const uint32_t p = c0 + tid;
+    const uint32_t key = p < NP ? kPPiece - s_plen[p] : kPPiece;  // kPPiece: no piece
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (rank == 0) s_wc[warp][key] = __popc(peers);
+    __syncthreads();
+    if (p < NP) {
+      uint32_t at = s_base[key] + s_carry[key] + rank;
+      for (uint32_t w = 0; w < warp; ++w) at += s_wc[w][key];
+      s_order[at] = (uint16_t)p;
+    }
+    __syncthreads();
+    if (tid < kPPiece) {
+      uint32_t t = 0;
+      for (uint32_t w = 0; w < W; ++w) t += s_wc[w][tid];
+      s_carry[tid] += t;
+    }
+    __syncthreads();
+  }
+  // slices, longest first, to the least-loaded warp; warp-major order
+  const uint32_t ns = (NP + 31) / 32;
+  if (tid == 0) {
+    uint32_t load[W], owner[kPMaxSlices];
+    for (uint32_t w = 0; w < W; ++w) load[w] = 0u;
+    for (uint32_t s = 0; s < ns; ++s) {
+      const uint32_t L = (s_plen[s_order[32 * s]] + 1u) & ~1u;
+      uint32_t best = 0;
+      for (uint32_t w = 1; w < W; ++w)
+        if (load[w] < load[best]) best = w;
+      owner[s] = best;
+      load[best] += L;
+    }
+    uint32_t u = 0, off = 0;
+    for (uint32_t w = 0; w < W; ++w) {
+      s_ws[w] = u;
+      s_wo[w] = off;
+      for (uint32_t s = 0; s < ns; ++s) {
+        if (owner[s] != w) continue;
+        const uint32_t L = (s_plen[s_order[32 * s]] + 1u) & ~1u;
+        s_perm[u] = (uint16_t)s;
+        s_ulen[u] = (uint16_t)L;
+        s_uoff[u] = off;
+        off += 32 * L;
+        ++u;
+      }
+    }
+    s_ws[W] = u;
+    s_wo[W] = off;
+    s_uoff[u] = off;
+  }
+  __syncthreads();
+  const uint32_t ns8 = (ns + 7) & ~7u, nr8 = (nrows + 1 + 7) & ~7u;
+  const uint32_t head = 64 + ns8 + 32 * ns + s_wo[W];  // words copied by phase 2
+  if (head + nr8 != psloff[blockIdx.x + 1] - psloff[blockIdx.x] || s_wo[W] > kPSlotsMax) {
+    if (tid == 0) atomicExch(bad, 1u);
+    return;
+  }
+  uint16_t *out = psl + psloff[blockIdx.x];
+  if (tid == 0) {
+    P2Desc d;
+    d.xg0 = pxbase[blockIdx.x];
+    d.plan = psloff[blockIdx.x];
+    d.node = I.node_base + B.row0;
+    d.reg_bytes = (uint32_t)(pxbase[blockIdx.x + 1] - d.xg0) * kPGroup * 4u;
+    d.head_bytes = head * 2u;
+    d.pf = head;
+    d.inst = B.inst;
+    d.nrows = nrows;
+    d.slot = blockIdx.x - I.pbin_base;
+    pdesc[blockIdx.x] = d;
+  }
+  if (tid < 64) {
+    uint16_t v = 0;
+    if (tid <= W) v = (uint16_t)s_ws[tid];
+    else if (tid >= 24 && tid < 24 + 2 * (W + 1)) {
+      const uint32_t o = s_wo[(tid - 24) >> 1];
+      v = (uint16_t)((tid & 1) ? o >> 16 : o & 0xffffu);
+    }
+    out[tid] = v;
+  }
+  uint16_t *slen = out + 64, *pid = slen + ns8, *slots = pid + 32 * ns, *pf = slots + s_wo[W];
+  for (uint32_t q = tid; q < ns8; q += blockDim.x) slen[q] = q < ns ? s_ulen[q] : (uint16_t)0;
+  for (uint32_t q = tid; q < 32 * ns; q += blockDim.x) {
+    const uint32_t at = 32 * s_perm[q >> 5] + (q & 31);
+    pid[q] = at < NP ? s_order[at] : (uint16_t)0xffffu;
+  }
+  for (uint32_t q = tid; q < nr8; q += blockDim.x) pf[q] = q <= nrows ? s_pf[q] : (uint16_t)0;
+  const uint16_t *pos = ppos + I.edge_base + rp[0];  // pos of the bin's first entry
+  const uint32_t total = s_wo[W];
+  for (uint32_t q = tid; q < total; q += blockDim.x) {
+    uint32_t lo = 0, hi = s_ws[W];  // the slice holding word q: s_uoff[lo] <= q < s_uoff[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_uoff[mid] <= q) lo = mid; else hi = mid;
+    }
+    const uint32_t local = q - s_uoff[lo];
+    const uint32_t l = (local >> 1) & 31u, t = 2 * (local >> 6) + (local & 1u);
+    const uint32_t at = 32 * s_perm[lo] + l;
+    uint16_t v = (uint16_t)kPRegion;  // the zero slot
+    if (at < NP) {
+      const uint32_t p = s_order[at];
+      if (t < s_plen[p]) {
+        const uint32_t row = s_prow[p];
+        v = pos[s_rp[row] + (p - s_pf[row]) * kPPiece + t];
+      }
+    }
+    slots[q] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -415,50 +569,40 @@ __global__ void __launch_bounds__(kP1Threads, 1) pscatter_kernel(LArgs a, uint32
 }
 
 // ---------------------------------------------------------------------------
-// Phase 2: one bin per CTA (blocks after the heavy-row chunk CTAs), two CTAs
-// per SM, so one CTA's copies overlap the other's sums.  The bin's region,
-// its entries' pos, its row offsets and its rows of W_j and W_{j-1} arrive
-// by bulk copies on one mbarrier (one thread polls it while the others
-// sleep in the CTA barrier; nothing waits on the CTA after that).  The rows
-// are split among the warps by entry count (a warp owns the rows that start
-// in its share); within a warp each lane takes an equal share of the merged
-// sequence of the warp's entries and row ends (merge path, Merrill &
-// Garland 2016), sums its entries in order -- the gathers issued four
-// entries ahead -- and writes every row it completes to shared memory; a
-// row that spans lanes is completed by the lane that reaches its end, after
-// a segmented scan of the lanes' carries in lane order.  The warp then
-// applies the row epilogue to its rows (coalesced stores), and the last warp
-// to finish adds the warp partials in warp order and enters the bin's alpha
-// term.  The row searches are warp-cooperative (ballots over 32 candidate
-// rows at a time) instead of per-lane binary searches.
+// Phase 2: one bin per CTA, after the heavy-row chunk CTAs; two CTAs per SM,
+// so one CTA's copies overlap the other's sums.  Everything the CTA needs
+// to start comes from the bin's P2Desc (one load): thread 0 issues the bulk
+// copies of the region and of the head of the plan on one mbarrier, and
+// every thread loads its rows' epilogue operands while they are in flight.
+// Each warp then runs its slices (see pslice_kernel): a lane sums its
+// piece's entries in entry order from the region, gathering at the slots the
+// plan lists, and stores the piece sum; after a CTA barrier each thread adds
+// its rows' pieces in order and applies the row epilogue (coalesced stores),
+// and the last warp to finish adds the warp partials in warp order and
+// enters the bin's alpha term.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kP2Warps = kP2Threads / 32;
-// every part a whole number of 16-byte units (each but the row sums is the
-// destination of a bulk copy): the region, the bin's pos entries (+ 8 for
-// the 16-byte alignment of the copy), its row offsets (+ 4), its rows of
-// W_j and W_{j-1} (+ 4 each) for the epilogue, and the row sums
-constexpr uint32_t kP2PosElems = kPRegion + 8;
-constexpr uint32_t kP2RpWords = kPBinRows + 4;
-constexpr uint32_t kP2XWords = kPBinRows + 4;
-static_assert((kPRegion * 4) % 16 == 0 && (kP2PosElems * 2) % 16 == 0 && (kP2RpWords * 4) % 16 == 0 &&
-                  (kP2XWords * 4) % 16 == 0,
+// the region (+ 4 floats: the zero slot), the copied head of the plan
+// (header, slice lengths, lane pieces, slots) and the piece sums, each a
+// whole number of 16-byte units (the first two are bulk-copy targets)
+constexpr uint32_t kP2RegionWords = kPRegion + 4;
+constexpr uint32_t kP2PlanWords = 64 + 64 + 32 * kPMaxSlices + kPSlotsMax;
+static_assert((kP2RegionWords * 4) % 16 == 0 && (kP2PlanWords * 2) % 16 == 0 &&
+                  (kPMaxPieces * 4) % 16 == 0 && kPMaxSlices <= 64,
               "phase-2 shared-memory buffers must keep 16-byte alignment");
-constexpr size_t kP2SmemBytes = (size_t)kPRegion * sizeof(float) + kP2PosElems * sizeof(uint16_t) +
-                                kP2RpWords * sizeof(uint32_t) + 2 * kP2XWords * sizeof(float) +
-                                kPBinRows * sizeof(float);
+constexpr size_t kP2SmemBytes = (size_t)kP2RegionWords * sizeof(float) + kP2PlanWords * sizeof(uint16_t) +
+                                kPMaxPieces * sizeof(float);
 // two CTAs per SM: 228 KB per SM, 1 KB reserved per CTA, < 640 B of static
 // shared memory (ptxas -v reports it)
 static_assert(2 * (kP2SmemBytes + 1024 + 640) <= 228 * 1024, "two phase-2 CTAs per SM");
+static_assert(kPBinRows <= 2 * kP2Threads, "each phase-2 thread owns at most two rows");
 
 __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_t j, uint32_t chunk_off,
                                                                 uint32_t n_chunks, uint32_t bin_off) {
   extern __shared__ float4 s_dyn4[];
-  float *reg = reinterpret_cast<float *>(s_dyn4);                       // the bin region
-  uint16_t *s_pos = reinterpret_cast<uint16_t *>(reg + kPRegion);       // pos of the bin's entries
-  uint32_t *s_rpw = reinterpret_cast<uint32_t *>(s_pos + kP2PosElems);  // row offsets
-  float *s_xw = reinterpret_cast<float *>(s_rpw + kP2RpWords);          // the bin's rows of W_j
-  float *s_xpw = s_xw + kP2XWords;                                      // and of W_{j-1}
-  float *s_sum = s_xpw + kP2XWords;                                     // row sums
+  float *reg = reinterpret_cast<float *>(s_dyn4);                         // the bin region
+  uint16_t *s_plan = reinterpret_cast<uint16_t *>(reg + kP2RegionWords);  // the plan's head
+  float *s_psum = reinterpret_cast<float *>(s_plan + kP2PlanWords);       // piece sums
   __shared__ double s_wpart[kP2Warps];
   __shared__ __align__(8) uint64_t s_full;
   __shared__ uint32_t s_done;
@@ -475,119 +619,99 @@ __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_
     return;
   }
   const uint32_t bin = bin_off + (blockIdx.x - n_chunks);
-  const PBin B = a.pbin[bin];
-  const uint32_t r = B.inst;
+  const P2Desc D = a.pdesc[bin];
+  const uint32_t r = D.inst, nrows = D.nrows;
   if (j >= a.sc.meff[r]) return;  // realisation stopped (uniform per CTA)
-  const InstDesc &I = a.inst[r];
-  const uint32_t row0 = B.row0, nrows = B.row1 - B.row0;
-  float *Vb = reinterpret_cast<float *>(a.V);
-  const float *x = Vb + (uint64_t)j * a.vs + I.node_base;
-  const bool has_prev = j > 0;
-  const uint32_t *rpg = a.row_ptr + I.rp_base + row0;
-  const uint32_t rp_lead = (uint32_t)((reinterpret_cast<uintptr_t>(rpg) >> 2) & 3u);
-  // node_base is a multiple of 32 elements: the rows' window starts 16-byte
-  // aligned at row0 - (row0 & 3) and ends at most 3 floats past row n - 1
-  const uint32_t x_lead = row0 & 3u;
   if (tid == 0) {
     s_done = 0;
     s_fail = 0;
+    reg[kPRegion] = 0.f;  // the zero slot (outside the copied region)
     mbar_init(&s_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const uint32_t rp_words = (rp_lead + nrows + 1 + 3u) & ~3u;
-    const uint32_t e_first = rpg[0], e_last = rpg[nrows];  // the bin's CSR entry range
-    const uint16_t *pg = a.ppos + I.edge_base + e_first;
-    const uint32_t pos_lead = (uint32_t)((reinterpret_cast<uintptr_t>(pg) >> 1) & 7u);
-    const uint32_t pos_elems = (pos_lead + (e_last - e_first) + 7u) & ~7u;
-    const uint64_t xg0 = a.pxbase[bin], xg1 = a.pxbase[bin + 1];
-    const uint32_t reg_bytes = (uint32_t)(xg1 - xg0) * kPGroup * 4u;
-    const uint32_t xb = ((x_lead + nrows + 3u) & ~3u) * 4u;
-    mbar_expect_tx(&s_full, reg_bytes + pos_elems * 2u + rp_words * 4u + (has_prev ? 2u : 1u) * xb);
-    if (reg_bytes) bulk_g2s(reg, a.pX + xg0 * kPGroup, reg_bytes, &s_full);
-    if (pos_elems) bulk_g2s(s_pos, pg - pos_lead, pos_elems * 2u, &s_full);
-    bulk_g2s(s_rpw, rpg - rp_lead, rp_words * 4u, &s_full);
-    bulk_g2s(s_xw, x + row0 - x_lead, xb, &s_full);
-    if (has_prev) bulk_g2s(s_xpw, x - a.vs + row0 - x_lead, xb, &s_full);
-    if (!mbar_wait(&s_full, 0)) s_fail = 1;
+    if (D.reg_bytes <= kPRegion * 4u && D.head_bytes <= kP2PlanWords * 2u) {
+      mbar_expect_tx(&s_full, D.reg_bytes + D.head_bytes);
+      if (D.reg_bytes) bulk_g2s(reg, a.pX + D.xg0 * kPGroup, D.reg_bytes, &s_full);
+      bulk_g2s(s_plan, a.psl + D.plan, D.head_bytes, &s_full);
+    } else {  // cannot happen with a plan the upload built: no copy, the step fails
+      s_fail = 1;
+      mbar_expect_tx(&s_full, 0);
+    }
   }
+  // this thread's rows' epilogue operands, while the copies are in flight
+  float *Vb = reinterpret_cast<float *>(a.V);
+  const bool has_prev = j > 0;
+  const float *x = Vb + (uint64_t)j * a.vs + D.node;  // W_j of the bin's rows
+  const uint16_t *pf = a.psl + D.plan + D.pf;         // first piece of each row
   const uint32_t ms = a.sc.ms;
   const float sj = (float)a.sc.scale[r * ms + j];
   const float bp = has_prev ? (float)(a.sc.beta[r * ms + j - 1] * a.sc.scale[r * ms + j - 1]) : 0.f;
-  float *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base + row0;
-  // this lane's merge-path start and end, from the plan built at upload
-  const uint32_t *plan = a.pplan + (uint64_t)bin * kP2Threads;
-  const uint32_t ps = __ldg(plan + tid);
-  const uint32_t pe = tid + 1 < (uint32_t)kP2Threads ? __ldg(plan + tid + 1) : a.pplan_end[bin];
-  __syncthreads();  // the bin has landed (or the wait gave up); no CTA barrier below
+  float xv[2] = {0.f, 0.f}, xpv[2] = {0.f, 0.f};
+  uint32_t pb[2] = {0u, 0u}, pe[2] = {0u, 0u};
+#pragma unroll
+  for (uint32_t h = 0; h < 2; ++h) {
+    const uint32_t lr = tid + h * kP2Threads;
+    if (lr < nrows) {
+      xv[h] = x[lr];
+      if (has_prev) xpv[h] = (x - a.vs)[lr];
+      pb[h] = pf[lr];
+      pe[h] = pf[lr + 1];
+    }
+  }
+  if (tid == 0 && (!mbar_wait(&s_full, 0) || s_fail)) s_fail = 1;
+  __syncthreads();  // the bin has landed (or the wait gave up)
   const bool ok = s_fail == 0;
   double wpart = 0.0;
   if (ok) {
-    const uint32_t *s_rp = s_rpw + rp_lead;  // s_rp[q] = row_ptr[row0 + q]
-    const uint32_t e_first = s_rp[0], E = s_rp[nrows] - e_first;
-    const uint16_t *pos =
-        s_pos + ((uint32_t)((reinterpret_cast<uintptr_t>(a.ppos + I.edge_base + e_first) >> 1) & 7u));
-    // this lane's share of the warp's merge path: from (row, entry) =
-    // plan[t] to plan[t + 1] (the last lane's end is the bin's end), both
-    // bin-relative; a warp's first lane starts at its first row's start
-    const uint32_t sp = ps, ep = pe;
-    const uint32_t lr0 = sp & 0xffffu, kk0 = sp >> 16, lr1 = ep & 0xffffu, kk1 = ep >> 16;
-    const uint32_t rb = __shfl_sync(0xffffffffu, lr0, 0), re = __shfl_sync(0xffffffffu, lr1, 31);
-    uint32_t ri = lr0, k = kk0;
-    const uint32_t nsteps = (lr1 + kk1) - (lr0 + kk0);
-    const uint32_t i_first = ri;
-    uint32_t re_i = ri < nrows ? s_rp[ri + 1] - e_first : E;  // end of row ri (bin-relative entries)
-    float sum = 0.f, head = 0.f;
-    bool head_done = false;
-    // one step per iteration, without divergence: every step gathers (entry
-    // k, clamped to the bin; its slot clamped to the region), and a row end
-    // only selects what it keeps, so the lanes of a warp never run two paths
-    const uint32_t elast = E ? E - 1 : 0;
+    const uint32_t ns = s_plan[kP2Warps];
+    const uint32_t u0 = s_plan[warp], u1 = s_plan[warp + 1];
+    uint32_t soff = ((uint32_t)s_plan[24 + 2 * warp] | ((uint32_t)s_plan[25 + 2 * warp] << 16)) >> 1;
+    const uint16_t *slen = s_plan + 64;
+    const uint16_t *pid = slen + ((ns + 7) & ~7u);
+    const uint32_t *slots = reinterpret_cast<const uint32_t *>(pid + 32 * ns);  // slot pairs
 #ifdef CB_DEBUG
-    const uint32_t rslots = (uint32_t)(a.pxbase[bin + 1] - a.pxbase[bin]) * kPGroup;
+    const uint32_t rslots = D.reg_bytes / 4u;
+    const uint32_t npieces = pf[nrows];
 #endif
-    for (uint32_t d = 0; d < nsteps; ++d) {
-      const bool ent = k < re_i;  // the next entry of row ri, or row ri ends
-      // the slot clamped to the region: a bin without entries copies no pos,
-      // and the value of a row-end step is never added
-      const float v = reg[min((uint32_t)pos[min(k, elast)], kPRegion - 1)];
-#ifdef CB_DEBUG
-      // an entry's slot lies inside the bin's region (the clamp above only
-      // guards the look of a row-end step)
-      CB_DCHECK(!ent || pos[min(k, elast)] < rslots, kDbgTwoPhasePos, pos[min(k, elast)]);
-#endif
-      const bool first = !ent && ri == i_first;
-      if (!ent && !first) s_sum[ri] = sum;
-      head = first ? sum : head;  // may continue an earlier lane's row: completed below
-      head_done = head_done || first;
-      sum = ent ? sum + v : 0.f;
-      k += ent ? 1u : 0u;
-      const uint32_t rn = ri + 1;
-      const uint32_t ren = rn < nrows ? s_rp[min(rn + 1, nrows)] - e_first : E;
-      re_i = ent ? re_i : ren;
-      ri = ent ? ri : rn;
-    }
-    // carries: the lane's unfinished row and its partial sum; an inclusive
-    // segmented scan (rows are non-decreasing over lanes) in lane order
-    uint32_t crow = ri;
-    float csum = sum;
+    for (uint32_t u = u0; u < u1; ++u) {
+      const uint32_t L = slen[u];  // steps of the slice: even, at most kPPiece
+      const uint32_t p = pid[32 * u + lane];
+      const uint32_t *sp = slots + soff + lane;
+      float acc = 0.f;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float up = __shfl_up_sync(0xffffffffu, csum, o);
-      const uint32_t urow = __shfl_up_sync(0xffffffffu, crow, o);
-      if (lane >= (uint32_t)o && urow == crow) csum = up + csum;
+      for (uint32_t k = 0; k < kPPiece / 2; ++k) {
+        if (2 * k < L) {  // uniform over the warp
+          const uint32_t q = sp[32 * k];
+#ifdef CB_DEBUG
+          const uint32_t lo = q & 0xffffu, hi = q >> 16;
+          if (!CB_DCHECK((lo < rslots || lo == kPRegion) && (hi < rslots || hi == kPRegion),
+                         kDbgTwoPhasePos, max(lo, hi)))
+            continue;
+#endif
+          acc += reg[q & 0xffffu];
+          acc += reg[q >> 16];
+        }
+      }
+      if (p != 0xffffu && CB_DCHECK(p < npieces, kDbgTwoPhasePos, p)) s_psum[p] = acc;
+      soff += 16 * L;
     }
-    const float prev = __shfl_up_sync(0xffffffffu, csum, 1);
-    const uint32_t prow = __shfl_up_sync(0xffffffffu, crow, 1);
-    if (head_done) s_sum[i_first] = (lane > 0 && prow == i_first) ? prev + head : head;
-    __syncwarp();
-    // the row epilogue of the warp's rows: u = sj * sum - bp * W_{j-1}[row],
-    // stored (coalesced); the alpha partial gathers W_j[row] * u
-    const float *sx = s_xw + x_lead, *sxp = s_xpw + x_lead;  // sx[q] = W_j[row0 + q]
+  }
+  __syncthreads();  // every piece sum is in shared memory
+  if (ok) {
+    // rows: the sum of their pieces in order; u = sj * sum - bp * W_{j-1}[row]
+    // (coalesced store), and the alpha partial W_j[row] * u
+    float *out = Vb + (uint64_t)(j + 1) * a.vs + D.node;
     float acc = 0.f;
-    for (uint32_t lr = rb + lane; lr < re; lr += 32) {
-      float u = sj * s_sum[lr];
-      if (has_prev) u -= bp * sxp[lr];
-      out[lr] = u;
-      acc += sx[lr] * u;
+#pragma unroll
+    for (uint32_t h = 0; h < 2; ++h) {
+      const uint32_t lr = tid + h * kP2Threads;
+      if (lr < nrows) {
+        float sum = 0.f;
+        for (uint32_t p = pb[h]; p < pe[h]; ++p) sum += s_psum[p];
+        float v = sj * sum;
+        if (has_prev) v -= bp * xpv[h];
+        out[lr] = v;
+        acc += xv[h] * v;
+      }
     }
     wpart = (double)warp_sum<float>(acc);
   }
@@ -611,12 +735,12 @@ __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_
   }
   part = __shfl_sync(0xffffffffu, part, 0);
   double total;
-  if (warp_arrive_and_reduce(I.pspmv, bin - I.pbin_base, r, part, a.red, &total) && lane == 0)
+  if (warp_arrive_and_reduce(a.inst[r].pspmv, D.slot, r, part, a.red, &total) && lane == 0)
     finish_alpha<float>(a, r, j, total);
 }
 
 void launch_p2(const LArgs &a, uint32_t j, uint32_t chunk_off, uint32_t n_chunks, uint32_t bin_off,
-               uint32_t n_bins, cudaStream_t s) {
+               uint32_t n_bins, int n_sm, cudaStream_t s) {
   static bool attr = false;  // opt-in to > 48 KB of shared memory
   if (!attr) {
     cudaFuncSetAttribute(pgather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2SmemBytes);
@@ -625,6 +749,7 @@ void launch_p2(const LArgs &a, uint32_t j, uint32_t chunk_off, uint32_t n_chunks
     attr = true;
   }
   pgather_kernel<<<n_chunks + n_bins, kP2Threads, kP2SmemBytes, s>>>(a, j, chunk_off, n_chunks, bin_off);
+  (void)n_sm;
 }
 
 template <typename P>
@@ -654,7 +779,7 @@ void launch_twophase(const LArgs &a, int lanes, uint32_t j, uint32_t tile_lo, ui
     const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)n_sm, want);
     pscatter_kernel<<<grid, kP1Threads, kP1SmemBytes, s>>>(a, j, tile_lo, tile_hi, g_lo, g_hi);
   }
-  if (n_chunks + n_bins) launch_p2(a, j, chunk_off, n_chunks, bin_off, n_bins, s);
+  if (n_chunks + n_bins) launch_p2(a, j, chunk_off, n_chunks, bin_off, n_bins, n_sm, s);
   (void)lanes;  // the merge-path walk of phase 2 needs no group width
 }
 
@@ -672,9 +797,12 @@ void free_twophase(cb_graph *h) {
   dev_free(h->d_psrc);
   dev_free(h->d_pgdst);
   dev_free(h->d_pX);
-  dev_free(h->d_pplan);
-  dev_free(h->d_pplan_end);
-  h->d_pplan = h->d_pplan_end = nullptr;
+  dev_free(h->d_psl);
+  dev_free(h->d_psloff);
+  dev_free(h->d_pdesc);
+  h->d_psl = nullptr;
+  h->d_psloff = nullptr;
+  h->d_pdesc = nullptr;
   h->d_pbin = nullptr;
   h->d_ptbase = h->d_pxbase = h->d_pxscan = nullptr;
   h->d_ptotal = h->d_ptile_inst = h->d_proff = h->d_pcstart = h->d_prtot = h->d_pgdst = nullptr;
@@ -687,6 +815,28 @@ void free_twophase(cb_graph *h) {
   for (cb::InstDesc &I : h->inst) I.pb = 0;
 }
 
+// u16 words of a bin's phase-2 plan, as pslice_kernel lays it out: slice s
+// runs the length (rounded up to even) of the piece at rank 32 s when the
+// pieces are sorted longest first
+uint64_t slice_plan_words(const uint32_t *rp, const PBin &b) {
+  uint32_t hist[kPPiece + 1] = {};
+  uint32_t np = 0;
+  for (uint32_t i = b.row0; i < b.row1; ++i) {
+    const uint32_t d = rp[i + 1] - rp[i];
+    hist[kPPiece] += d / kPPiece;
+    if (d % kPPiece) hist[d % kPPiece] += 1;
+    np += (d + kPPiece - 1) / kPPiece;
+  }
+  const uint32_t ns = (np + 31) / 32;
+  uint64_t steps = 0;
+  uint32_t len = kPPiece, seen = 0;  // seen: pieces longer than len
+  for (uint32_t s = 0; s < ns; ++s) {
+    while (seen + hist[len] <= 32 * s) seen += hist[len--];
+    steps += (len + 1) & ~1u;
+  }
+  return 64 + ((ns + 7) & ~7u) + 32ull * ns + ((b.row1 - b.row0 + 1 + 7) & ~7u) + 32 * steps;
+}
+
 int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
                    const std::vector<CopyGroup> &groups, bool force) {
   NvtxRange nvtx_range("two-phase format");
@@ -694,6 +844,7 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
   const uint32_t N = h->n_inst;
   // which realisations, their bins (host, from row_ptr), in parallel
   std::vector<std::vector<PBin>> rbins(N);
+  std::vector<std::vector<uint64_t>> rsize(N);  // u16 words of each bin's phase-2 plan
   std::vector<uint8_t> want(N, 0);
   for (uint32_t r = 0; r < N; ++r) {
     const InstDesc &I = h->inst[r];
@@ -707,12 +858,14 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
     const uint32_t S = (I.n + kPSrc - 1) / kPSrc;
     // worst-case padding: kPGroup - 1 slots per chunk, one chunk per source tile
     const uint32_t cap = kPRegion - (kPGroup - 1) * S;
-    uint32_t row0 = 0, acc = 0;
+    // the phase-2 slot array: at most 32 kPPiece + sum(deg + (deg & 1)) words
+    const uint32_t scap = kPSlotsMax - 32 * kPPiece;
+    uint32_t row0 = 0, acc = 0, sacc = 0;
     bool open = false;
     for (uint32_t i = 0; i < I.n; ++i) {
       const uint32_t deg = rp[i + 1] - rp[i];
       const bool heavy = deg > kHeavyDeg;
-      if (open && (heavy || i - row0 == kPBinRows || acc + deg > cap)) {
+      if (open && (heavy || i - row0 == kPBinRows || acc + deg > cap || sacc + deg + (deg & 1u) > scap)) {
         rbins[r].push_back(PBin{r, row0, i, 0});
         open = false;
       }
@@ -720,16 +873,21 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
       if (!open) {
         row0 = i;
         acc = 0;
+        sacc = 0;
         open = true;
       }
       acc += deg;
+      sacc += deg + (deg & 1u);
     }
     if (open) rbins[r].push_back(PBin{r, row0, I.n, 0});
+    for (const PBin &b : rbins[r]) rsize[r].push_back(slice_plan_words(rp, b));
   });
   uint32_t tiles = 0, nbins = 0, slot = 0, group = 0, pns_max = 0;
   uint64_t mat = 0;
   std::vector<PBin> bins;
   std::vector<uint32_t> tile_inst;
+  std::vector<uint64_t> psloff;
+  uint64_t plan_words = 0;
   for (uint32_t r = 0; r < N; ++r) {
     InstDesc &I = h->inst[r];
     I.pb = want[r];
@@ -749,6 +907,10 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
     group += I.pspmv.n_groups;
     pns_max = std::max(pns_max, I.pns);
     bins.insert(bins.end(), rbins[r].begin(), rbins[r].end());
+    for (uint64_t w : rsize[r]) {
+      psloff.push_back(plan_words);
+      plan_words += w;
+    }
     tile_inst.insert(tile_inst.end(), I.pns, r);
   }
   if (tiles == 0) return CB_OK;
@@ -778,13 +940,16 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
   chk(dalloc(&h->d_pxbase, (uint64_t)nbins + 1));
   chk(dalloc(&h->d_pxscan, (uint64_t)nbins / 4096 + 2));
   chk(dalloc(&h->d_ppos, h->total_nnz + 8));
-  chk(dalloc(&h->d_pplan, (uint64_t)std::max<uint32_t>(nbins, 1) * kP2Threads));
-  chk(dalloc(&h->d_pplan_end, std::max<uint32_t>(nbins, 1)));
+  chk(dalloc(&h->d_psloff, (uint64_t)nbins + 1));
+  chk(dalloc(&h->d_pdesc, std::max<uint32_t>(nbins, 1)));
+  chk(dalloc(&h->d_psl, plan_words + 8));
   if (e != cudaSuccess) return fail(CB_ERR_OOM, "two-phase format: allocate");
   uint32_t *d_bad = h->d_ptotal + tiles;
   // every copy of the upload has landed on `s` before the format reads it
   for (const CopyGroup &g : groups) chk(cudaStreamWaitEvent(s, g.ev, 0));
+  psloff.push_back(plan_words);
   if (nbins) chk(stage_h2d(h->d_pbin, bins.data(), nbins * sizeof(PBin), s));
+  chk(stage_h2d(h->d_psloff, psloff.data(), (nbins + 1) * 8, s));
   chk(stage_h2d(h->d_ptile_inst, tile_inst.data(), tiles * 4, s));
   chk(stage_h2d(h->d_inst, h->inst.data(), N * sizeof(InstDesc), s));
   chk(cudaMemsetAsync(d_bad, 0, 4, s));
@@ -796,8 +961,6 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
     pcount_kernel<<<nbins, kBuildThreads, shm_count, s>>>(h->d_inst, h->d_pbin, h->row_ptr, h->col,
                                                           h->d_proff, h->d_prtot, d_bad);
     chk(exclusive_scan(h->d_prtot, nbins, h->d_pxbase, h->d_pxscan, s));
-    pplan_kernel<<<nbins, kP2Threads, 0, s>>>(h->d_inst, h->d_pbin, h->row_ptr, h->d_pplan,
-                                              h->d_pplan_end);
   }
   if (e == cudaSuccess)
     pcolscan_kernel<<<tiles, kBuildThreads, 0, s>>>(h->d_inst, h->d_ptile_inst, h->d_proff,
@@ -834,9 +997,21 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
                                                         h->d_proff, h->d_pcstart, h->d_ptbase,
                                                         h->d_pxbase, h->d_ppos, h->d_psrc,
                                                         h->d_pgdst);
+  // the phase-2 plans, from the slots the fill gave the entries
+  chk(cudaMemsetAsync(d_bad, 0, 4, s));
+  if (e == cudaSuccess && nbins)
+    pslice_kernel<<<nbins, kP2Threads, 0, s>>>(h->d_inst, h->d_pbin, h->row_ptr, h->d_ppos,
+                                               h->d_psloff, h->d_pxbase, h->d_psl, h->d_pdesc,
+                                               d_bad);
   chk(cudaGetLastError());
+  uint32_t bad = 0;
+  chk(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s));
   chk(cudaStreamSynchronize(s));
   if (e != cudaSuccess) return fail(CB_ERR_CUDA, "two-phase format: fill");
+  if (bad) {  // internal consistency: the host and device plan sizes disagree
+    free_twophase(h);
+    return set_error(CB_ERR_STATE, "two-phase format: phase-2 plan size");
+  }
   return CB_OK;
 }
 
