@@ -430,6 +430,20 @@ def tuned_choice(B, gs, prec=0):
             {"formats": ms[6]}}
 
 
+def check_run(B, gs, m, prec):
+    """One more call, outside the timed region, with the per-realisation
+    report: a realisation that failed (a device wait that gave up, a
+    non-finite recurrence scalar) makes the whole measurement invalid."""
+    import torch
+
+    ls, _, rep = B.ensemble_scores(gs, m, prec, report=True)
+    torch.cuda.synchronize()
+    bad = [(q, r.status) for q, r in enumerate(rep) if r.status != 0]
+    if bad or not math.isfinite(float(ls.item())):
+        raise RuntimeError(f"bench: realisations failed (index, status): {bad[:8]}; "
+                           f"log scale {float(ls.item())}")
+
+
 def extra_leg(B, name, steps, warmup, dev, csr_only=False, precs=(0,), built=None, tune=False):
     """One more workload timed the way the main line is (warm-up, CUDA
     events around `steps` steps of ensemble scores + top-k (+ the edge
@@ -473,6 +487,7 @@ def extra_leg(B, name, steps, warmup, dev, csr_only=False, precs=(0,), built=Non
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
+            check_run(B, gs, m, prec)
             units = sum(g.nnz for g in ens.graphs) * m
             fam = kernel_families(B, step, steps)
             path = "csr" if (csr_only or prec == 1) else spmv_path(ens)
@@ -585,6 +600,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
+    check_run(B, gs, m, B.CB_FP32)
     ms, value = combine_ranks(ms, units, dist, dev)
 
     # per-kernel times (CUDA events around each launch, same stream), separate pass

@@ -118,8 +118,10 @@ typedef struct {
  *              CB_TWO_PHASE: build the two-phase format (FP32 SpMV in two
  *              passes over a stream of edge values, both gathering from
  *              shared memory) for every realisation instead of only those
- *              with n > 32 * 16384; about 8 B per entry on the device.
- *              Realisations with n > 2^27 run the tiled-CSR SpMV.
+ *              with n > 32 * 16384; about 11 B per entry on the device.
+ *              Realisations with n > 1170 * 32768 (about 3.8e7) run the
+ *              tiled-CSR SpMV: a bin must hold any row of up to 8192
+ *              entries beside the worst-case padding of its chunks.
  *              CB_CSR_ONLY with CB_TWO_PHASE, or other bits: CB_ERR_ARG.
  *              A column index >= n fails the two-phase build (CB_ERR_ARG).
  *   stream     used for the copies.  The call synchronises `stream` before

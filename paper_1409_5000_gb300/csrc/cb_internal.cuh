@@ -60,7 +60,7 @@ constexpr uint32_t kPGroup = 8;              // slots per group: one 32-byte sec
 constexpr uint32_t kPRegion = 16384;         // slots per bin region (64 KB)
 constexpr uint32_t kPBinRows = 1024;         // most rows per bin
 constexpr int kP1Threads = 1024;             // phase-1 CTA (one per SM: 128 KB tile)
-constexpr int kP2Threads = 512;              // phase-2 CTA (persistent, one per SM)
+constexpr int kP2Threads = 512;              // phase-2 CTA (two per SM: ~111 KB each)
 // Phase 2 sums rows in pieces of at most kPPiece entries, 32 pieces (one per
 // lane) at a time; a bin has at most kPMaxPieces pieces, and bins are closed
 // so that their slot array (the pieces' region slots, padded) stays within

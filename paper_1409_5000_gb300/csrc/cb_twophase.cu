@@ -598,7 +598,8 @@ static_assert(2 * (kP2SmemBytes + 1024 + 640) <= 228 * 1024, "two phase-2 CTAs p
 static_assert(kPBinRows <= 2 * kP2Threads, "each phase-2 thread owns at most two rows");
 
 __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_t j, uint32_t chunk_off,
-                                                                uint32_t n_chunks, uint32_t bin_off) {
+                                                                uint32_t n_chunks, uint32_t bin_off,
+                                                                uint32_t n_bins, uint32_t ahead) {
   extern __shared__ float4 s_dyn4[];
   float *reg = reinterpret_cast<float *>(s_dyn4);                         // the bin region
   uint16_t *s_plan = reinterpret_cast<uint16_t *>(reg + kP2RegionWords);  // the plan's head
@@ -635,6 +636,16 @@ __global__ void __launch_bounds__(kP2Threads, 2) pgather_kernel(LArgs a, uint32_
     } else {  // cannot happen with a plan the upload built: no copy, the step fails
       s_fail = 1;
       mbar_expect_tx(&s_full, 0);
+    }
+    // the bin `ahead` places on (about one wave of CTAs later) into L2, so
+    // that DRAM keeps streaming while the resident CTAs sum
+    const uint32_t nb = bin + ahead;
+    if (nb < bin_off + n_bins) {
+      const P2Desc N = a.pdesc[nb];
+      if (N.reg_bytes <= kPRegion * 4u && N.head_bytes <= kP2PlanWords * 2u) {
+        if (N.reg_bytes) l2_prefetch(a.pX + N.xg0 * kPGroup, N.reg_bytes);
+        l2_prefetch(a.psl + N.plan, N.head_bytes);
+      }
     }
   }
   // this thread's rows' epilogue operands, while the copies are in flight
@@ -748,8 +759,9 @@ void launch_p2(const LArgs &a, uint32_t j, uint32_t chunk_off, uint32_t n_chunks
                          cudaSharedmemCarveoutMaxShared);
     attr = true;
   }
-  pgather_kernel<<<n_chunks + n_bins, kP2Threads, kP2SmemBytes, s>>>(a, j, chunk_off, n_chunks, bin_off);
-  (void)n_sm;
+  // prefetch distance: the CTAs resident at once (two per SM)
+  pgather_kernel<<<n_chunks + n_bins, kP2Threads, kP2SmemBytes, s>>>(a, j, chunk_off, n_chunks, bin_off,
+                                                                     n_bins, 2u * (uint32_t)n_sm);
 }
 
 template <typename P>
@@ -849,7 +861,12 @@ int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cu
   for (uint32_t r = 0; r < N; ++r) {
     const InstDesc &I = h->inst[r];
     const bool big = I.n > kBMaxBlocks * kBCol;
-    want[r] = (force || big) && I.n <= kPSrc * kPMaxSrc && !I.blocked ? 1 : 0;
+    // every row of at most kHeavyDeg entries must fit a bin with the
+    // worst-case chunk padding: (kPGroup - 1) S + kHeavyDeg <= kPRegion, so
+    // n <= 1170 tiles (about 3.8e7 nodes); larger ones keep the tiled CSR
+    const uint32_t S = (I.n + kPSrc - 1) / kPSrc;
+    const bool fits = I.n <= kPSrc * kPMaxSrc && (kPGroup - 1) * S + kHeavyDeg <= kPRegion;
+    want[r] = (force || big) && fits && !I.blocked ? 1 : 0;
   }
   parallel_for(N, [&](uint32_t r) {
     if (!want[r]) return;
