@@ -5,25 +5,30 @@
 // The format lets the SpMV stage a block of kBCol entries of v_j in shared
 // memory and gather only from there:
 //   * rows are tiled by kBTileRows; thread i of a tile owns rows
-//     i + kBThreads * k, k = 0..kBRowsPerThread-1 (row slot k), so even a
-//     partly filled tile spreads its rows over all warps;
+//     i + kBThreads * k, k = 0..kBRowsPerThread-1 (row slot k), and its row
+//     sums sit in shared memory at k * kBThreads + i, so the sums of one
+//     warp's rows fall in bank (i mod 32) of the owning lane;
 //   * a tile's edges are grouped by column block b = col >> kBColBits into
-//     one segment per (tile, b); thread i's edges of a segment (its rows in
-//     order, each row's columns in order) form its stream;
-//   * the 32 streams of a warp are interleaved in stripes of 4: element q of
-//     lane l sits at start(segment, warp) + 128 (q / 4) + 4 l + q % 4, and
-//     every stream is padded to the warp's longest, rounded up to a multiple
-//     of 4 (len(segment, warp)).  A lane reads 4 columns (8 bytes) and 4
-//     slots (4 bytes) per stripe; a warp's stripe is 384 contiguous bytes, so
-//     the loads are coalesced and need no per-element range checks;
-//   * each element stores the local column (u16, col & (kBCol-1)) and the row
-//     slot of the owning lane (u8, 0..kBRowsPerThread-1); padding elements
-//     carry column kBPadCol (a zero word after the staged block) and slot 0,
-//     so they add +0.
+//     one segment per (tile, b), and within it per warp: the elements of the
+//     warp's 512 rows, taken lane by lane (each lane's rows in slot order,
+//     each row's columns in order), are dealt round-robin over the T steps
+//     of the warp's stream: element j goes to step j mod T, lane j / T.
+//     With T >= the elements / 32, >= half the elements of any one lane and
+//     >= the elements of any one row, a step holds at most 32 elements, never
+//     two of one row (no two lanes add into the same sum at once) and at
+//     most two of one lane's rows (at most two-way bank conflicts on the
+//     sums), while the padding stays a few percent instead of the spread
+//     between the warp's fullest and emptiest lane;
+//   * an element is one u32: the local column (col & (kBCol-1)) and, above
+//     it, the offset of its row sum from the warp's base (k * kBThreads +
+//     owner lane); steps are stored in pairs, [step / 2][lane][2], so a lane
+//     reads two elements per 8-byte load and a warp 256 contiguous bytes;
+//   * padding elements read column 0 into the executing lane's spare sum
+//     (slot kBRowsPerThread), which the epilogue never reads.
 // Rows with more than kBLongDeg entries stay out of the streams; the SpMV
 // sums them from the CSR with whole-CTA global gathers.  Built on the device
 // from the CSR (one count pass per group of realisations as its copies land,
-// a device prefix over segment lengths, one fill pass), once per upload.
+// a device prefix over the step counts, one fill pass), once per upload.
 #include <algorithm>
 #include <cstdlib>
 
@@ -66,16 +71,20 @@ __device__ __forceinline__ void load_batch(const uint32_t *cl, uint32_t e, uint3
   for (uint32_t u = 0; u < kFillBatch; ++u) cv[u] = e + u < e1 ? __ldg(cl + e + u) : 0u;
 }
 
-// Per (segment, warp) stream length: the largest per-lane element count of the
-// warp in that column block, rounded up to a multiple of 4.  CTAs of
-// kFillThreads lanes of a tile; per-(block, lane) counters in shared memory.
+// Per (segment, warp): the stream's step count T, the smallest even T with
+// 32 T >= the warp's elements in the column block, 2 T >= the most elements
+// of one lane, and T >= the most elements of one row (see the layout in the
+// header).  CTAs of kFillThreads lanes of a tile; per-(block, lane) counters
+// in shared memory.  Columns of a row are sorted, so a row's elements in one
+// block are one run of its walk.
 __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *inst,
                                                               const uint32_t *btile_inst,
                                                               const uint64_t *bseg_base,
                                                               const uint32_t *row_ptr,
                                                               const uint32_t *col, uint32_t *bwlen,
                                                               uint32_t *unsorted, uint32_t t_off) {
-  __shared__ uint16_t s_cnt[kBMaxBlocks][kFillThreads];
+  __shared__ uint16_t s_cnt[kBMaxBlocks][kFillThreads];  // elements of the lane in block b
+  __shared__ uint16_t s_run[kBMaxBlocks][kFillThreads];  // its longest row in block b
   const uint32_t t = t_off + blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
@@ -84,14 +93,17 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
   const uint32_t tid = threadIdx.x;
   const uint32_t v = blockIdx.y * kFillThreads + tid;
   const uint32_t nb = I.nb;
-  for (uint32_t b = 0; b < nb; ++b) s_cnt[b][tid] = 0;
+  for (uint32_t b = 0; b < nb; ++b) {
+    s_cnt[b][tid] = 0;
+    s_run[b][tid] = 0;
+  }
   bool bad = false;
   uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
   row_ranges(rp, row0 + v, I.n, re0, re1);
 #pragma unroll
   for (int k = 0; k < kBRowsPerThread; ++k) {
     const uint32_t e0 = re0[k], e1 = re1[k];
-    uint32_t prev = 0;
+    uint32_t prev = 0, cur_b = kBMaxBlocks, run = 0;
     for (uint32_t e = e0; e < e1; e += kFillBatch) {
       uint32_t cv[kFillBatch];
       load_batch(cl, e, e1, cv);
@@ -100,116 +112,120 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
         if (e + u >= e1) break;
         const uint32_t c = cv[u];
         const uint32_t b = c >> kBColBits;
-        if (b < nb) s_cnt[b][tid]++;    // columns >= n are invalid input: skipped
         bad |= e + u > e0 && c < prev;  // the format needs sorted rows
         prev = c;
+        if (b >= nb) continue;          // columns >= n are invalid input: skipped
+        s_cnt[b][tid]++;
+        if (b == cur_b) {
+          ++run;
+        } else {
+          if (cur_b < nb) s_run[cur_b][tid] = (uint16_t)max((uint32_t)s_run[cur_b][tid], run);
+          cur_b = b;
+          run = 1;
+        }
       }
     }
+    if (cur_b < nb) s_run[cur_b][tid] = (uint16_t)max((uint32_t)s_run[cur_b][tid], run);
   }
   if (bad) *unsorted = 1u;
   for (uint32_t b = 0; b < nb; ++b) {
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, (uint32_t)s_cnt[b][tid]);
-    if ((tid & 31) == 0)
-      bwlen[(bseg_base[t] + b) * 32 + (v >> 5)] = (wmax + 3) & ~3u;
+    const uint32_t c = s_cnt[b][tid];
+    const uint32_t tot = __reduce_add_sync(0xffffffffu, c);
+    const uint32_t most = __reduce_max_sync(0xffffffffu, c);
+    const uint32_t row = __reduce_max_sync(0xffffffffu, (uint32_t)s_run[b][tid]);
+    const uint32_t T = max(max((tot + 31) / 32, (most + 1) / 2), row);
+    if ((tid & 31) == 0) bwlen[(bseg_base[t] + b) * 32 + (v >> 5)] = (T + 1) & ~1u;
   }
 }
 
-// Fill the streams in one pass over the CSR.  A CTA takes kFillThreads of the
-// tile's kBThreads lanes ("virtual threads" v); each walks its rows in slot
-// order and each row's columns once, appending every element to the stream
-// of its column block.  Per (block, lane), the 4 elements of the open stripe
-// wait in shared memory and go out as one 8-byte and one 4-byte store when
-// the stripe is full; partial stripes are written at the end (their unfilled
-// positions keep the padding values).  The element order within a stream is
-// the lane's rows in slot order, each row's columns in input order.
+// Fill the streams: each lane walks its rows twice (slot order, columns in
+// input order).  The first walk counts its elements per block; a warp
+// prefix over the lanes then gives each lane the first index j of its
+// elements in the warp's sequence (lanes in order, each lane's in walk
+// order), and the second walk writes element j at step j mod T, lane
+// j / T.  The positions past the warp's last element (j from its count to
+// 32 T) get the lane's padding element.
 __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *inst,
                                                              const uint32_t *btile_inst,
                                                              const uint64_t *bseg_base,
                                                              const uint64_t *bwstart,
+                                                             const uint32_t *bwlen,
                                                              const uint32_t *row_ptr,
-                                                             const uint32_t *col, uint16_t *bcol,
-                                                             uint8_t *bslot, uint32_t nbmax) {
-  // dynamic shared memory, nbmax column blocks:
-  //   start[nbmax][4] u64, col[nbmax][4][128] u16, q[nbmax][128] u16, slot[nbmax][4][128] u8
+                                                             const uint32_t *col, uint32_t *belem,
+                                                             uint32_t nbmax) {
+  // dynamic shared memory: next index [nbmax][kFillThreads] u32, then per
+  // (block, warp of the CTA) the stream start (u64) and step count (u32)
   extern __shared__ uint64_t s_dyn[];
   uint64_t *s_start = s_dyn;
-  uint16_t *s_col = reinterpret_cast<uint16_t *>(s_start + nbmax * (kFillThreads / 32));
-  uint16_t *s_q = s_col + nbmax * 4 * kFillThreads;
-  uint8_t *s_slot = reinterpret_cast<uint8_t *>(s_q + nbmax * kFillThreads);
+  uint32_t *s_T = reinterpret_cast<uint32_t *>(s_start + nbmax * (kFillThreads / 32));
+  uint32_t *s_next = s_T + nbmax * (kFillThreads / 32);
   const uint32_t t = blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
   const uint32_t *cl = col + I.edge_base;
   const uint32_t row0 = (t - I.btile_base) * kBTileRows;
   const uint32_t tid = threadIdx.x;
-  const uint32_t v = blockIdx.y * kFillThreads + tid;  // lane index within the tile
+  const uint32_t v = blockIdx.y * kFillThreads + tid;  // lane index within the tile (SpMV thread)
   const uint32_t lane = v & 31, wl = tid >> 5;          // wl: warp within this CTA
   const uint32_t nb = I.nb;
-  // element (b, p) of this thread's open stripes
-#define COL(b, p) s_col[((b) * 4 + (p)) * kFillThreads + tid]
-#define SLOT(b, p) s_slot[((b) * 4 + (p)) * kFillThreads + tid]
-  for (uint32_t b = 0; b < nb; ++b) s_q[b * kFillThreads + tid] = 0;
+  for (uint32_t b = 0; b < nb; ++b) s_next[b * kFillThreads + tid] = 0;
   for (uint32_t q = tid; q < nb * (kFillThreads / 32); q += kFillThreads) {
     const uint32_t b = q / (kFillThreads / 32), w = q % (kFillThreads / 32);
-    s_start[q] = bwstart[(bseg_base[t] + b) * 32 + blockIdx.y * (kFillThreads / 32) + w];
+    const uint64_t wi = (bseg_base[t] + b) * 32 + blockIdx.y * (kFillThreads / 32) + w;
+    s_start[q] = bwstart[wi];
+    s_T[q] = bwlen[wi];
   }
   __syncthreads();
-  auto flush = [&](uint32_t b, uint32_t stripe) {
-    uint2 cv;
-    cv.x = (uint32_t)COL(b, 0) | ((uint32_t)COL(b, 1) << 16);
-    cv.y = (uint32_t)COL(b, 2) | ((uint32_t)COL(b, 3) << 16);
-    const uint32_t sv = (uint32_t)SLOT(b, 0) | ((uint32_t)SLOT(b, 1) << 8) |
-                        ((uint32_t)SLOT(b, 2) << 16) | ((uint32_t)SLOT(b, 3) << 24);
-    const uint64_t st = s_start[b * (kFillThreads / 32) + wl];
-#ifdef CB_DEBUG
-    // the stripe lies inside this (segment, warp) stream: before the next one starts
-    const uint64_t wi = (bseg_base[t] + b) * 32 + blockIdx.y * (kFillThreads / 32) + wl;
-    if (!CB_DCHECK(st + 128ull * stripe + 4 * lane + 3 < bwstart[wi + 1], kDbgBlockedFill,
-                   st + 128ull * stripe + 4 * lane))
-      return;
-#endif
-    reinterpret_cast<uint2 *>(bcol + st)[32 * stripe + lane] = cv;
-    reinterpret_cast<uint32_t *>(bslot + st)[32 * stripe + lane] = sv;
-  };
   uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
   row_ranges(rp, row0 + v, I.n, re0, re1);
+  auto walk = [&](bool write) {
 #pragma unroll
-  for (int k = 0; k < kBRowsPerThread; ++k) {
-    const uint32_t e1 = re1[k];
-    for (uint32_t e = re0[k]; e < e1; e += kFillBatch) {
-      uint32_t cv[kFillBatch];
-      load_batch(cl, e, e1, cv);
+    for (int k = 0; k < kBRowsPerThread; ++k) {
+      const uint32_t e1 = re1[k];
+      const uint32_t off = (uint32_t)k * kBThreads + lane;  // accumulator of (slot k, lane)
+      for (uint32_t e = re0[k]; e < e1; e += kFillBatch) {
+        uint32_t cv[kFillBatch];
+        load_batch(cl, e, e1, cv);
 #pragma unroll
-      for (uint32_t u = 0; u < kFillBatch; ++u) {
-        if (e + u >= e1) break;
-        const uint32_t c = cv[u];
-        const uint32_t b = c >> kBColBits;
-        if (b >= nb) continue;  // columns >= n are invalid input: skipped
-        const uint32_t q = s_q[b * kFillThreads + tid];
-        const uint32_t p = q & 3;
-        COL(b, p) = (uint16_t)(c & (kBCol - 1));
-        SLOT(b, p) = (uint8_t)k;
-        s_q[b * kFillThreads + tid] = (uint16_t)(q + 1);
-        if (p == 3) flush(b, q >> 2);
+        for (uint32_t u = 0; u < kFillBatch; ++u) {
+          if (e + u >= e1) break;
+          const uint32_t c = cv[u];
+          const uint32_t b = c >> kBColBits;
+          if (b >= nb) continue;  // columns >= n are invalid input: skipped
+          const uint32_t j = s_next[b * kFillThreads + tid]++;
+          if (!write) continue;
+          const uint32_t T = s_T[b * (kFillThreads / 32) + wl];
+          const uint32_t s = j % T, l = j / T;
+          const uint64_t at = s_start[b * (kFillThreads / 32) + wl] + 64ull * (s >> 1) + 2 * l + (s & 1);
+          if (CB_DCHECK(l < 32u, kDbgBlockedFill, j)) belem[at] = (c & (kBCol - 1)) | (off << kBColBits);
+        }
       }
     }
-  }
+  };
+  walk(false);
+  // exclusive prefix of the counts over the warp's lanes; the padding
   for (uint32_t b = 0; b < nb; ++b) {
-    const uint32_t q = s_q[b * kFillThreads + tid];
-    if (q & 3) {
-      for (uint32_t p = q & 3; p < 4; ++p) {
-        COL(b, p) = (uint16_t)kBPadCol;
-        SLOT(b, p) = 0;
-      }
-      flush(b, q >> 2);
+    const uint32_t c = s_next[b * kFillThreads + tid];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+    s_next[b * kFillThreads + tid] = incl - c;
+    const uint32_t T = s_T[b * (kFillThreads / 32) + wl];
+    const uint64_t st = s_start[b * (kFillThreads / 32) + wl];
+    for (uint32_t j = tot + lane; j < 32 * T; j += 32) {
+      const uint32_t s = j % T, l = j / T;
+      belem[st + 64ull * (s >> 1) + 2 * l + (s & 1)] = kBPadOff(l) << kBColBits;
     }
   }
-#undef COL
-#undef SLOT
+  walk(true);
 }
 
 size_t fill_smem_bytes(uint32_t nbmax) {
-  return (size_t)nbmax * ((kFillThreads / 32) * 8 + kFillThreads * (4 * 2 + 2 + 4));
+  return (size_t)nbmax * ((kFillThreads / 32) * (8 + 4) + kFillThreads * 4);
 }
 
 // x[i] *= 32: stream offsets in elements from the prefix of per-lane lengths
@@ -231,15 +247,13 @@ void free_blocked(cb_graph *h) {
   dev_free(h->d_bwstart);
   dev_free(h->d_bwlen);
   dev_free(h->d_bwscan);
-  dev_free(h->d_bcol);
-  dev_free(h->d_bslot);
+  dev_free(h->d_belem);
   dev_free(h->d_blong_ptr);
   dev_free(h->d_blong_rows);
   h->d_btile_inst = nullptr;
   h->d_bseg_base = h->d_bwstart = h->d_bwscan = nullptr;
   h->d_bwlen = nullptr;
-  h->d_bcol = nullptr;
-  h->d_bslot = nullptr;
+  h->d_belem = nullptr;
   h->d_blong_ptr = h->d_blong_rows = nullptr;
   h->total_btiles = 0;
   h->total_bseg = 0;
@@ -348,20 +362,16 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
     }
     const uint64_t alloc = tot + 16;
-    chk(dalloc(&h->d_bcol, alloc));
-    chk(dalloc(&h->d_bslot, alloc));
+    chk(dalloc(&h->d_belem, alloc));
     if (e == cudaSuccess) {
-      static_assert((kBPadCol >> 8) == (kBPadCol & 0xff), "padding column must be a repeated byte");
-      chk(cudaMemsetAsync(h->d_bcol, (int)(kBPadCol & 0xff), alloc * 2, s));  // padding: zero word
-      chk(cudaMemsetAsync(h->d_bslot, 0, alloc, s));                          // into slot 0
       uint32_t nbmax = 1;
       for (uint32_t r = 0; r < h->n_inst; ++r) nbmax = std::max(nbmax, h->inst[r].nb);
       const size_t shm = fill_smem_bytes(nbmax);
       if (shm > 48 * 1024)
         chk(cudaFuncSetAttribute(bfill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
       bfill_kernel<<<dim3(nbt, kBThreads / kFillThreads), kFillThreads, shm, s>>>(
-          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->row_ptr, h->col, h->d_bcol,
-          h->d_bslot, nbmax);
+          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->d_bwlen, h->row_ptr, h->col,
+          h->d_belem, nbmax);
       chk(cudaGetLastError());
       chk(cudaStreamSynchronize(s));
     }

@@ -38,11 +38,10 @@ constexpr int kBRowsPerThread = 16;
 constexpr int kBTileRows = kBThreads * kBRowsPerThread;  // 16384
 constexpr uint32_t kBColBits = 14;
 constexpr uint32_t kBCol = 1u << kBColBits;              // 16384 floats = 64 KB per buffer
-// Padding elements of the edge streams read column kBPadCol, a zero word placed
-// after each staged block, into row slot 0: they add +0 and need no test.
-// (0x4040 is a repeated byte, so the padding is a plain byte memset.)
-constexpr uint32_t kBPadCol = 0x4040;
-constexpr uint32_t kBBuf = kBPadCol + 4;                 // floats per staging buffer (16-byte multiple)
+constexpr uint32_t kBBuf = kBCol + 4;                    // floats per staging buffer (16-byte multiple)
+// A padding element of lane l adds into the lane's spare row sum (slot
+// kBRowsPerThread), which no row reads.
+__host__ __device__ constexpr uint32_t kBPadOff(uint32_t l) { return kBRowsPerThread * kBThreads + l; }
 constexpr uint32_t kBMaxBlocks = 32;                     // blocked when n <= 32 * kBCol
 constexpr uint32_t kBLongDeg = 512;                      // longer rows: whole-CTA global gathers
 
@@ -201,9 +200,8 @@ struct cb_graph {
   uint64_t *d_bseg_base = nullptr;       // first (tile, column block) segment of each tile
   uint64_t *d_bwstart = nullptr;         // per (segment, warp): first element of its region
   uint64_t *d_bwscan = nullptr;          // scratch of the prefix that makes d_bwstart
-  uint32_t *d_bwlen = nullptr;           // per (segment, warp): longest lane stream
-  uint16_t *d_bcol = nullptr;            // local column (col & (kBCol-1)) per element (padding: kBPadCol)
-  uint8_t *d_bslot = nullptr;            // row slot (0..15) of the owning lane (padding: 0)
+  uint32_t *d_bwlen = nullptr;           // per (segment, warp): steps T of its stream (even)
+  uint32_t *d_belem = nullptr;           // stream elements: local column | row-sum offset << kBColBits
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
   // two-phase format (FP32 SpMV), for realisations with pb = 1

@@ -286,9 +286,10 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(LArgs a, uint32_t j, uin
 // single writer, so the result is deterministic.
 // ---------------------------------------------------------------------------
 
-// two column blocks of W_j (each followed by its zero word), then
-// kBRowsPerThread accumulator slots per thread
-constexpr size_t kBSmemBytes = (2 * kBBuf + kBRowsPerThread * kBThreads) * sizeof(float);
+// two column blocks of W_j, then kBRowsPerThread row sums per thread and
+// one spare per thread (the padding elements add into it)
+constexpr size_t kBSmemBytes = (2 * kBBuf + (kBRowsPerThread + 1) * kBThreads) * sizeof(float);
+static_assert(kBSmemBytes + 1024 <= 227 * 1024, "column-blocked CTA shared memory");
 
 __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j,
                                                              uint32_t btile_off) {
@@ -318,10 +319,9 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   const uint32_t row0 = (t - I.btile_base) * kBTileRows;
   const uint32_t tid = threadIdx.x;
 
-  for (uint32_t q = tid; q < kBRowsPerThread * kBThreads; q += kBThreads) sacc[q] = 0.f;
+  for (uint32_t q = tid; q < (kBRowsPerThread + 1) * kBThreads; q += kBThreads) sacc[q] = 0.f;
   for (uint32_t q = tid; q < kBTileRows / 32; q += kBThreads) s_long[q] = 0u;
   if (tid < 2) {
-    xs[tid * kBBuf + kBPadCol] = 0.f;  // the padding elements read these
     mbar_init(&s_full[tid], 1);
     s_done[tid] = 0;
     s_issued[tid] = 0;
@@ -342,21 +342,18 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   }
 
   const uint32_t lane = tid & 31, warp = tid >> 5;
-  // Stripe rounds: a warp's stream of block b has ns_b = len_b / 4 stripes,
-  // read 4 stripes (16 elements per lane) per round.  The loads of the next
-  // round -- in the same block or, after the last round, round 0 of the next
-  // block -- are issued before the current round is processed, so the
-  // global-memory latency overlaps the shared-memory work and the barrier.
-  uint64_t my = a.bwstart[sbase * 32 + warp] + 4 * lane;
-  uint32_t ns = a.bwlen[sbase * 32 + warp] >> 2;
-  uint2 cvA[4], cvB[4];
-  uint32_t svA[4], svB[4];
+  // Rounds: a warp's stream of block b has T_b steps, read as T_b / 2 pairs
+  // (two elements per lane per 8-byte load), 4 pairs per round.  The loads of
+  // the next round -- in the same block or, after the last round, round 0 of
+  // the next block -- are issued before the current round is processed, so
+  // the global-memory latency overlaps the shared-memory work and the wait.
+  uint64_t my = a.bwstart[sbase * 32 + warp] + 2 * lane;
+  uint32_t np = a.bwlen[sbase * 32 + warp] >> 1;
+  uint2 eA[4], eB[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    if ((uint32_t)u < ns) {
-      cvA[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * u));
-      svA[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * u));
-    }
+    if ((uint32_t)u < np) eA[u] = __ldcs(reinterpret_cast<const uint2 *>(a.belem + my + 64ull * u));
+  float *sw = sacc + 32 * warp;  // this warp's row sums: sw[k * kBThreads + lane]
   // Column block b of W_j goes to buffer b & 1 by one bulk copy that
   // completes on s_full[b & 1].  No CTA-wide barrier per block: each warp
   // waits only for the block it needs, and the last warp to finish with a
@@ -371,10 +368,7 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   // b + 2 is staged, so the warps' stream loads find them there.
   auto prefetch_seg = [&](uint32_t b) {
     const uint64_t e0 = s_seg[b], e1 = s_seg[b + 1];
-    if (e1 > e0) {
-      l2_prefetch(a.bcol + e0, (uint32_t)(2 * (e1 - e0)));
-      l2_prefetch(a.bslot + e0, (uint32_t)(e1 - e0));
-    }
+    if (e1 > e0) l2_prefetch(a.belem + e0, (uint32_t)(4 * (e1 - e0)));
   };
   if (tid == 0) {
     for (uint32_t b = 1; b < 3 && b < nb; ++b) prefetch_seg(b);
@@ -388,61 +382,50 @@ __global__ void __launch_bounds__(kBThreads, 1) bspmv_kernel(LArgs a, uint32_t j
   bool aborted = false;
   for (uint32_t b = 0; b < nb; ++b) {
     uint64_t my1 = 0;
-    uint32_t ns1 = 0;
+    uint32_t np1 = 0;
     if (b + 1 < nb) {
       const uint64_t nseg = sbase + b + 1;
-      my1 = a.bwstart[nseg * 32 + warp] + 4 * lane;
-      ns1 = a.bwlen[nseg * 32 + warp] >> 2;
+      my1 = a.bwstart[nseg * 32 + warp] + 2 * lane;
+      np1 = a.bwlen[nseg * 32 + warp] >> 1;
     }
     if (!mbar_wait(&s_full[b & 1], (b >> 1) & 1u)) {
       aborted = true;  // the copy never landed: give up on this tile
       break;
     }
     const float *cur = xs + (b & 1) * kBBuf;
-    float *mine = sacc + tid;
-    const uint32_t nr = (ns + 3) >> 2;
+    const uint32_t nr = (np + 3) >> 2;
     const uint32_t iters = nr ? nr : 1u;  // one pass even when empty: prefetch the next block
     for (uint32_t r = 0; r < iters; ++r) {
       // next round's loads
       if (r + 1 < nr) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (4 * (r + 1) + u < ns) {
-            cvB[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my + 128ull * (4 * (r + 1) + u)));
-            svB[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my + 128ull * (4 * (r + 1) + u)));
-          }
+          if (4 * (r + 1) + u < np)
+            eB[u] = __ldcs(reinterpret_cast<const uint2 *>(a.belem + my + 64ull * (4 * (r + 1) + u)));
       } else if (b + 1 < nb) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if ((uint32_t)u < ns1) {
-            cvB[u] = __ldcs(reinterpret_cast<const uint2 *>(a.bcol + my1 + 128ull * u));
-            svB[u] = __ldcs(reinterpret_cast<const uint32_t *>(a.bslot + my1 + 128ull * u));
-          }
+          if ((uint32_t)u < np1) eB[u] = __ldcs(reinterpret_cast<const uint2 *>(a.belem + my1 + 64ull * u));
       }
-      // this round
+      // this round: no two lanes of a step add into one row sum
       if (r < nr) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (4 * r + u < ns) {
+          if (4 * r + u < np) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const uint32_t col = ((e < 2 ? cvA[u].x : cvA[u].y) >> (16 * (e & 1))) & 0xffffu;
-              const uint32_t k = (svA[u] >> (8 * e)) & 0xffu;
-              // padding: cur[kBPadCol] = 0 into slot 0
-              if (CB_DCHECK((col < kBCol || col == kBPadCol) && k < (uint32_t)kBRowsPerThread,
-                            kDbgBlockedElem, col | (k << 16)))
-                mine[k * kBThreads] += cur[col];
+            for (int e = 0; e < 2; ++e) {
+              const uint32_t v = e ? eA[u].y : eA[u].x;
+              const uint32_t col = v & (kBCol - 1), off = v >> kBColBits;
+              if (CB_DCHECK((off & (kBThreads - 1)) < 32u && off <= kBPadOff(31), kDbgBlockedElem, v))
+                sw[off] += cur[col];
             }
           }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        cvA[u] = cvB[u];
-        svA[u] = svB[u];
-      }
+      for (int u = 0; u < 4; ++u) eA[u] = eB[u];
     }
     my = my1;
-    ns = ns1;
+    np = np1;
     // this warp is done with buffer b & 1; the last warp refills it with block b + 2
     __syncwarp();
     if (lane == 0) {
@@ -779,8 +762,7 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.bseg_base = h->d_bseg_base;
   a.bwstart = h->d_bwstart;
   a.bwlen = h->d_bwlen;
-  a.bcol = h->d_bcol;
-  a.bslot = h->d_bslot;
+  a.belem = h->d_belem;
   a.blong_ptr = h->d_blong_ptr;
   a.blong_rows = h->d_blong_rows;
   // FP32 path: the column-blocked kernel needs about one 16384-row tile per

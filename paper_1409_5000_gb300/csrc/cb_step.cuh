@@ -31,8 +31,7 @@ struct LArgs {
   const uint32_t *btile_inst;
   const uint64_t *bseg_base, *bwstart;
   const uint32_t *bwlen;
-  const uint16_t *bcol;
-  const uint8_t *bslot;
+  const uint32_t *belem;
   const uint32_t *blong_ptr, *blong_rows;
   uint32_t skip_blocked;  // the tiled-CSR kernel leaves blocked realisations alone
   uint32_t stall_btile;   // test hook: this tile's first column block is never copied
