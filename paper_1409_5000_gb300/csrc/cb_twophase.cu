@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kP1Threads, 1) pscatter_kernel(LArgs a, uint32
               o.y = vt[sv.x >> 16];
               o.z = vt[sv.y & 0xffffu];
               o.w = vt[sv.y >> 16];
-              X[2ull * d + half] = o;
+              __stcs(X + 2ull * d + half, o);  // read back by phase 2 only, much later
             }
           }
           // this warp is done with buffer b; the last warp refills it
