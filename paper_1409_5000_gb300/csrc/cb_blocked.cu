@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
                                                               const uint64_t *bseg_base,
                                                               const uint32_t *row_ptr,
                                                               const uint32_t *col, uint32_t *bwlen,
-                                                              uint32_t *unsorted, uint32_t t_off) {
+                                                              uint16_t *bcnt, uint32_t *unsorted,
+                                                              uint32_t t_off) {
   __shared__ uint16_t s_cnt[kBMaxBlocks][kFillThreads];  // elements of the lane in block b
   __shared__ uint16_t s_run[kBMaxBlocks][kFillThreads];  // its longest row in block b
   const uint32_t t = t_off + blockIdx.x;
@@ -135,30 +136,42 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
     const uint32_t row = __reduce_max_sync(0xffffffffu, (uint32_t)s_run[b][tid]);
     const uint32_t T = max(max((tot + 31) / 32, (most + 1) / 2), row);
     if ((tid & 31) == 0) bwlen[(bseg_base[t] + b) * 32 + (v >> 5)] = (T + 1) & ~1u;
+    bcnt[(bseg_base[t] + b) * kBThreads + v] = (uint16_t)c;  // the fill's lane offsets
   }
 }
 
-// Fill the streams: each lane walks its rows twice (slot order, columns in
-// input order).  The first walk counts its elements per block; a warp
-// prefix over the lanes then gives each lane the first index j of its
-// elements in the warp's sequence (lanes in order, each lane's in walk
-// order), and the second walk writes element j at step j mod T, lane
-// j / T.  The positions past the warp's last element (j from its count to
-// 32 T) get the lane's padding element.
+// Fill the streams.  The count pass left each lane's elements per block; a
+// warp prefix over the lanes gives each lane the first index j of its
+// elements in the warp's sequence (lanes in order, each lane's in walk order:
+// rows in slot order, columns in input order).  Element j belongs at
+// step j mod T, lane j / T, and the positions past the warp's last element
+// (j from its count to 32 T) take the lane's padding element.  The streams
+// are then written a batch of blocks at a time: each warp assembles its
+// streams of the batch in shared memory (a second walk, resumed where the
+// previous batch stopped -- the columns of a row are sorted) and copies them
+// out with coalesced 16-byte stores.  A block whose stream does not fit the
+// staging area is written element by element.
+constexpr uint32_t kStageWords = 3072;  // staging u32 words per warp
+
 __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *inst,
                                                              const uint32_t *btile_inst,
                                                              const uint64_t *bseg_base,
                                                              const uint64_t *bwstart,
                                                              const uint32_t *bwlen,
+                                                             const uint16_t *bcnt,
                                                              const uint32_t *row_ptr,
                                                              const uint32_t *col, uint32_t *belem,
                                                              uint32_t nbmax) {
-  // dynamic shared memory: next index [nbmax][kFillThreads] u32, then per
-  // (block, warp of the CTA) the stream start (u64) and step count (u32)
-  extern __shared__ uint64_t s_dyn[];
-  uint64_t *s_start = s_dyn;
+  // dynamic shared memory: the staging areas [4][kStageWords] u32, then per
+  // (block, warp of the CTA) the stream start (u64), step count and element
+  // count (u32), then the next index [nbmax][kFillThreads] u32
+  extern __shared__ uint4 s_dyn4[];
+  uint32_t *s_stage = reinterpret_cast<uint32_t *>(s_dyn4);
+  uint64_t *s_start = reinterpret_cast<uint64_t *>(s_stage + (kFillThreads / 32) * kStageWords);
   uint32_t *s_T = reinterpret_cast<uint32_t *>(s_start + nbmax * (kFillThreads / 32));
-  uint32_t *s_next = s_T + nbmax * (kFillThreads / 32);
+  uint32_t *s_tot = s_T + nbmax * (kFillThreads / 32);
+  uint32_t *s_sb = s_tot + nbmax * (kFillThreads / 32);  // staging offset of block b's stream
+  uint32_t *s_next = s_sb + nbmax * (kFillThreads / 32);
   const uint32_t t = blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
@@ -168,64 +181,113 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
   const uint32_t v = blockIdx.y * kFillThreads + tid;  // lane index within the tile (SpMV thread)
   const uint32_t lane = v & 31, wl = tid >> 5;          // wl: warp within this CTA
   const uint32_t nb = I.nb;
+  constexpr uint32_t W = kFillThreads / 32;
+  uint32_t *stage = s_stage + wl * kStageWords;  // this warp's staging area
   for (uint32_t b = 0; b < nb; ++b) s_next[b * kFillThreads + tid] = 0;
-  for (uint32_t q = tid; q < nb * (kFillThreads / 32); q += kFillThreads) {
-    const uint32_t b = q / (kFillThreads / 32), w = q % (kFillThreads / 32);
-    const uint64_t wi = (bseg_base[t] + b) * 32 + blockIdx.y * (kFillThreads / 32) + w;
+  for (uint32_t q = tid; q < nb * W; q += kFillThreads) {
+    const uint32_t b = q / W, w = q % W;
+    const uint64_t wi = (bseg_base[t] + b) * 32 + blockIdx.y * W + w;
     s_start[q] = bwstart[wi];
     s_T[q] = bwlen[wi];
   }
   __syncthreads();
   uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
   row_ranges(rp, row0 + v, I.n, re0, re1);
-  auto walk = [&](bool write) {
-#pragma unroll
-    for (int k = 0; k < kBRowsPerThread; ++k) {
-      const uint32_t e1 = re1[k];
-      const uint32_t off = (uint32_t)k * kBThreads + lane;  // accumulator of (slot k, lane)
-      for (uint32_t e = re0[k]; e < e1; e += kFillBatch) {
-        uint32_t cv[kFillBatch];
-        load_batch(cl, e, e1, cv);
-#pragma unroll
-        for (uint32_t u = 0; u < kFillBatch; ++u) {
-          if (e + u >= e1) break;
-          const uint32_t c = cv[u];
-          const uint32_t b = c >> kBColBits;
-          if (b >= nb) continue;  // columns >= n are invalid input: skipped
-          const uint32_t j = s_next[b * kFillThreads + tid]++;
-          if (!write) continue;
-          const uint32_t T = s_T[b * (kFillThreads / 32) + wl];
-          const uint32_t s = j % T, l = j / T;
-          const uint64_t at = s_start[b * (kFillThreads / 32) + wl] + 64ull * (s >> 1) + 2 * l + (s & 1);
-          if (CB_DCHECK(l < 32u, kDbgBlockedFill, j)) belem[at] = (c & (kBCol - 1)) | (off << kBColBits);
-        }
-      }
-    }
-  };
-  walk(false);
-  // exclusive prefix of the counts over the warp's lanes; the padding
+  // the walk loops over the row slots without unrolling (the kernel stays
+  // small enough for the instruction cache); re0/re1/ecur live in local memory.
+  // The lane's elements per block come from the count pass; their exclusive
+  // prefix over the warp's lanes gives each lane its first position (step s,
+  // lane l), kept as l << 16 | s and advanced per element
   for (uint32_t b = 0; b < nb; ++b) {
-    const uint32_t c = s_next[b * kFillThreads + tid];
+    const uint32_t c = bcnt[(bseg_base[t] + b) * kBThreads + v];
     uint32_t incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= (uint32_t)o) incl += y;
     }
-    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-    s_next[b * kFillThreads + tid] = incl - c;
-    const uint32_t T = s_T[b * (kFillThreads / 32) + wl];
-    const uint64_t st = s_start[b * (kFillThreads / 32) + wl];
-    for (uint32_t j = tot + lane; j < 32 * T; j += 32) {
-      const uint32_t s = j % T, l = j / T;
-      belem[st + 64ull * (s >> 1) + 2 * l + (s & 1)] = kBPadOff(l) << kBColBits;
-    }
+    const uint32_t j0 = incl - c, T = s_T[b * W + wl];
+    s_next[b * kFillThreads + tid] = T ? ((j0 / T) << 16) | (j0 % T) : 0u;
+    if (lane == 31) s_tot[b * W + wl] = incl;
   }
-  walk(true);
+  __syncwarp();
+  // second walk, a batch of blocks [b0, b1) at a time; the batch ends before
+  // the block that would overflow the staging area of this warp
+  uint32_t ecur[kBRowsPerThread];
+#pragma unroll
+  for (int k = 0; k < kBRowsPerThread; ++k) ecur[k] = re0[k];
+  uint32_t b0 = 0;
+  while (b0 < nb) {
+    uint32_t b1 = b0, used = 0;
+    while (b1 < nb && (used + 32 * s_T[b1 * W + wl] <= kStageWords || b1 == b0)) {
+      if (lane == 0) s_sb[b1 * W + wl] = used;
+      used += 32 * s_T[b1 * W + wl];
+      ++b1;
+    }
+    __syncwarp();
+    const bool staged = used <= kStageWords;  // false: one block too large, written directly
+    // the padding of the batch's streams
+    for (uint32_t b = b0; b < b1; ++b) {
+      const uint32_t T = s_T[b * W + wl], base = s_sb[b * W + wl];
+      const uint64_t st = s_start[b * W + wl];
+      for (uint32_t j = s_tot[b * W + wl] + lane; j < 32 * T; j += 32) {
+        const uint32_t s = j % T, l = j / T;
+        const uint32_t q = 64 * (s >> 1) + 2 * l + (s & 1);
+        const uint32_t el = kBPadOff(l) << kBColBits;
+        if (staged) stage[base + q] = el; else belem[st + q] = el;
+      }
+    }
+    // the elements of blocks [b0, b1), resuming each row where the last batch stopped
+#pragma unroll 1
+    for (int k = 0; k < kBRowsPerThread; ++k) {
+      const uint32_t e1 = re1[k];
+      const uint32_t off = (uint32_t)k * kBThreads + lane;  // row sum of (slot k, lane)
+      uint32_t e = ecur[k];
+      bool more = e < e1;
+      while (more) {  // kFillBatch columns per round of loads
+        uint32_t cv[kFillBatch];
+        load_batch(cl, e, e1, cv);
+        uint32_t taken = kFillBatch;
+#pragma unroll
+        for (uint32_t u = 0; u < kFillBatch; ++u) {
+          if (e + u >= e1 || (cv[u] >> kBColBits) >= b1) {  // the row is done for this batch
+            taken = u;
+            break;
+          }
+          const uint32_t c = cv[u];
+          const uint32_t b = c >> kBColBits;  // b0 <= b < b1 (columns >= n end the row's walk)
+          const uint32_t T = s_T[b * W + wl];
+          uint32_t p = s_next[b * kFillThreads + tid];
+          const uint32_t s = p & 0xffffu, l = p >> 16;
+          p = s + 1 == T ? p + (1u << 16) - s : p + 1;
+          s_next[b * kFillThreads + tid] = p;
+          if (!CB_DCHECK(l < 32u && s < T, kDbgBlockedFill, p)) continue;
+          const uint32_t q = 64 * (s >> 1) + 2 * l + (s & 1);
+          const uint32_t el = (c & (kBCol - 1)) | (off << kBColBits);
+          if (staged) stage[s_sb[b * W + wl] + q] = el; else belem[s_start[b * W + wl] + q] = el;
+        }
+        e += taken;
+        more = taken == kFillBatch && e < e1;
+      }
+      ecur[k] = e;
+    }
+    __syncwarp();
+    if (staged) {  // the batch's streams, 16 bytes per lane per store
+      for (uint32_t b = b0; b < b1; ++b) {
+        const uint32_t words = 32 * s_T[b * W + wl];
+        uint4 *dst = reinterpret_cast<uint4 *>(belem + s_start[b * W + wl]);
+        const uint4 *src = reinterpret_cast<const uint4 *>(stage + s_sb[b * W + wl]);
+        for (uint32_t q = lane; q < words / 4; q += 32) dst[q] = src[q];
+      }
+    }
+    __syncwarp();
+    b0 = b1;
+  }
 }
 
 size_t fill_smem_bytes(uint32_t nbmax) {
-  return (size_t)nbmax * ((kFillThreads / 32) * (8 + 4) + kFillThreads * 4);
+  return (size_t)(kFillThreads / 32) * kStageWords * 4 +
+         (size_t)nbmax * ((kFillThreads / 32) * (8 + 4 + 4 + 4) + kFillThreads * 4);
 }
 
 // x[i] *= 32: stream offsets in elements from the prefix of per-lane lengths
@@ -246,6 +308,8 @@ void free_blocked(cb_graph *h) {
   dev_free(h->d_bseg_base);
   dev_free(h->d_bwstart);
   dev_free(h->d_bwlen);
+  dev_free(h->d_bcnt);
+  h->d_bcnt = nullptr;
   dev_free(h->d_bwscan);
   dev_free(h->d_belem);
   dev_free(h->d_blong_ptr);
@@ -319,6 +383,7 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
     chk(dalloc(&h->d_bseg_base, nbt));
     chk(dalloc(&h->d_bwstart, nw + 1));
     chk(dalloc(&h->d_bwlen, nw + 1));  // + the sortedness flag of the count pass
+    chk(dalloc(&h->d_bcnt, nseg * kBThreads));
     chk(dalloc(&h->d_bwscan, nw / 4096 + 2));  // prefix scratch
     chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
     chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
@@ -343,7 +408,8 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       const uint32_t t1 = h->inst[g.r_end - 1].btile_base + h->inst[g.r_end - 1].n_btiles;
       if (t1 > t0 && e == cudaSuccess)
         bcount_kernel<<<dim3(t1 - t0, kBThreads / kFillThreads), kFillThreads, 0, s>>>(
-            h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr, h->col, h->d_bwlen, d_unsorted, t0);
+            h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr, h->col, h->d_bwlen, h->d_bcnt,
+            d_unsorted, t0);
       r_begin = g.r_end;
     }
     chk(cudaGetLastError());
@@ -370,8 +436,8 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       if (shm > 48 * 1024)
         chk(cudaFuncSetAttribute(bfill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
       bfill_kernel<<<dim3(nbt, kBThreads / kFillThreads), kFillThreads, shm, s>>>(
-          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->d_bwlen, h->row_ptr, h->col,
-          h->d_belem, nbmax);
+          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->d_bwlen, h->d_bcnt, h->row_ptr,
+          h->col, h->d_belem, nbmax);
       chk(cudaGetLastError());
       chk(cudaStreamSynchronize(s));
     }

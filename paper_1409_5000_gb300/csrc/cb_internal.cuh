@@ -201,6 +201,7 @@ struct cb_graph {
   uint64_t *d_bwstart = nullptr;         // per (segment, warp): first element of its region
   uint64_t *d_bwscan = nullptr;          // scratch of the prefix that makes d_bwstart
   uint32_t *d_bwlen = nullptr;           // per (segment, warp): steps T of its stream (even)
+  uint16_t *d_bcnt = nullptr;            // per (segment, lane): its elements (format build)
   uint32_t *d_belem = nullptr;           // stream elements: local column | row-sum offset << kBColBits
   uint32_t *d_blong_ptr = nullptr;       // per blocked tile: range in d_blong_rows
   uint32_t *d_blong_rows = nullptr;      // local rows with degree > kBLongDeg, in row order
