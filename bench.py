@@ -94,12 +94,13 @@ def workload(name):
 # source that decides the traffic (kernels, epilogue, format builder,
 # constants) still hashes to the captured version.
 _TRAFFIC = {
-    "blocked": {"sources_sha256_16": "93b7b04521a0dccc", "bytes_per_edge": (778.72e6 + 21.19e6) / 151654698,
+    # one launch on the 40-realisation case: 703.01 MB read + 20.04 MB written
+    "blocked": {"sources_sha256_16": "950b36dfd490de8e", "bytes_per_edge": (703.01e6 + 20.04e6) / 151654698,
                 "kernel": "bspmv_kernel", "captured_on": "er-ensemble-40"},
-    # one launch of each phase on the 10M-node graph: phase 1 492.13 MB read +
-    # 664.68 MB written, phase 2 1.17 GB read + 34.36 MB written
-    "twophase": {"sources_sha256_16": "03028aa62d3c3036",
-                 "bytes_per_edge": (492.13e6 + 664.68e6 + 1.17e9 + 34.36e6) / 160000252,
+    # one launch of each phase on the 10M-node graph: phase 1 492.12 MB read +
+    # 661.91 MB written, phase 2 1173.79 MB read + 34.77 MB written
+    "twophase": {"sources_sha256_16": "3be61c496ed83da9",
+                 "bytes_per_edge": (492.12e6 + 661.91e6 + 1173.79e6 + 34.77e6) / 160000252,
                  "kernel": "pscatter_kernel + pgather_kernel", "captured_on": "ba-1e7"},
 }
 
