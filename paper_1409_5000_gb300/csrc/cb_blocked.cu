@@ -183,7 +183,6 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
   const uint32_t nb = I.nb;
   constexpr uint32_t W = kFillThreads / 32;
   uint32_t *stage = s_stage + wl * kStageWords;  // this warp's staging area
-  for (uint32_t b = 0; b < nb; ++b) s_next[b * kFillThreads + tid] = 0;
   for (uint32_t q = tid; q < nb * W; q += kFillThreads) {
     const uint32_t b = q / W, w = q % W;
     const uint64_t wi = (bseg_base[t] + b) * 32 + blockIdx.y * W + w;

@@ -777,7 +777,6 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   a.ptbase = h->d_ptbase;
   a.ptile_inst = h->d_ptile_inst;
   a.pxbase = h->d_pxbase;
-  a.ppos = h->d_ppos;
   a.psrc = h->d_psrc;
   a.pgdst = h->d_pgdst;
   a.pX = h->d_pX;

@@ -40,7 +40,7 @@ struct LArgs {
   const uint64_t *ptbase;
   const uint32_t *ptile_inst;
   const uint64_t *pxbase;
-  const uint16_t *ppos, *psrc;
+  const uint16_t *psrc;
   const uint32_t *pgdst;
   float *pX;
   const uint16_t *psl;      // phase-2 plans (sliced rows)
