@@ -371,10 +371,13 @@ def kernel_families(B, step, steps):
 
 
 def spmv_path(ens, csr_only=False):
-    """Which FP32 SpMV the workload runs under the automatic path: 'twophase'
-    (a realisation above 2^19 nodes), 'blocked' (otherwise, when the handle
-    has at least one 16384-row blocked tile per SM) or 'csr' (fewer tiles,
-    or CB_CSR_ONLY)."""
+    """Which SpMV the workload runs under the automatic path: 'small' (every
+    realisation at most 8192 nodes and 2^20 entries: one launch of m steps),
+    'twophase' (a realisation above 2^19 nodes), 'blocked' (otherwise, when
+    the handle has at least one 16384-row blocked tile per SM) or 'csr'
+    (fewer tiles, or CB_CSR_ONLY)."""
+    if all(g.n <= 8192 and g.nnz <= (1 << 20) for g in ens.graphs):
+        return "small"
     if csr_only:
         return "csr"
     if max(g.n for g in ens.graphs) > 32 * 16384:
@@ -385,25 +388,28 @@ def spmv_path(ens, csr_only=False):
     return "blocked" if tiles >= torch.cuda.get_device_properties(0).multi_processor_count else "csr"
 
 
-_KERNEL_NAMES = {"blocked": "bspmv_kernel (column-blocked Lanczos SpMV step)",
+_KERNEL_NAMES = {"small": "lanczos_small_kernel (all m Lanczos steps of a small realisation per CTA)",
+                 "blocked": "bspmv_kernel (column-blocked Lanczos SpMV step)",
                  "twophase": "pscatter_kernel + pgather_kernel (two-phase Lanczos SpMV step)",
                  "csr": "spmv_kernel (tiled-CSR Lanczos SpMV step)"}
 
 
-def roofline_for(ens, fam, path):
+def roofline_for(ens, fam, path, m=1):
     """The roofline object of the SpMV family: algorithmic bytes of one
     launch over its average event-timed duration, against the measured HBM
-    copy bandwidth."""
+    copy bandwidth.  On the 'small' path one launch runs all m steps, so its
+    bytes are m SpMVs' (vector traffic beyond the SpMV's is not counted)."""
     tot = sum(t for t, _ in fam.values())
     spmv_ms, spmv_n = fam["spmv"]
     spmv_avg = spmv_ms / max(spmv_n, 1)
     peak, peak_kind = measured_peak()
-    achieved = alg_bytes_spmv(ens) / (spmv_avg * 1e-3) / 1e9
+    per_launch = (m if path == "small" else 1) * alg_bytes_spmv(ens)
+    achieved = per_launch / (spmv_avg * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": _KERNEL_NAMES[path], "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "frac_of_8TBs_nominal": achieved / 8000.0,
-            "traffic": traffic_per_launch(ens, path) if path != "csr" else None,
-            "alg_bytes_per_launch": alg_bytes_spmv(ens), "avg_launch_ms": spmv_avg,
+            "traffic": traffic_per_launch(ens, path) if path in ("blocked", "twophase") else None,
+            "alg_bytes_per_launch": per_launch, "avg_launch_ms": spmv_avg,
             "kernel_shares": {k: round(t / tot, 4) for k, (t, _) in fam.items()}}
 
 
@@ -411,6 +417,9 @@ def launches_for(m, path, with_grad=False):
     """Kernel launches of one step: init (2) + per Lanczos step the SpMV
     (two kernels on the two-phase path), finalize and beta + tridiag +
     combine (2) + top-k (init, 12 radix passes, collect, sort)."""
+    if path == "small":  # one launch for all m steps
+        n = 2 + 1 + 1 + 2 + 15
+        return n + (3 + 1) + 3 if with_grad else n
     per_step = (2 if path == "twophase" else 1) + 2
     n = 2 + per_step * m + 1 + 2 + 15
     if with_grad:  # the Lanczos run from the indicator (the basis from 1 is the
@@ -443,6 +452,36 @@ def check_run(B, gs, m, prec):
     if bad or not math.isfinite(float(ls.item())):
         raise RuntimeError(f"bench: realisations failed (index, status): {bad[:8]}; "
                            f"log scale {float(ls.item())}")
+
+
+def budgeted_backward(B, gs, m, prec, idx, k, grad, gls, stream):
+    """The adjoint of the same top-k under a budget of a quarter of its working
+    set (cb_scores_backward_budget: groups of realisations, bases recomputed in
+    temporary handles), timed against the unbudgeted call; both synchronous."""
+    import torch
+
+    r4 = (m + 3) // 4 * 4
+    esz = 8 if prec == 1 else 4
+    ws = sum(esz * n * (2 * (m + 1) + 2 * r4) for n in gs.n) + 12 * sum(gs.nnz)
+    g2 = torch.empty_like(grad)
+    l2 = torch.empty_like(gls)
+    t = {}
+    for label, budget in (("unbudgeted", 0), ("budget", ws // 4)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if budget:
+            B.cb_scores_backward_budget(gs.h, m, prec, idx.data_ptr(), k, g2.data_ptr(),
+                                        l2.data_ptr(), budget, stream.cuda_stream)
+        else:
+            B.cb_scores_backward(gs.h, m, prec, idx.data_ptr(), k, grad.data_ptr(), gls.data_ptr(),
+                                 stream.cuda_stream)
+        torch.cuda.synchronize()
+        t[label] = 1e3 * (time.perf_counter() - t0)
+    a, b = g2.double(), grad.double()
+    return {"budget_bytes": ws // 4, "working_set_bytes": ws, "ms": t["budget"],
+            "ms_unbudgeted": t["unbudgeted"],
+            "max_abs_diff_rel": float((a - b).abs().max() / b.abs().max()),
+            "api": "cb_scores_backward_budget vs cb_scores_backward, wall time of one synchronous call"}
 
 
 def extra_leg(B, name, steps, warmup, dev, csr_only=False, precs=(0,), built=None, tune=False):
@@ -491,17 +530,21 @@ def extra_leg(B, name, steps, warmup, dev, csr_only=False, precs=(0,), built=Non
             check_run(B, gs, m, prec)
             units = sum(g.nnz for g in ens.graphs) * m
             fam = kernel_families(B, step, steps)
-            path = "csr" if (csr_only or prec == 1) else spmv_path(ens)
+            path = spmv_path(ens, csr_only)
+            if path != "small" and prec == 1:
+                path = "csr"
             leg = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
-                   "dtype": "f64" if prec == 1 else "f32", "roofline": roofline_for(ens, fam, path),
+                   "dtype": "f64" if prec == 1 else "f32", "roofline": roofline_for(ens, fam, path, m),
                    "gpu_launches_per_step": launches_for(m, path, with_grad)}
             if prec == 1:  # FP64 bytes: 8-byte vector elements
-                leg["roofline"]["alg_bytes_per_launch"] = alg_bytes_spmv(ens, fp64=True)
-                a = alg_bytes_spmv(ens, fp64=True) / (leg["roofline"]["avg_launch_ms"] * 1e-3) / 1e9
+                b64 = (m if path == "small" else 1) * alg_bytes_spmv(ens, fp64=True)
+                leg["roofline"]["alg_bytes_per_launch"] = b64
+                a = b64 / (leg["roofline"]["avg_launch_ms"] * 1e-3) / 1e9
                 leg["roofline"].update(achieved=a, frac=a / leg["roofline"]["peak"],
                                        frac_of_8TBs_nominal=a / 8000.0)
             if with_grad:
                 leg["backward_share"] = round(fam["backward"][0] / sum(t for t, _ in fam.values()), 4)
+                leg["budgeted"] = budgeted_backward(B, gs, m, prec, idx, k, grad, gls, stream)
             leg["scores"] = (float(ls.item()), S.cpu().numpy())
             out["f64" if prec == 1 else "f32"] = leg
         if tune:
@@ -607,7 +650,7 @@ def main():
     # per-kernel times (CUDA events around each launch, same stream), separate pass
     fam = kernel_families(B, step, args.steps)
     path_kind = spmv_path(ens, args.csr_only)
-    roofline = roofline_for(ens, fam, path_kind)
+    roofline = roofline_for(ens, fam, path_kind, m)
     launches_per_step = launches_for(m, path_kind, with_grad)
 
     extra = {}

@@ -69,8 +69,11 @@ extern "C" {
 #define CB_TWO_PHASE 8u   /* the two-phase format for every realisation (default: n > 2^19 only) */
 
 /* FP32 SpMV path of a handle (cb_graph_set_path) */
-#define CB_PATH_AUTO 0    /* column-blocked kernel when the handle has >= one blocked tile per SM,
-                             two-phase kernels where built, else tiled CSR */
+#define CB_PATH_AUTO 0    /* one launch of all m steps (one CTA per realisation) when every
+                             realisation of the call has n <= 8192 and <= 2^20 entries and no
+                             reorthogonalisation is asked; otherwise, per step, the
+                             column-blocked kernel when the handle has >= one blocked tile per
+                             SM, two-phase kernels where built, else tiled CSR */
 #define CB_PATH_FORMATS 1 /* column-blocked and two-phase kernels wherever their format was built */
 #define CB_PATH_CSR 2     /* the tiled-CSR kernel for every realisation */
 

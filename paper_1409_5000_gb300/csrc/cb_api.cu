@@ -609,6 +609,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     InstDesc &I = h->inst[r];
     std::memset(&I, 0, sizeof I);
     I.n = n[r];
+    I.nnz = (uint32_t)nnz[r];
     I.node_base = node_off;
     I.edge_base = edge_off;
     I.rp_base = rp_off;

@@ -99,7 +99,7 @@ struct InstDesc {
   uint64_t edge_base;  // offset of the first column index in col[]
   uint64_t rp_base;    // offset of row_ptr[0] in the row_ptr array
   uint32_t n;
-  uint32_t nnz_hi;     // unused (nnz < 2^32 per instance); keeps alignment
+  uint32_t nnz;        // CSR entries of the realisation (< 2^32)
   uint32_t tile_base, n_tiles;    // SpMV tiles (<= kTileRows rows, ~kTileNnz entries)
   uint32_t heavy_base, n_heavy;   // heavy rows
   uint32_t chunk_base, n_chunks;  // heavy-row chunks

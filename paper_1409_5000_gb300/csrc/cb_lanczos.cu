@@ -579,6 +579,88 @@ __global__ void __launch_bounds__(kThreads) finalize_beta_kernel(LArgs a, uint32
 }
 
 // ---------------------------------------------------------------------------
+// Small realisations (n <= kSmallN, at most kSmallNnz entries): one CTA per
+// realisation runs all m Lanczos steps in one launch -- SpMV with the row
+// epilogue, alpha, the axpy w = u - alpha_j scale_j W_j, beta_j and the
+// breakdown test, the same arithmetic as spmv_kernel + finalize_kernel +
+// finalize_beta_kernel -- with W_j staged in shared memory and the
+// reductions CTA-wide (no grid-wide one is needed), so a pass of m steps is
+// one launch instead of 3m.  Rows are summed by groups of 8 lanes.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSmallN = 8192;
+constexpr uint32_t kSmallNnz = 1u << 20;
+constexpr int kSmallThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) lanczos_small_kernel(LArgs a, uint32_t r0, uint32_t m) {
+  extern __shared__ float4 s_dyn4[];
+  T *xs = reinterpret_cast<T *>(s_dyn4);  // W_j of the realisation
+  __shared__ double s_red[32];
+  const uint32_t r = r0 + blockIdx.x;
+  const InstDesc &I = a.inst[r];
+  const uint32_t n = I.n, ms = a.sc.ms;
+  const uint32_t *rp = a.row_ptr + I.rp_base;
+  const uint32_t *cl = a.col + I.edge_base;
+  T *Vb = reinterpret_cast<T *>(a.V);
+  const uint32_t tid = threadIdx.x, l8 = tid & 7u, grp = tid >> 3;
+  const unsigned gmask = 0xffu << (tid & 24u);  // the 8 lanes of this thread's group
+  constexpr uint32_t kGroups = kSmallThreads / 8;
+  for (uint32_t j = 0; j < m; ++j) {
+    if (j >= a.sc.meff[r]) break;  // uniform: written by thread 0 before a CTA barrier
+    const T *x = Vb + (uint64_t)j * a.vs + I.node_base;
+    const T *xp = j > 0 ? x - a.vs : x;
+    T *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
+    for (uint32_t i = tid; i < n; i += kSmallThreads) xs[i] = x[i];
+    __syncthreads();
+    const T sj = (T)a.sc.scale[r * ms + j];
+    const T bp = j > 0 ? (T)(a.sc.beta[r * ms + j - 1] * a.sc.scale[r * ms + j - 1]) : T(0);
+    T acc = T(0);
+    for (uint32_t i = grp; i < n; i += kGroups) {
+      T sum = T(0);
+      for (uint32_t e = rp[i] + l8; e < rp[i + 1]; e += 8) {
+        const uint32_t c = cl[e];
+        if (CB_DCHECK(c < n, kDbgCsrCol, c)) sum += xs[c];
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o, 8);
+      if (l8 == 0) {
+        T u = sj * sum;
+        if (j > 0) u -= bp * xp[i];
+        out[i] = u;
+        acc += xs[i] * u;
+      }
+    }
+    const double dot = block_sum_to_double<T>(acc, s_red);  // also orders `out` for the CTA
+    if (tid == 0) finish_alpha<T>(a, r, j, dot);
+    __syncthreads();
+    if (j >= a.sc.meff[r]) break;  // alpha was not finite
+    const T coef = (T)(a.sc.alpha[r * ms + j] * a.sc.scale[r * ms + j]);
+    T acc2 = T(0);
+    for (uint32_t i = tid; i < n; i += kSmallThreads) {
+      const T w = out[i] - coef * xs[i];
+      out[i] = w;
+      acc2 += w * w;
+    }
+    const double total = block_sum_to_double<T>(acc2, s_red);
+    if (tid == 0) {  // beta_j, the breakdown test and scale_{j+1}, as finalize_beta_kernel
+      const double beta = sqrt(total);
+      const double alpha = a.sc.alpha[r * ms + j];
+      const double bprev = j > 0 ? a.sc.beta[r * ms + j - 1] : 0.0;
+      a.sc.beta[r * ms + j] = beta;
+      if (!isfinite(beta)) {
+        a.sc.status[r] = CB_ERR_NONFINITE;
+        a.sc.meff[r] = j + 1;
+      } else if (beta <= a.tau * (fabs(alpha) + bprev) || beta == 0.0) {
+        a.sc.meff[r] = j + 1;
+      } else {
+        a.sc.scale[r * ms + j + 1] = 1.0 / beta;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Full reorthogonalisation (CB_REORTH), after the finalize of step j: the new
 // vector w (basis slot j + 1, unnormalised) is orthogonalised against
 // v_i = scale_i W_i, i = 0..j, by classical Gram-Schmidt,
@@ -833,6 +915,25 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   init_scalars_kernel<<<(uint32_t)((nsc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
       a, r0, r1, m, start_idx, k, per_inst, rscale);
   prof_end(tok, s);
+  // small realisations only (and the automatic path, no reorthogonalisation):
+  // the whole recurrence in one launch, one CTA per realisation
+  bool small = h->path == CB_PATH_AUTO && !h->reorth && h->stall_btile == UINT32_MAX;
+  for (uint32_t r = r0; r < r1 && small; ++r) small = h->inst[r].n <= kSmallN && h->inst[r].nnz <= kSmallNnz;
+  if (small) {
+    const size_t shm = (size_t)nmax * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(lanczos_small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmallN * sizeof(double)));
+      cudaFuncSetAttribute(lanczos_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmallN * sizeof(double)));
+      attr = true;
+    }
+    tok = prof_begin(CB_K_SPMV, s);
+    lanczos_small_kernel<T><<<r1 - r0, kSmallThreads, shm, s>>>(a, r0, m);
+    prof_end(tok, s);
+    return cuda_error(cudaGetLastError(), "lanczos launch");
+  }
   for (uint32_t j = 0; j < m; ++j) {
     tok = prof_begin(CB_K_SPMV, s);
     if (any_csr) launch_spmv_lanes<T>(h->lanes, a, j, chunk_off, n_chunks, tile_off, n_tiles, s);

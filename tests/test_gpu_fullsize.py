@@ -100,3 +100,35 @@ def test_adjoint_64_sampled_realisations(B):
         norm = float(np.linalg.norm(a - g_o) / np.linalg.norm(g_o))
         assert head <= 1e-3 and norm <= 1e-3, dict(r=r, head=head, norm=norm)
     assert n == 100_000
+
+
+def test_adjoint_64_budgeted_groups_full_size(B):
+    """The C5 shape under a device-memory budget of a quarter of its adjoint
+    working set: cb_scores_backward_budget runs the 64 realisations in groups
+    (about four) in temporary handles, recomputing each group's bases.  A
+    group handle holds fewer blocked tiles than one per SM, so its automatic
+    FP32 SpMV path is the tiled-CSR kernel where the whole handle's is the
+    column-blocked one: the bases differ by FP32 rounding, so the gradient,
+    brought to the same log scale, is compared at 1e-4 (relative to its
+    largest entry and in the 2-norm), with the same zero pattern."""
+    ens = synth.er_ensemble_grad()
+    m, k = ens.meta["m"], ens.meta["k"]
+    r4 = (m + 3) // 4 * 4
+    ws = sum(4 * g.n * (2 * (m + 1) + 2 * r4) + 12 * g.nnz for g in ens.graphs)
+    with B.GraphSet(ens.graphs) as gs:
+        _, S = B.ensemble_scores(gs, m, B.CB_FP32)
+        idx, _ = B.topk(S, k)
+        ls0, g0 = B.scores_backward(gs, m, idx, B.CB_FP32)
+        g = torch.empty_like(g0)
+        ls = torch.empty(1, dtype=torch.float64, device="cuda")
+        B.cb_scores_backward_budget(gs.h, m, B.CB_FP32, idx.data_ptr(), k, g.data_ptr(),
+                                    ls.data_ptr(), ws // 4, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        shift = float(ls.item()) - float(ls0.item())
+        assert abs(shift) <= 1e-6
+        a = g.cpu().numpy().astype(np.float64) * math.exp(shift)
+        b = g0.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(a - b)) <= 1e-4 * np.max(np.abs(b))
+    assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b)
+    assert np.array_equal(a == 0, b == 0)
+

@@ -345,3 +345,30 @@ def test_upload_concurrent_with_compute(B):
             gb.close()
         assert np.array_equal(got_a.cpu().numpy(), ref_a)
     assert np.array_equal(got_b, ref_b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_path_single_launch(B, prec):
+    """Realisations of at most 8192 nodes run all m steps in one launch (one
+    CTA per realisation) on the automatic path: the scores meet the oracle bar,
+    agree with the per-step tiled-CSR kernels (CB_PATH_CSR) to rounding, and
+    the breakdowns (K_30, whose all-ones vector is an eigenvector, and an
+    isolated-node realisation: m_eff = 1) stop where the per-step path stops.
+    Uneven sizes up to the limit."""
+    graphs = [synth.er(n, 10.0 / (n - 1), 40 + q) for q, n in enumerate([500, 8192, 3001, 64])]
+    graphs.append(synth.from_edges(30, [(i, j) for i in range(30) for j in range(i + 1, 30)]))
+    graphs.append(synth.from_edges(700, np.zeros((0, 2), np.uint32)))
+    m = 20
+    th_o, S_o = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], m)
+    out = {}
+    for path in (0, 2):  # automatic (single launch), tiled CSR per step
+        with B.GraphSet(graphs, path=path) as gs:
+            ls, S, rep = B.ensemble_scores(gs, m, PREC[prec], report=True)
+            torch.cuda.synchronize()
+            out[path] = (float(ls.item()), S.cpu().numpy(), [(r.m_eff, r.status) for r in rep])
+    parity.assert_scores(out[0][0], out[0][1], th_o, S_o, prec)
+    assert out[0][2] == out[2][2], (out[0][2], out[2][2])
+    assert out[0][2][4][0] == 1 and out[0][2][5][0] == 1 and out[0][2][0][0] == m
+    e = parity.errors(out[0][0], out[0][1], out[2][0], out[2][1])
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert e["head_rel"] <= tol and e["norm_rel"] <= tol, e
