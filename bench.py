@@ -413,15 +413,17 @@ def roofline_for(ens, fam, path, m=1):
             "kernel_shares": {k: round(t / tot, 4) for k, (t, _) in fam.items()}}
 
 
-def launches_for(m, path, with_grad=False):
+def launches_for(m, path, with_grad=False, n_scores=None):
     """Kernel launches of one step: init (2) + per Lanczos step the SpMV
     (two kernels on the two-phase path), finalize and beta + tridiag +
-    combine (2) + top-k (init, 12 radix passes, collect, sort)."""
+    combine (2) + top-k (init, 12 radix passes, collect, sort; one sort of
+    all scores up to 4096 of them)."""
+    topk = 1 if n_scores is not None and n_scores <= 4096 else 15
     if path == "small":  # one launch for all m steps
-        n = 2 + 1 + 1 + 2 + 15
+        n = 2 + 1 + 1 + 2 + topk
         return n + (3 + 1) + 3 if with_grad else n
     per_step = (2 if path == "twophase" else 1) + 2
-    n = 2 + per_step * m + 1 + 2 + 15
+    n = 2 + per_step * m + 1 + 2 + topk
     if with_grad:  # the Lanczos run from the indicator (the basis from 1 is the
         # forward pass's) + 3 adjoint kernels
         n += (3 + per_step * m) + 3
@@ -535,7 +537,7 @@ def extra_leg(B, name, steps, warmup, dev, csr_only=False, precs=(0,), built=Non
                 path = "csr"
             leg = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
                    "dtype": "f64" if prec == 1 else "f32", "roofline": roofline_for(ens, fam, path, m),
-                   "gpu_launches_per_step": launches_for(m, path, with_grad)}
+                   "gpu_launches_per_step": launches_for(m, path, with_grad, gs.n_max)}
             if prec == 1:  # FP64 bytes: 8-byte vector elements
                 b64 = (m if path == "small" else 1) * alg_bytes_spmv(ens, fp64=True)
                 leg["roofline"]["alg_bytes_per_launch"] = b64
@@ -651,7 +653,7 @@ def main():
     fam = kernel_families(B, step, args.steps)
     path_kind = spmv_path(ens, args.csr_only)
     roofline = roofline_for(ens, fam, path_kind, m)
-    launches_per_step = launches_for(m, path_kind, with_grad)
+    launches_per_step = launches_for(m, path_kind, with_grad, gs.n_max)
 
     extra = {}
     if with_grad:

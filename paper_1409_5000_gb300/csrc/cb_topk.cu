@@ -16,6 +16,7 @@
 //    is needed;
 //  * one pass collects the k elements at or above the prefix, one CTA sorts
 //    them (bitonic) and writes indices and values.
+// Up to 4096 scores, one CTA sorts them all instead (one launch).
 //
 // Every pass is launched unconditionally and returns at once when the
 // selection is complete, so the sequence needs no host round trip.
@@ -174,10 +175,58 @@ __global__ void __launch_bounds__(1024) topk_sort(const double *__restrict__ S, 
   }
 }
 
+// n <= kTopkSmallN: one CTA sorts all n composite keys (bitonic, in shared
+// memory, the same order as topk_sort) and writes the first k -- one launch
+// instead of the 15 of the radix select.
+constexpr uint32_t kTopkSmallN = 4096;
+
+__global__ void __launch_bounds__(1024) topk_small(const double *__restrict__ S, uint32_t n,
+                                                   uint32_t k, uint32_t P, uint32_t *idx,
+                                                   double *val) {
+  extern __shared__ unsigned char s_raw[];
+  unsigned long long *sk = reinterpret_cast<unsigned long long *>(s_raw);
+  uint32_t *si = reinterpret_cast<uint32_t *>(sk + P);
+  for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) {
+    if (q < n) { sk[q] = order_key(S[q]); si[q] = q; }
+    else { sk[q] = 0ull; si[q] = 0xffffffffu; }  // after every element, NaN included
+  }
+  __syncthreads();
+  for (uint32_t size = 2; size <= P; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) {
+        const uint32_t p = q ^ stride;
+        if (p > q) {
+          const bool desc = (q & size) == 0;
+          const bool swap = desc ? before(sk[p], si[p], sk[q], si[q])
+                                 : before(sk[q], si[q], sk[p], si[p]);
+          if (swap) {
+            const unsigned long long tk = sk[q]; sk[q] = sk[p]; sk[p] = tk;
+            const uint32_t ti = si[q]; si[q] = si[p]; si[p] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t q = threadIdx.x; q < k; q += blockDim.x) {
+    idx[q] = si[q];
+    val[q] = S[si[q]];
+  }
+}
+
 }  // namespace
 
 int topk_launch(const double *S, uint32_t n, uint32_t k, uint32_t *idx, double *val,
                 void *scratch, cudaStream_t s) {
+  if (n <= kTopkSmallN) {
+    uint32_t P = 1;
+    while (P < n) P <<= 1;
+    const int tok = prof_begin(CB_K_TOPK, s);
+    topk_small<<<1, 1024, (size_t)P * (sizeof(unsigned long long) + sizeof(uint32_t)), s>>>(S, n, k, P,
+                                                                                          idx, val);
+    prof_end(tok, s);
+    return cuda_error(cudaGetLastError(), "topk launch");
+  }
   TopkState *st = reinterpret_cast<TopkState *>(scratch);
   Cand *buf = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) +
                                        ((sizeof(TopkState) + 255) / 256) * 256);

@@ -167,8 +167,8 @@ def test_empty_and_complete_breakdown(B):
     assert rep.m_eff == 1 and np.allclose(np.exp(theta) * y, math.exp(39), rtol=parity.TOL_FP32)
 
 
-@pytest.mark.parametrize("n,k", [(1, 1), (7, 7), (1000, 1), (100_000, 64), (1_234_567, 20),
-                                 (50_000, 4096)])
+@pytest.mark.parametrize("n,k", [(1, 1), (7, 7), (1000, 1), (2049, 2000), (4096, 17), (4096, 4096),
+                                 (4097, 30), (100_000, 64), (1_234_567, 20), (50_000, 4096)])
 def test_topk_bit_exact(B, n, k):
     rng = np.random.default_rng(n + k)
     S = rng.integers(0, 50, size=n).astype(np.float64) * 0.25  # many exact ties
