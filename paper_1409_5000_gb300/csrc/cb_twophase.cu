@@ -792,7 +792,7 @@ void launch_twophase(const LArgs &a, int lanes, uint32_t j, uint32_t tile_lo, ui
     pscatter_kernel<<<grid, kP1Threads, kP1SmemBytes, s>>>(a, j, tile_lo, tile_hi, g_lo, g_hi);
   }
   if (n_chunks + n_bins) launch_p2(a, j, chunk_off, n_chunks, bin_off, n_bins, n_sm, s);
-  (void)lanes;  // the merge-path walk of phase 2 needs no group width
+  (void)lanes;  // the sliced rows of phase 2 need no group width
 }
 
 void free_twophase(cb_graph *h) {
