@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
 // previous batch stopped -- the columns of a row are sorted) and copies them
 // out with coalesced 16-byte stores.  A block whose stream does not fit the
 // staging area is written element by element.
-constexpr uint32_t kStageWords = 3072;  // staging u32 words per warp
+constexpr uint32_t kStageWords = 2048;  // staging u32 words per warp
 
 __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *inst,
                                                              const uint32_t *btile_inst,
@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
   uint32_t *s_tot = s_T + nbmax * (kFillThreads / 32);
   uint32_t *s_sb = s_tot + nbmax * (kFillThreads / 32);  // staging offset of block b's stream
   uint32_t *s_next = s_sb + nbmax * (kFillThreads / 32);
+  uint32_t *s_ecur = s_next + nbmax * kFillThreads;  // [k][lane]: next entry of row slot k
+  uint32_t *s_re1 = s_ecur + kBRowsPerThread * kFillThreads;  // [k][lane]: end of row slot k
   const uint32_t t = blockIdx.x;
   const InstDesc I = inst[btile_inst[t]];
   const uint32_t *rp = row_ptr + I.rp_base;
@@ -190,10 +192,18 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
     s_T[q] = bwlen[wi];
   }
   __syncthreads();
-  uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
-  row_ranges(rp, row0 + v, I.n, re0, re1);
+  {
+    uint32_t re0[kBRowsPerThread], re1[kBRowsPerThread];
+    row_ranges(rp, row0 + v, I.n, re0, re1);
+#pragma unroll
+    for (int k = 0; k < kBRowsPerThread; ++k) {
+      s_ecur[k * kFillThreads + tid] = re0[k];
+      s_re1[k * kFillThreads + tid] = re1[k];
+    }
+  }
   // the walk loops over the row slots without unrolling (the kernel stays
-  // small enough for the instruction cache); re0/re1/ecur live in local memory.
+  // small enough for the instruction cache); the row cursors live in shared
+  // memory.
   // The lane's elements per block come from the count pass; their exclusive
   // prefix over the warp's lanes gives each lane its first position (step s,
   // lane l), kept as l << 16 | s and advanced per element
@@ -212,9 +222,6 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
   __syncwarp();
   // second walk, a batch of blocks [b0, b1) at a time; the batch ends before
   // the block that would overflow the staging area of this warp
-  uint32_t ecur[kBRowsPerThread];
-#pragma unroll
-  for (int k = 0; k < kBRowsPerThread; ++k) ecur[k] = re0[k];
   uint32_t b0 = 0;
   while (b0 < nb) {
     uint32_t b1 = b0, used = 0;
@@ -239,9 +246,9 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
     // the elements of blocks [b0, b1), resuming each row where the last batch stopped
 #pragma unroll 1
     for (int k = 0; k < kBRowsPerThread; ++k) {
-      const uint32_t e1 = re1[k];
+      const uint32_t e1 = s_re1[k * kFillThreads + tid];
       const uint32_t off = (uint32_t)k * kBThreads + lane;  // row sum of (slot k, lane)
-      uint32_t e = ecur[k];
+      uint32_t e = s_ecur[k * kFillThreads + tid];
       bool more = e < e1;
       while (more) {  // kFillBatch columns per round of loads
         uint32_t cv[kFillBatch];
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
         e += taken;
         more = taken == kFillBatch && e < e1;
       }
-      ecur[k] = e;
+      s_ecur[k * kFillThreads + tid] = e;
     }
     __syncwarp();
     if (staged) {  // the batch's streams, 16 bytes per lane per store
@@ -286,7 +293,8 @@ __global__ void __launch_bounds__(kFillThreads) bfill_kernel(const InstDesc *ins
 
 size_t fill_smem_bytes(uint32_t nbmax) {
   return (size_t)(kFillThreads / 32) * kStageWords * 4 +
-         (size_t)nbmax * ((kFillThreads / 32) * (8 + 4 + 4 + 4) + kFillThreads * 4);
+         (size_t)nbmax * ((kFillThreads / 32) * (8 + 4 + 4 + 4) + kFillThreads * 4) +
+         2 * kBRowsPerThread * kFillThreads * 4;
 }
 
 // x[i] *= 32: stream offsets in elements from the prefix of per-lane lengths
