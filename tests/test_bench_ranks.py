@@ -83,3 +83,29 @@ def test_traffic_guard_hashes_the_kernel_sources():
         t = bench._TRAFFIC[kind]
         if t["bytes_per_edge"] is not None:  # at least the 3 B of a blocked element
             assert t["bytes_per_edge"] > 3.0
+
+
+def test_launch_and_path_accounting():
+    """The launch counts the bench claims follow the library's paths: one launch
+    of all m steps for realisations of at most 8192 nodes, three per Lanczos
+    step otherwise (four on the two-phase path), and one top-k launch for at
+    most 4096 scores (15 otherwise)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class G:
+        def __init__(self, n, nnz):
+            self.n, self.nnz = n, nnz
+
+    class E:
+        def __init__(self, graphs):
+            self.graphs = graphs
+
+    assert bench.spmv_path(E([G(500, 4000)] * 10)) == "small"
+    assert bench.spmv_path(E([G(8192, 1 << 20)])) == "small"
+    assert bench.spmv_path(E([G(8193, 80_000)]), csr_only=True) == "csr"
+    assert bench.spmv_path(E([G(10_000_000, 160_000_000)])) == "twophase"
+    assert bench.launches_for(20, "small", n_scores=500) == 2 + 1 + 1 + 2 + 1
+    assert bench.launches_for(25, "blocked", n_scores=400_000) == 2 + 3 * 25 + 1 + 2 + 15
+    assert bench.launches_for(40, "twophase", n_scores=10_000_000) == 2 + 4 * 40 + 1 + 2 + 15
+    assert bench.launches_for(30, "small", with_grad=True, n_scores=1000) == 7 + 4 + 3
