@@ -535,11 +535,13 @@ int cb_grad_rescale(float *grad, uint64_t count, const double *log_scale_grad,
 /*
  * Bounds-checked debug build.  A library compiled with -DCB_DEBUG
  * (libcb_debug.so, built beside libcb.so) checks, on the device, every
- * column-blocked stream element (column < 16384 or the padding column, row
- * slot < 16) and stream write position, every CSR column the SpMV kernels
- * gather through (< n), the two-phase kernels' source offsets (< the tile's
- * nodes), group places (< the value array) and region slots (< the bin's
- * region), and the adjoint's edge columns (< n).  A failed check counts a
+ * column-blocked stream element (its row-sum offset names one of the warp's
+ * rows or the executing lane's spare sum) and stream write position (inside
+ * the warp's stream), every CSR column the SpMV kernels gather through
+ * (< n), the two-phase kernels' source offsets (< the tile's nodes), group
+ * places (< the value array), region slots (< the bin's region or the zero
+ * slot) and piece numbers (< the bin's pieces), and the adjoint's edge
+ * columns (< n).  A failed check counts a
  * violation, records the first one as (site << 48) | index (sites 1-7 in the
  * order above: blocked element, blocked fill, CSR column, two-phase source,
  * two-phase place, two-phase slot, adjoint column) and skips the access;
