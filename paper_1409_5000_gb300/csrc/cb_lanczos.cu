@@ -583,7 +583,8 @@ __global__ void __launch_bounds__(kThreads) finalize_beta_kernel(LArgs a, uint32
 // realisation runs all m Lanczos steps in one launch -- SpMV with the row
 // epilogue, alpha, the axpy w = u - alpha_j scale_j W_j, beta_j and the
 // breakdown test, the same arithmetic as spmv_kernel + finalize_kernel +
-// finalize_beta_kernel -- with W_j staged in shared memory and the
+// finalize_beta_kernel -- with W_j, W_{j-1} and the new vector resident in
+// shared memory (each new vector is also written to the basis) and the
 // reductions CTA-wide (no grid-wide one is needed), so a pass of m steps is
 // one launch instead of 3m.  Rows are summed by groups of 8 lanes.
 // ---------------------------------------------------------------------------
@@ -593,27 +594,44 @@ constexpr int kSmallThreads = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads) lanczos_small_kernel(LArgs a, uint32_t r0, uint32_t m) {
+  // three vectors of the realisation rotate through shared memory: W_j, W_{j-1}
+  // and the new one (u, then w); each new vector is also stored to the basis
   extern __shared__ float4 s_dyn4[];
-  T *xs = reinterpret_cast<T *>(s_dyn4);  // W_j of the realisation
-  __shared__ double s_red[32];
   const uint32_t r = r0 + blockIdx.x;
   const InstDesc &I = a.inst[r];
   const uint32_t n = I.n, ms = a.sc.ms;
+  T *xs = reinterpret_cast<T *>(s_dyn4);  // W_j
+  T *xps = xs + ((n + 3) & ~3u);          // W_{j-1}
+  T *us = xps + ((n + 3) & ~3u);          // u, then W_{j+1}
+  __shared__ double s_red[32];
   const uint32_t *rp = a.row_ptr + I.rp_base;
   const uint32_t *cl = a.col + I.edge_base;
   T *Vb = reinterpret_cast<T *>(a.V);
   const uint32_t tid = threadIdx.x, l8 = tid & 7u, grp = tid >> 3;
   const unsigned gmask = 0xffu << (tid & 24u);  // the 8 lanes of this thread's group
   constexpr uint32_t kGroups = kSmallThreads / 8;
-  for (uint32_t j = 0; j < m; ++j) {
-    if (j >= a.sc.meff[r]) break;  // uniform: written by thread 0 before a CTA barrier
-    const T *x = Vb + (uint64_t)j * a.vs + I.node_base;
-    const T *xp = j > 0 ? x - a.vs : x;
+  {
+    const T *x0 = Vb + I.node_base;
+    for (uint32_t i = tid; i < n; i += kSmallThreads) xs[i] = x0[i];
+  }
+  // the recurrence scalars stay in shared memory between steps (thread 0
+  // writes them to the Scalars arrays as it forms them, never reads them back)
+  __shared__ double s_scale, s_beta_prev, s_alpha;
+  __shared__ int s_stop;
+  if (tid == 0) {
+    s_scale = a.sc.scale[r * ms];
+    s_beta_prev = 0.0;
+    s_stop = a.sc.meff[r] == 0u;
+  }
+  const uint32_t mr = a.sc.meff[r] < m ? a.sc.meff[r] : m;  // steps allowed from the start
+  __syncthreads();
+  double scale_prev = 0.0;  // scale_{j-1} (all threads)
+  for (uint32_t j = 0; j < mr; ++j) {
+    if (s_stop) break;  // uniform: set by thread 0 before a CTA barrier
     T *out = Vb + (uint64_t)(j + 1) * a.vs + I.node_base;
-    for (uint32_t i = tid; i < n; i += kSmallThreads) xs[i] = x[i];
-    __syncthreads();
-    const T sj = (T)a.sc.scale[r * ms + j];
-    const T bp = j > 0 ? (T)(a.sc.beta[r * ms + j - 1] * a.sc.scale[r * ms + j - 1]) : T(0);
+    const double scale_j = s_scale;
+    const T sj = (T)scale_j;
+    const T bp = j > 0 ? (T)(s_beta_prev * scale_prev) : T(0);
     T acc = T(0);
     for (uint32_t i = grp; i < n; i += kGroups) {
       T sum = T(0);
@@ -625,38 +643,56 @@ __global__ void __launch_bounds__(kSmallThreads) lanczos_small_kernel(LArgs a, u
       for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o, 8);
       if (l8 == 0) {
         T u = sj * sum;
-        if (j > 0) u -= bp * xp[i];
-        out[i] = u;
+        if (j > 0) u -= bp * xps[i];
+        us[i] = u;
         acc += xs[i] * u;
       }
     }
-    const double dot = block_sum_to_double<T>(acc, s_red);  // also orders `out` for the CTA
-    if (tid == 0) finish_alpha<T>(a, r, j, dot);
+    const double dot = block_sum_to_double<T>(acc, s_red);  // also orders `us` for the CTA
+    if (tid == 0) {  // alpha_j, as finish_alpha
+      const double alpha = scale_j * dot;
+      a.sc.alpha[r * ms + j] = alpha;
+      s_alpha = alpha;
+      if (!isfinite(alpha)) {
+        if (a.sc.status[r] == CB_OK) a.sc.status[r] = CB_ERR_NONFINITE;
+        a.sc.meff[r] = j;
+        s_stop = 1;
+      }
+    }
     __syncthreads();
-    if (j >= a.sc.meff[r]) break;  // alpha was not finite
-    const T coef = (T)(a.sc.alpha[r * ms + j] * a.sc.scale[r * ms + j]);
+    if (s_stop) break;  // alpha was not finite
+    const T coef = (T)(s_alpha * scale_j);
     T acc2 = T(0);
     for (uint32_t i = tid; i < n; i += kSmallThreads) {
-      const T w = out[i] - coef * xs[i];
+      const T w = us[i] - coef * xs[i];
+      us[i] = w;
       out[i] = w;
       acc2 += w * w;
     }
     const double total = block_sum_to_double<T>(acc2, s_red);
     if (tid == 0) {  // beta_j, the breakdown test and scale_{j+1}, as finalize_beta_kernel
       const double beta = sqrt(total);
-      const double alpha = a.sc.alpha[r * ms + j];
-      const double bprev = j > 0 ? a.sc.beta[r * ms + j - 1] : 0.0;
+      const double alpha = s_alpha, bprev = s_beta_prev;
       a.sc.beta[r * ms + j] = beta;
       if (!isfinite(beta)) {
         a.sc.status[r] = CB_ERR_NONFINITE;
         a.sc.meff[r] = j + 1;
+        s_stop = 1;
       } else if (beta <= a.tau * (fabs(alpha) + bprev) || beta == 0.0) {
         a.sc.meff[r] = j + 1;
+        s_stop = 1;
       } else {
         a.sc.scale[r * ms + j + 1] = 1.0 / beta;
+        s_scale = 1.0 / beta;
       }
+      s_beta_prev = beta;
     }
+    scale_prev = scale_j;
     __syncthreads();
+    T *t = xps;  // rotate: W_{j-1} <- W_j, W_j <- W_{j+1}
+    xps = xs;
+    xs = us;
+    us = t;
   }
 }
 
@@ -920,13 +956,13 @@ static int run_t(cb_graph *h, Workspace &W, uint32_t r0, uint32_t r1, uint32_t m
   bool small = h->path == CB_PATH_AUTO && !h->reorth && h->stall_btile == UINT32_MAX;
   for (uint32_t r = r0; r < r1 && small; ++r) small = h->inst[r].n <= kSmallN && h->inst[r].nnz <= kSmallNnz;
   if (small) {
-    const size_t shm = (size_t)nmax * sizeof(T);
+    const size_t shm = 3 * (size_t)((nmax + 3) & ~3u) * sizeof(T);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(lanczos_small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kSmallN * sizeof(double)));
+                           (int)(3 * kSmallN * sizeof(double)));
       cudaFuncSetAttribute(lanczos_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kSmallN * sizeof(double)));
+                           (int)(3 * kSmallN * sizeof(double)));
       attr = true;
     }
     tok = prof_begin(CB_K_SPMV, s);
