@@ -439,7 +439,7 @@ def tuned_choice(B, gs, prec=0):
     names = {B.CB_PATH_AUTO: "auto", B.CB_PATH_FORMATS: "formats", B.CB_PATH_CSR: "csr"}
     return {"lanes": lanes, "path": names.get(B.cb_graph_path(gs.h), "?"),
             "ms_per_3_step_run": {"csr_lanes_" + str(w): m for w, m in zip((1, 2, 4, 8, 16, 32), ms)} |
-            {"formats": ms[6]}}
+            {"formats": ms[6], "single_launch": ms[7]}}
 
 
 def check_run(B, gs, m, prec):

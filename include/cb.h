@@ -256,15 +256,19 @@ int cb_subgraph_centrality(cb_graph *h, uint32_t inst, uint32_t m, int prec, uin
  * formats built at upload (column-blocked kernel for n <= 32 * 16384,
  * two-phase kernels above) or the tiled-CSR kernel for every realisation.
  * Candidates: the six widths 1, 2, 4, 8, 16, 32 on the tiled-CSR path, then
- * (FP32, when the handle has a blocked or two-phase format) the format path.
+ * (FP32, when the handle has a blocked or two-phase format) the format path,
+ * then (when every realisation has n <= 8192 and <= 2^20 entries) the
+ * automatic path, which runs all steps of such a handle in one launch.
  * Each is timed on a 3-step Lanczos run over all realisations (CUDA events,
  * two repetitions after a warm-up, on a workspace of its own); the fastest
  * is kept (cb_graph_set_lanes / cb_graph_set_path).  FP64 always runs the
- * tiled-CSR kernel, so only the width is tuned there.  Results do not depend
+ * tiled-CSR kernel (or the single launch of a small handle), so only the
+ * width, and for a small handle the single launch, is tuned there.  Results do not depend
  * on the choice beyond FP summation order.  Synchronises `stream`.
  *   lanes_out  optional host uint32[1]: the width kept.
- *   ms_out     optional host double[7]: ms per run for each width, then for
- *              the format path (-1 when not timed).
+ *   ms_out     optional host double[8]: ms per run for each width, then for
+ *              the format path, then for the single launch (-1 when not
+ *              timed).
  *   The path kept is read back with cb_graph_path.
  */
 int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_out, void *stream);

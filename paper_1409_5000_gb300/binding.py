@@ -228,10 +228,10 @@ def cb_scores_backward_budget(h, m, prec, topk_idx_ptr, k, grad_ptr, log_scale_p
 
 def cb_graph_tune(h, prec, stream):
     """Returns (lanes kept, [ms per candidate: widths 1, 2, 4, 8, 16, 32 on the
-    tiled-CSR path, then the format path; -1 = not timed]).  The path kept is
-    cb_graph_path(h)."""
+    tiled-CSR path, then the format path, then the single launch of a small
+    handle; -1 = not timed]).  The path kept is cb_graph_path(h)."""
     lanes = ctypes.c_uint32()
-    ms = (ctypes.c_double * 7)()
+    ms = (ctypes.c_double * 8)()
     _check(lib().cb_graph_tune(ctypes.c_void_p(h), prec, ctypes.byref(lanes), ms,
                                ctypes.c_void_p(stream)))
     return int(lanes.value), list(ms)

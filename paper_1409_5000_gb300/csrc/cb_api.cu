@@ -839,9 +839,14 @@ CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_
   h->reorth = false;
   if (prec != CB_FP32 && prec != CB_FP64) return set_error(CB_ERR_ARG, "cb_graph_tune: bad precision");
   static const uint32_t kCand[6] = {1, 2, 4, 8, 16, 32};
-  for (int c = 0; ms_out && c < 7; ++c) ms_out[c] = -1.0;
-  // the format path is a candidate in FP32 when a format was built
+  for (int c = 0; ms_out && c < 8; ++c) ms_out[c] = -1.0;
+  // the format path is a candidate in FP32 when a format was built; the
+  // single launch of all steps (the automatic path) when every realisation is
+  // small enough for it
   const bool formats = prec == CB_FP32 && (h->total_btiles > 0 || h->total_ptiles > 0);
+  bool small = true;
+  for (uint32_t r = 0; r < h->n_inst && small; ++r)
+    small = h->inst[r].n <= kSmallN && h->inst[r].nnz <= kSmallNnz;
   constexpr uint32_t kProbe = 3;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Workspace W;
@@ -876,7 +881,9 @@ CB_API int cb_graph_tune(cb_graph *h, int prec, uint32_t *lanes_out, double *ms_
   for (int c = 0; c < 6 && e == cudaSuccess && rc == CB_OK; ++c) time_one((int)kCand[c], CB_PATH_CSR, c);
   // the format path, with the best width for any tiled-CSR realisations left
   if (formats && e == cudaSuccess && rc == CB_OK) time_one(best_lanes, CB_PATH_FORMATS, 6);
-  if (prec == CB_FP64) best_path = keep_path;  // FP64 does not depend on the path
+  if (small && e == cudaSuccess && rc == CB_OK) time_one(best_lanes, CB_PATH_AUTO, 7);
+  // FP64 depends on the path only through the single launch of small handles
+  if (prec == CB_FP64 && !small) best_path = keep_path;
   h->lanes = best_lanes;
   h->path = best_path;
   if (best_lanes != keep_lanes || best_path != keep_path) drop_graphs(h);

@@ -28,6 +28,10 @@ constexpr uint32_t kHeavyDeg = 8192; // rows above this degree are split across 
 constexpr uint32_t kChunk = 4096;    // edges per heavy-row chunk
 constexpr uint32_t kLongDeg = 1024;  // rows above this (<= kHeavyDeg) use the whole CTA
 constexpr int kNodeAlign = 32;       // per-instance node offset alignment (elements)
+// Realisations of at most kSmallN nodes and kSmallNnz entries can run all
+// their Lanczos steps in one launch, one CTA each (lanczos_small_kernel).
+constexpr uint32_t kSmallN = 8192;
+constexpr uint32_t kSmallNnz = 1u << 20;
 
 // Column-blocked SpMV (FP32): a CTA of kBThreads owns kBTileRows rows,
 // kBRowsPerThread rows per thread (strided by kBThreads); the columns are cut into

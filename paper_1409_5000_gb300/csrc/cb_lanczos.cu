@@ -588,8 +588,6 @@ __global__ void __launch_bounds__(kThreads) finalize_beta_kernel(LArgs a, uint32
 // reductions CTA-wide (no grid-wide one is needed), so a pass of m steps is
 // one launch instead of 3m.  Rows are summed by groups of 8 lanes.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSmallN = 8192;
-constexpr uint32_t kSmallNnz = 1u << 20;
 constexpr int kSmallThreads = 512;
 
 template <typename T>

@@ -38,7 +38,7 @@ def test_tuner_keeps_fastest(B):
         lanes, ms = B.cb_graph_tune(gs.h, B.CB_FP64, 0)
         assert lanes in (1, 2, 4, 8, 16, 32) and B.cb_graph_lanes(gs.h) == lanes
         timed = [x for x in ms if x >= 0]
-        assert len(timed) == 6 and ms[6] == -1.0  # FP64: the width only
+        assert len(timed) == 6 and ms[6] == -1.0 and ms[7] == -1.0  # FP64: the width only
         assert ms[[1, 2, 4, 8, 16, 32].index(lanes)] == min(timed)
 
 
@@ -47,11 +47,29 @@ def test_tuner_fp32_picks_width_and_path(B):
     tiled-CSR path and the format path are all timed, and the fastest is kept."""
     with B.GraphSet([synth.er(60_000, 10.0 / 60_000, 5)]) as gs:
         lanes, ms = B.cb_graph_tune(gs.h, B.CB_FP32, 0)
-        assert len(ms) == 7 and all(x >= 0 for x in ms)
+        assert len(ms) == 8 and all(x >= 0 for x in ms[:7]) and ms[7] == -1.0
         path = B.cb_graph_path(gs.h)
         kept = 6 if path == B.CB_PATH_FORMATS else [1, 2, 4, 8, 16, 32].index(lanes)
         assert path in (B.CB_PATH_FORMATS, B.CB_PATH_CSR)
-        assert ms[kept] == min(ms)
+        assert ms[kept] == min(ms[:7])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tuner_times_the_single_launch_of_small_handles(B, prec):
+    """A handle whose realisations all fit the single-launch path: the tuner
+    also times it (slot 7) and keeps it when fastest; scores then meet the
+    oracle bar whatever was kept."""
+    graphs = [synth.er(n, 8.0 / n, 70 + q) for q, n in enumerate([500, 2000, 800] * 20)]
+    with B.GraphSet(graphs) as gs:
+        lanes, ms = B.cb_graph_tune(gs.h, prec, 0)
+        assert ms[7] >= 0
+        path = B.cb_graph_path(gs.h)
+        if path == B.CB_PATH_AUTO:
+            assert ms[7] == min(x for x in ms if x >= 0)
+        ls, S = B.ensemble_scores(gs, 20, prec)
+        torch.cuda.synchronize()
+        th_o, S_o = oc.ensemble_scores([(g.n, g.row_ptr, g.col) for g in graphs], 20)
+        parity.assert_scores(float(ls.item()), S.cpu().numpy(), th_o, S_o, "fp64" if prec else "fp32")
 
 
 @pytest.mark.parametrize("path", [0, 1, 2])
