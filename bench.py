@@ -95,7 +95,7 @@ def workload(name):
 # constants) still hashes to the captured version.
 _TRAFFIC = {
     # one launch on the 40-realisation case: 703.01 MB read + 20.04 MB written
-    "blocked": {"sources_sha256_16": "57fe2446bd5bcc15", "bytes_per_edge": (703.01e6 + 20.04e6) / 151654698,
+    "blocked": {"sources_sha256_16": "4ce8ff9dadfd2966", "bytes_per_edge": (703.01e6 + 20.04e6) / 151654698,
                 "kernel": "bspmv_kernel", "captured_on": "er-ensemble-40"},
     # one launch of each phase on the 10M-node graph: phase 1 492.12 MB read +
     # 661.91 MB written, phase 2 1173.79 MB read + 34.77 MB written

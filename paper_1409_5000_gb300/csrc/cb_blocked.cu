@@ -74,9 +74,10 @@ __device__ __forceinline__ void load_batch(const uint32_t *cl, uint32_t e, uint3
 // Per (segment, warp): the stream's step count T, the smallest even T with
 // 32 T >= the warp's elements in the column block, 2 T >= the most elements
 // of one lane, and T >= the most elements of one row (see the layout in the
-// header).  CTAs of kFillThreads lanes of a tile; per-(block, lane) counters
-// in shared memory.  Columns of a row are sorted, so a row's elements in one
-// block are one run of its walk.
+// header), and each lane's element count per block, kept for the fill.
+// CTAs of kFillThreads lanes of a tile; per-(block, lane) counters in shared
+// memory.  Columns of a row are sorted, so a row's elements in one block are
+// one run of its walk.
 __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *inst,
                                                               const uint32_t *btile_inst,
                                                               const uint64_t *bseg_base,
@@ -147,9 +148,9 @@ __global__ void __launch_bounds__(kFillThreads) bcount_kernel(const InstDesc *in
 // step j mod T, lane j / T, and the positions past the warp's last element
 // (j from its count to 32 T) take the lane's padding element.  The streams
 // are then written a batch of blocks at a time: each warp assembles its
-// streams of the batch in shared memory (a second walk, resumed where the
-// previous batch stopped -- the columns of a row are sorted) and copies them
-// out with coalesced 16-byte stores.  A block whose stream does not fit the
+// streams of the batch in shared memory (one walk over the rows, each row
+// resumed where the previous batch stopped -- the columns of a row are
+// sorted) and copies them out with coalesced 16-byte stores.  A block whose stream does not fit the
 // staging area is written element by element.
 constexpr uint32_t kStageWords = 2048;  // staging u32 words per warp
 
