@@ -415,7 +415,9 @@ class GraphSet:
     def __init__(self, graphs, validate=False, stream=None, csr_only=False, two_phase=False,
                  path=None):
         """`graphs`: sequence of objects with .n, .row_ptr, .col (numpy uint32
-        arrays, host or pinned torch tensors, or CUDA torch tensors).
+        arrays, host or pinned torch tensors, or CUDA torch tensors; CUDA
+        arrays hold exactly nnz columns, and the upload reads them in order on
+        `stream`, so they may still be in the making there).
         `csr_only`: no column-blocked or two-phase format (CB_CSR_ONLY).
         `two_phase`: the two-phase format for every realisation (CB_TWO_PHASE).
         `path`: FP32 SpMV path (CB_PATH_*; default CB_PATH_AUTO)."""
@@ -440,7 +442,8 @@ class GraphSet:
             rps.append(_ptr(rp))
             cols.append(_ptr(c))
         n = [int(g.n) for g in graphs]
-        nnz = [int(g.row_ptr[-1]) for g in graphs]
+        # no read of a device row_ptr here: it would wait for `stream`'s work
+        nnz = [int(g.col.numel()) if d else int(g.row_ptr[-1]) for g, d in zip(graphs, dev)]
         self.n = n
         self.nnz = nnz
         self.n_max = max(n)

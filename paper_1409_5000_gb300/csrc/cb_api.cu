@@ -523,8 +523,9 @@ struct UploadCopies {
 };
 }  // namespace
 
-cudaError_t cb::stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
-  if (!bytes) return cudaSuccess;
+// A pinned block of `bytes` from the arena, valid until the current upload
+// ends (nullptr if pinned memory cannot be had).
+static char *stage_reserve(size_t bytes) {
   std::lock_guard<std::recursive_mutex> lk(g_stage_mu);
   const size_t need = (bytes + 255) & ~(size_t)255;
   while (g_stage.ci < g_stage.chunks.size() && g_stage.off + need > g_stage.chunks[g_stage.ci].second) {
@@ -534,13 +535,20 @@ cudaError_t cb::stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t
   if (g_stage.ci == g_stage.chunks.size()) {
     const size_t sz = std::max<size_t>(need, (size_t)16 << 20);
     char *p = nullptr;
-    const cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&p), sz);
-    if (e != cudaSuccess) return e;
+    if (cudaMallocHost(reinterpret_cast<void **>(&p), sz) != cudaSuccess) return nullptr;
     g_stage.chunks.push_back({p, sz});
     g_stage.off = 0;
   }
   char *p = g_stage.chunks[g_stage.ci].first + g_stage.off;
   g_stage.off += need;
+  return p;
+}
+
+cudaError_t cb::stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return cudaSuccess;
+  std::lock_guard<std::recursive_mutex> lk(g_stage_mu);
+  char *p = stage_reserve(bytes);
+  if (!p) return cudaErrorMemoryAllocation;
   std::memcpy(p, src, bytes);
   return cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, s);
 }
@@ -570,9 +578,36 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   h->n_inst = n_inst;
   h->inst.resize(n_inst);
 
-  // host views of row_ptr (device uploads copy them back for the tables)
-  std::vector<std::vector<uint32_t>> rp_host(dev ? n_inst : 0);
-  auto rp_of = [&](uint32_t r) -> const uint32_t * { return dev ? rp_host[r].data() : row_ptr[r]; };
+  // host views of row_ptr: device uploads read all of them back into one
+  // pinned block (one copy per realisation, one wait) for the tables
+  std::vector<const uint32_t *> rp_view(row_ptr, row_ptr + n_inst);
+  if (dev) {
+    uint64_t words = 0;
+    for (uint32_t r = 0; r < n_inst; ++r) {
+      if (n[r] == 0 || !row_ptr[r]) {
+        delete h;
+        return set_error(CB_ERR_ARG, "cb_graph_upload: realisation with n = 0 or null array");
+      }
+      words += (uint64_t)n[r] + 1;
+    }
+    uint32_t *hb = reinterpret_cast<uint32_t *>(stage_reserve(words * 4));
+    if (!hb) {
+      delete h;
+      return set_error(CB_ERR_OOM, "cb_graph_upload: no pinned host memory to read row_ptr into");
+    }
+    cudaError_t e = cudaSuccess;
+    uint64_t o = 0;
+    for (uint32_t r = 0; r < n_inst && e == cudaSuccess; o += (uint64_t)n[r] + 1, ++r) {
+      rp_view[r] = hb + o;
+      e = cudaMemcpyAsync(hb + o, row_ptr[r], ((size_t)n[r] + 1) * 4, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_error(e, "cb_graph_upload: read row_ptr");
+    }
+  }
+  auto rp_of = [&](uint32_t r) -> const uint32_t * { return rp_view[r]; };
 
   uint64_t node_off = 0, edge_off = 0, rp_off = 0;
   uint32_t tile_off = 0, fin_off = 0, slot_off = 0, group_off = 0;
@@ -584,15 +619,6 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     if (nnz[r] >= 0xffffffffull) {
       delete h;
       return set_error(CB_ERR_ARG, "cb_graph_upload: nnz of one realisation must be < 2^32");
-    }
-    if (dev) {
-      rp_host[r].resize((size_t)n[r] + 1);
-      cudaError_t e = cudaMemcpy(rp_host[r].data(), row_ptr[r], ((size_t)n[r] + 1) * 4,
-                                 cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) {
-        delete h;
-        return cuda_error(e, "cb_graph_upload: read row_ptr");
-      }
     }
     const uint32_t *rp = rp_of(r);
     if (rp[0] != 0 || rp[n[r]] != nnz[r]) {

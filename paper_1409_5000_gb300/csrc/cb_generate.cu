@@ -92,17 +92,32 @@ __device__ __forceinline__ uint32_t ba_target(const GenArgs &a, uint32_t r, uint
   }
 }
 
+// Realisation of draw g (g < D): draw_off[r] <= g < draw_off[r + 1].
+__device__ __forceinline__ uint32_t draw_owner(const GenArgs &a, uint64_t g) {
+  uint32_t lo = 0, hi = a.n_inst;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a.draw_off[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Realisation of row i: node_off[r] <= i < node_off[r + 1].
+__device__ __forceinline__ uint32_t node_owner(const GenArgs &a, uint64_t i) {
+  uint32_t lo = 0, hi = a.n_inst;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a.node_off[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // Work item g -> realisation r and pair (u, v); false when it makes no edge.
-__device__ __forceinline__ bool gen_item(const GenArgs &a, uint64_t g, uint32_t &r, uint32_t &u,
-                                         uint32_t &v) {
-  const uint64_t D = a.draw_off[a.n_inst];
+// A draw (g < D) comes in with r already its owner; a target-edge item
+// (g >= D) sets r here.
+__device__ __forceinline__ bool gen_item(const GenArgs &a, uint64_t g, uint64_t D, uint32_t &r,
+                                         uint32_t &u, uint32_t &v) {
   if (g < D) {
-    uint32_t lo = 0, hi = a.n_inst;  // draw_off[lo] <= g < draw_off[hi]
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (a.draw_off[mid] <= g) lo = mid; else hi = mid;
-    }
-    r = lo;
     const uint64_t t = g - a.draw_off[r];
     const uint64_t nr = a.n[r];
     if (a.kind == kGenER) {
@@ -130,26 +145,72 @@ __device__ __forceinline__ bool gen_item(const GenArgs &a, uint64_t g, uint32_t 
   return u != v;
 }
 
+// The count and fill kernels give each CTA one chunk of kGenChunk
+// consecutive work items (thread t takes items base + j * kGenThreads + t).
+// CTAs are dispatched in order, so the items in flight belong to one or two
+// realisations and the rows they touch (the realisation's degree or cursor
+// array and its entry range) stay in L2 while they are written.  The owner
+// of a thread's first draw is found by bisection; later items move it on.
+constexpr uint32_t kGenItems = 8;
+constexpr uint32_t kGenChunk = kGenThreads * kGenItems;
+
+__device__ __forceinline__ void advance_owner(const GenArgs &a, uint64_t g, uint64_t D,
+                                              uint32_t &r) {
+  if (g < D)
+    while (a.draw_off[r + 1] <= g) ++r;
+}
+
 __global__ void __launch_bounds__(kGenThreads) gen_count_kernel(GenArgs a, uint32_t *deg) {
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < a.items;
-       g += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t r, u, v;
-    if (!gen_item(a, g, r, u, v)) continue;
+  const uint64_t D = a.draw_off[a.n_inst];
+  const uint64_t g0 = blockIdx.x * (uint64_t)kGenChunk + threadIdx.x;
+  uint32_t r0 = g0 < D ? draw_owner(a, g0) : 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kGenItems; ++j) {
+    const uint64_t g = g0 + (uint64_t)j * kGenThreads;
+    if (g >= a.items) break;
+    advance_owner(a, g, D, r0);
+    uint32_t r = r0, u, v;
+    if (!gen_item(a, g, D, r, u, v)) continue;
     atomicAdd(deg + a.node_off[r] + u, 1u);
     atomicAdd(deg + a.node_off[r] + v, 1u);
   }
 }
 
-// cursor[row] counts from the realisation's first entry (32-bit atomics)
-__global__ void __launch_bounds__(kGenThreads) gen_fill_kernel(GenArgs a, const uint64_t *ebase,
-                                                               uint32_t *cursor, uint32_t *raw) {
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < a.items;
-       g += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t r, u, v;
-    if (!gen_item(a, g, r, u, v)) continue;
-    const uint64_t eb = ebase[r];
-    raw[eb + atomicAdd(cursor + a.node_off[r] + u, 1u)] = v;
-    raw[eb + atomicAdd(cursor + a.node_off[r] + v, 1u)] = u;
+// cursor[row] counts from the realisation's first entry (32-bit atomics).
+// All of a thread's cursor increments are issued before its first store, so
+// up to 2 kGenItems returning atomics are in flight per thread.
+__global__ void __launch_bounds__(kGenThreads) gen_fill_kernel(GenArgs a,
+                                                               const uint64_t *__restrict__ ebase,
+                                                               uint32_t *__restrict__ cursor,
+                                                               uint32_t *__restrict__ raw) {
+  const uint64_t D = a.draw_off[a.n_inst];
+  const uint64_t g0 = blockIdx.x * (uint64_t)kGenChunk + threadIdx.x;
+  uint32_t r0 = g0 < D ? draw_owner(a, g0) : 0;
+  uint32_t rr[kGenItems], uu[kGenItems], vv[kGenItems], pu[kGenItems], pv[kGenItems];
+  uint32_t live = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kGenItems; ++j) {
+    const uint64_t g = g0 + (uint64_t)j * kGenThreads;
+    rr[j] = uu[j] = vv[j] = 0;
+    if (g >= a.items) continue;
+    advance_owner(a, g, D, r0);
+    rr[j] = r0;
+    if (gen_item(a, g, D, rr[j], uu[j], vv[j])) live |= 1u << j;
+  }
+#pragma unroll
+  for (uint32_t j = 0; j < kGenItems; ++j) {
+    pu[j] = pv[j] = 0;
+    if (!(live >> j & 1u)) continue;
+    const uint64_t row0 = a.node_off[rr[j]];
+    pu[j] = atomicAdd(cursor + row0 + uu[j], 1u);
+    pv[j] = atomicAdd(cursor + row0 + vv[j], 1u);
+  }
+#pragma unroll
+  for (uint32_t j = 0; j < kGenItems; ++j) {
+    if (!(live >> j & 1u)) continue;
+    const uint64_t eb = ebase[rr[j]];
+    raw[eb + pu[j]] = vv[j];
+    raw[eb + pv[j]] = uu[j];
   }
 }
 
@@ -157,21 +218,39 @@ __global__ void __launch_bounds__(kGenThreads) gen_cursor_kernel(GenArgs a, cons
                                                                  const uint64_t *ebase,
                                                                  uint32_t *cursor, uint64_t rows) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t lo = 0, hi = a.n_inst;  // node_off[lo] <= i < node_off[hi]
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (a.node_off[mid] <= i) lo = mid; else hi = mid;
-    }
-    cursor[i] = (uint32_t)(off[i] - ebase[lo]);
-  }
+       i += (uint64_t)gridDim.x * blockDim.x)
+    cursor[i] = (uint32_t)(off[i] - ebase[node_owner(a, i)]);
 }
 
-// Sort each row ascending and drop repeats, one warp per row; deg[i] becomes
-// the number of distinct columns.  Rows of up to 64 entries are sorted in
-// registers by a bitonic network over shuffles (entry e of the row sits in
-// lane e % 32, register e / 32; unused slots hold UINT32_MAX); longer rows
-// (rare: degrees are ~Poisson) fall back to an insertion sort by lane 0.
+// Sort each row ascending and drop repeats; deg[i] becomes the number of
+// distinct columns.  A warp takes kRowChunk consecutive rows, whose entries
+// are one contiguous range of raw.  When that range fits kSortStage words
+// the warp copies it into shared memory and each lane sorts its own row of
+// up to 32 entries in registers (a fixed bitonic network, padded with
+// UINT32_MAX), writes the distinct values to the front of the row's segment
+// and the warp copies the range back; entries after a row's distinct count
+// are left as they were (only deg[i] of them are read later).  Longer rows,
+// and every row of a chunk that does not fit, take the warp path below.
+constexpr uint32_t kRowChunk = 32;
+constexpr uint32_t kSortStage = 1024;  // words of shared memory per warp
+
+__device__ __forceinline__ void bitonic32_regs(uint32_t (&v)[32]) {
+#pragma unroll
+  for (uint32_t k = 2; k <= 32; k <<= 1)
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (uint32_t i = 0; i < 32; ++i) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const uint32_t lo = min(v[i], v[l]), hi = max(v[i], v[l]);
+          const bool up = (i & k) == 0;
+          v[i] = up ? lo : hi;
+          v[l] = up ? hi : lo;
+        }
+      }
+}
+
 __device__ __forceinline__ uint32_t bitonic_cx(uint32_t x, uint32_t y, bool keep_min) {
   return keep_min ? min(x, y) : max(x, y);
 }
@@ -183,106 +262,167 @@ __device__ __forceinline__ uint32_t bitonic_cx(uint32_t x, uint32_t y, bool keep
 // keep a serial insertion sort.
 constexpr uint32_t kSortMid = 1024, kSortBig = 32768;
 
-__global__ void __launch_bounds__(kGenThreads) gen_sort_kernel(const uint64_t *off, uint32_t *raw,
-                                                               uint32_t *deg, uint64_t rows,
-                                                               uint32_t *long_rows,
-                                                               uint32_t *long_cnt) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < rows;
-       i += warps) {
-    uint32_t *p = raw + off[i];
-    const uint32_t d = (uint32_t)(off[i + 1] - off[i]);
-    if (d > 64 && d <= kSortBig) {  // a CTA sorts it
-      if (lane == 0) {
-        if (d <= kSortMid)
-          long_rows[atomicAdd(&long_cnt[0], 1u)] = (uint32_t)i;
-        else
-          long_rows[rows - 1 - atomicAdd(&long_cnt[1], 1u)] = (uint32_t)i;
-      }
-      continue;
+// The warp path for row i (entries p[0, d)): up to 64 entries are sorted
+// across the warp by a bitonic network over shuffles (entry e in lane
+// e % 32, register e / 32), as wide as the next power of two of d.  Returns
+// the row's degree to record (its raw length when a CTA sorts it later).
+__device__ uint32_t sort_row_warp(uint32_t *p, uint32_t d, uint64_t i, uint64_t rows,
+                                  uint32_t *long_rows, uint32_t *long_cnt, uint32_t lane) {
+  if (d > 64 && d <= kSortBig) {  // a CTA sorts it and sets its degree
+    if (lane == 0) {
+      if (d <= kSortMid)
+        long_rows[atomicAdd(&long_cnt[0], 1u)] = (uint32_t)i;
+      else
+        long_rows[rows - 1 - atomicAdd(&long_cnt[1], 1u)] = (uint32_t)i;
     }
-    if (d > 64) {
-      uint32_t w = 0;
-      if (lane == 0) {
-        for (uint32_t q = 1; q < d; ++q) {
-          const uint32_t x = p[q];
-          uint32_t s = q;
-          while (s > 0 && p[s - 1] > x) {
-            p[s] = p[s - 1];
-            --s;
-          }
-          p[s] = x;
-        }
-        for (uint32_t q = 0; q < d; ++q)
-          if (w == 0 || p[q] != p[w - 1]) p[w++] = p[q];
-        deg[i] = w;
-      }
-      __syncwarp();
-      continue;
-    }
-    uint32_t x0 = lane < d ? p[lane] : 0xffffffffu;
-    uint32_t x1 = lane + 32 < d ? p[lane + 32] : 0xffffffffu;
-    const uint32_t kmax = d > 32 ? 64u : 32u;
-    for (uint32_t k = 2; k <= kmax; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        if (j == 32) {  // partner is the other register of the same lane (k = 64)
-          const uint32_t lo = min(x0, x1), hi = max(x0, x1);
-          x0 = lo;
-          x1 = hi;
-          continue;
-        }
-        const bool lower = (lane & j) == 0;
-        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, x0, j);
-        x0 = bitonic_cx(x0, y0, lower == ((lane & k) == 0));
-        if (kmax == 64) {
-          const uint32_t y1 = __shfl_xor_sync(0xffffffffu, x1, j);
-          x1 = bitonic_cx(x1, y1, lower == (((lane + 32) & k) == 0));
-        }
-      }
-    }
-    // distinct values: keep an entry unless it equals its predecessor
-    const uint32_t pr0 = __shfl_up_sync(0xffffffffu, x0, 1);
-    const uint32_t pr1 = __shfl_up_sync(0xffffffffu, x1, 1);
-    const uint32_t last0 = __shfl_sync(0xffffffffu, x0, 31);
-    const bool k0 = lane < d && (lane == 0 || x0 != pr0);
-    const bool k1 = lane + 32 < d && (lane == 0 ? x1 != last0 : x1 != pr1);
-    const uint32_t b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
-    const uint32_t lt = (1u << lane) - 1u;
-    __syncwarp();  // every lane has read its entries before any is overwritten
-    if (k0) p[__popc(b0 & lt)] = x0;
-    if (k1) p[__popc(b0) + __popc(b1 & lt)] = x1;
-    if (lane == 0) deg[i] = __popc(b0) + __popc(b1);
+    return d;
   }
+  if (d > 64) {
+    uint32_t w = 0;
+    if (lane == 0) {
+      for (uint32_t q = 1; q < d; ++q) {
+        const uint32_t x = p[q];
+        uint32_t s = q;
+        while (s > 0 && p[s - 1] > x) {
+          p[s] = p[s - 1];
+          --s;
+        }
+        p[s] = x;
+      }
+      for (uint32_t q = 0; q < d; ++q)
+        if (w == 0 || p[q] != p[w - 1]) p[w++] = p[q];
+    }
+    return __shfl_sync(0xffffffffu, w, 0);
+  }
+  uint32_t x0 = lane < d ? p[lane] : 0xffffffffu;
+  uint32_t x1 = lane + 32 < d ? p[lane + 32] : 0xffffffffu;
+  uint32_t kmax = 2;
+  while (kmax < d) kmax <<= 1;
+  for (uint32_t kk = 2; kk <= kmax; kk <<= 1) {
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      if (j == 32) {  // partner is the other register of the same lane (kk = 64)
+        const uint32_t lo = min(x0, x1), hi = max(x0, x1);
+        x0 = lo;
+        x1 = hi;
+        continue;
+      }
+      const bool lower = (lane & j) == 0;
+      const uint32_t y0 = __shfl_xor_sync(0xffffffffu, x0, j);
+      x0 = bitonic_cx(x0, y0, lower == ((lane & kk) == 0));
+      if (kmax == 64) {
+        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+        x1 = bitonic_cx(x1, y1, lower == (((lane + 32) & kk) == 0));
+      }
+    }
+  }
+  // distinct values: keep an entry unless it equals its predecessor
+  const uint32_t pr0 = __shfl_up_sync(0xffffffffu, x0, 1);
+  const uint32_t pr1 = __shfl_up_sync(0xffffffffu, x1, 1);
+  const uint32_t last0 = __shfl_sync(0xffffffffu, x0, 31);
+  const bool k0 = lane < d && (lane == 0 || x0 != pr0);
+  const bool k1 = lane + 32 < d && (lane == 0 ? x1 != last0 : x1 != pr1);
+  const uint32_t b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+  const uint32_t lt = (1u << lane) - 1u;
+  __syncwarp();  // every lane has read its entries before any is overwritten
+  if (k0) p[__popc(b0 & lt)] = x0;
+  if (k1) p[__popc(b0) + __popc(b1 & lt)] = x1;
+  return __popc(b0) + __popc(b1);
+}
+
+__global__ void __launch_bounds__(kGenThreads) gen_sort_kernel(const uint64_t *__restrict__ off,
+                                                               uint32_t *__restrict__ raw,
+                                                               uint32_t *__restrict__ deg,
+                                                               uint64_t rows,
+                                                               uint32_t *__restrict__ long_rows,
+                                                               uint32_t *__restrict__ long_cnt) {
+  __shared__ uint32_t s_stage[kGenThreads / 32][kSortStage];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t i0 =
+      (blockIdx.x * (uint64_t)(kGenThreads / 32) + (threadIdx.x >> 5)) * kRowChunk;
+  if (i0 >= rows) return;
+  const uint32_t nr = (uint32_t)(rows - i0 < kRowChunk ? rows - i0 : kRowChunk);
+  const uint64_t o_lane = lane < nr ? off[i0 + lane] : 0, o_end = off[i0 + nr];
+  const uint64_t o_next = __shfl_sync(0xffffffffu, o_lane, (lane + 1) & 31);
+  const uint32_t d_lane = lane < nr ? (uint32_t)((lane + 1 < nr ? o_next : o_end) - o_lane) : 0;
+  const uint64_t base = __shfl_sync(0xffffffffu, o_lane, 0);
+  const uint64_t total = o_end - base;
+  uint32_t my_deg = d_lane;
+  uint32_t warp_rows;  // rows left to the warp path
+  if (total <= kSortStage) {
+    uint32_t *sw = s_stage[threadIdx.x >> 5];
+    for (uint32_t q = lane; q < total; q += 32) sw[q] = raw[base + q];
+    __syncwarp();
+    if (d_lane <= 32 && lane < nr) {
+      uint32_t *seg = sw + (o_lane - base);
+      uint32_t v[32];
+#pragma unroll
+      for (uint32_t q = 0; q < 32; ++q) v[q] = q < d_lane ? seg[q] : 0xffffffffu;
+      bitonic32_regs(v);
+      uint32_t w = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < 32; ++q)
+        if (v[q] != 0xffffffffu && (q == 0 || v[q] != v[q - 1])) seg[w++] = v[q];
+      my_deg = w;
+    }
+    __syncwarp();
+    for (uint32_t q = lane; q < total; q += 32) raw[base + q] = sw[q];
+    __syncwarp();  // the copy-back is visible to the warp path's loads
+    warp_rows = __ballot_sync(0xffffffffu, d_lane > 32);
+  } else {
+    warp_rows = __ballot_sync(0xffffffffu, lane < nr);
+  }
+  while (warp_rows) {
+    const uint32_t k = __ffs(warp_rows) - 1;
+    warp_rows &= warp_rows - 1;
+    const uint64_t st = __shfl_sync(0xffffffffu, o_lane, k);
+    const uint32_t d = __shfl_sync(0xffffffffu, d_lane, k);
+    const uint32_t w = sort_row_warp(raw + st, d, i0 + k, rows, long_rows, long_cnt, lane);
+    if (lane == k) my_deg = w;
+  }
+  if (lane < nr) deg[i0 + lane] = my_deg;
 }
 
 // Compact the distinct columns into the concatenated CSR and write each
-// realisation's local row_ptr (n_r + 1 entries at node_off[r] + r).
-__global__ void __launch_bounds__(kGenThreads) gen_compact_kernel(GenArgs a, const uint64_t *off,
-                                                                  const uint32_t *raw,
-                                                                  const uint64_t *off2,
-                                                                  uint32_t *col, uint32_t *rp,
-                                                                  uint64_t rows) {
+// realisation's local row_ptr (n_r + 1 entries at node_off[r] + r).  A warp
+// takes kRowChunk consecutive rows; lane j reads the offsets of row i0 + j
+// and writes its row_ptr entry, then the rows are copied four at a time
+// (all four rows' loads before their stores).
+__global__ void __launch_bounds__(kGenThreads) gen_compact_kernel(
+    GenArgs a, const uint64_t *__restrict__ off, const uint32_t *__restrict__ raw,
+    const uint64_t *__restrict__ off2, uint32_t *__restrict__ col, uint32_t *__restrict__ rp,
+    uint64_t rows) {
   const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < rows;
-       i += warps) {
-    uint32_t lo = 0, hi = a.n_inst;  // node_off[lo] <= i < node_off[hi]
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (a.node_off[mid] <= i) lo = mid; else hi = mid;
+  const uint64_t i0 =
+      (blockIdx.x * (uint64_t)(kGenThreads / 32) + (threadIdx.x >> 5)) * kRowChunk;
+  if (i0 >= rows) return;
+  const uint32_t nr = (uint32_t)(rows - i0 < kRowChunk ? rows - i0 : kRowChunk);
+  uint64_t src = 0, dst = 0;
+  uint32_t d = 0;
+  if (lane < nr) {
+    const uint64_t i = i0 + lane;
+    src = off[i];
+    dst = off2[i];
+    const uint64_t dst_end = off2[i + 1];
+    d = (uint32_t)(dst_end - dst);
+    const uint32_t r = node_owner(a, i);
+    const uint64_t row0 = a.node_off[r], base = off2[row0];
+    rp[row0 + r + (i - row0)] = (uint32_t)(dst - base);
+    if (i + 1 == a.node_off[r + 1]) rp[row0 + r + (i - row0) + 1] = (uint32_t)(dst_end - base);
+  }
+  for (uint32_t k = 0; k < nr; k += 4) {
+    uint64_t sk[4], dk[4];
+    uint32_t nk[4], val[4];
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      sk[q] = __shfl_sync(0xffffffffu, src, k + q);
+      dk[q] = __shfl_sync(0xffffffffu, dst, k + q);
+      nk[q] = __shfl_sync(0xffffffffu, d, k + q);  // 0 for rows past nr
+      val[q] = lane < nk[q] ? raw[sk[q] + lane] : 0u;
     }
-    const uint32_t r = lo;
-    const uint64_t base = off2[a.node_off[r]];
-    const uint64_t d = off2[i + 1] - off2[i];
-    const uint32_t *src = raw + off[i];
-    uint32_t *dst = col + off2[i];
-    for (uint64_t q = lane; q < d; q += 32) dst[q] = src[q];
-    if (lane == 0) {
-      const uint64_t local = i - a.node_off[r];
-      rp[a.node_off[r] + r + local] = (uint32_t)(off2[i] - base);
-      if (i + 1 == a.node_off[r + 1])
-        rp[a.node_off[r] + r + local + 1] = (uint32_t)(off2[i + 1] - base);
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      if (lane < nk[q]) col[dk[q] + lane] = val[q];
+      for (uint32_t t = lane + 32; t < nk[q]; t += 32) col[dk[q] + t] = raw[sk[q] + t];
     }
   }
 }
@@ -396,7 +536,12 @@ uint32_t grid_for(uint64_t work) {
   return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(g, 1), 152ull * 16);
 }
 
-// device buffers of one generation call, freed on every exit path
+// one CTA per `per_cta` units of work (the chunked kernels; no grid-stride loop)
+uint64_t chunk_grid(uint64_t work, uint64_t per_cta) {
+  return std::max<uint64_t>((work + per_cta - 1) / per_cta, 1);
+}
+constexpr uint64_t kRowsPerCta = kRowChunk * (kGenThreads / 32);
+
 // One CTA per listed row: bitonic sort of the row (padded with UINT32_MAX
 // to a power of two) in shared memory, then thread 0 writes the distinct
 // values back and sets the row's degree.  rows_from_end: the row list is
@@ -436,6 +581,7 @@ __global__ void gen_sort_block_kernel(const uint64_t *off, uint32_t *raw, uint32
   }
 }
 
+// device buffers of one generation call, freed on every exit path
 struct GenBuffers {
   std::vector<void *> ptrs;
   template <typename P>
@@ -473,6 +619,7 @@ static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const u
   const uint64_t rows = node_off[n_inst];
   if (rows >= 0xffffffffull) return fail("need fewer than 2^32 nodes over all realisations");
   const uint64_t items = draw_off[n_inst] + (uint64_t)n_inst * n_tedges;
+  if (chunk_grid(items, kGenChunk) >= (1ull << 31)) return fail("too many draws");
 
   GenBuffers B;
   cudaError_t e = cudaSuccess;
@@ -515,7 +662,7 @@ static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const u
   a.n_tedges = n_tedges;
   a.items = items;
   if (e == cudaSuccess) {
-    gen_count_kernel<<<grid_for(items), kGenThreads, 0, s>>>(a, deg);
+    gen_count_kernel<<<(uint32_t)chunk_grid(items, kGenChunk), kGenThreads, 0, s>>>(a, deg);
     chk(cudaGetLastError());
     chk(exclusive_scan(deg, rows, off, bsum, s));
   }
@@ -528,10 +675,11 @@ static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const u
   if (e == cudaSuccess) {
     gather_bounds_kernel<<<(n_inst + 256) / 256, 256, 0, s>>>(off, d_node_off, n_inst, ebase);
     gen_cursor_kernel<<<grid_for(rows), kGenThreads, 0, s>>>(a, off, ebase, cursor, rows);
-    gen_fill_kernel<<<grid_for(items), kGenThreads, 0, s>>>(a, ebase, cursor, raw);
+    gen_fill_kernel<<<(uint32_t)chunk_grid(items, kGenChunk), kGenThreads, 0, s>>>(a, ebase, cursor,
+                                                                                raw);
     chk(cudaMemsetAsync(long_cnt, 0, 8, s));
-    gen_sort_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(off, raw, deg, rows, long_rows,
-                                                                long_cnt);
+    gen_sort_kernel<<<(uint32_t)chunk_grid(rows, kRowsPerCta), kGenThreads, 0, s>>>(
+        off, raw, deg, rows, long_rows, long_cnt);
     chk(cudaGetLastError());
     uint32_t nl[2] = {0, 0};
     chk(cudaMemcpyAsync(nl, long_cnt, 8, cudaMemcpyDeviceToHost, s));
@@ -563,7 +711,8 @@ static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const u
   chk(B.alloc(&col, std::max<uint64_t>(hb[n_inst], 1)));
   chk(B.alloc(&rp, rows + n_inst));
   if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": allocate CSR").c_str());
-  gen_compact_kernel<<<grid_for(rows * 32), kGenThreads, 0, s>>>(a, off, raw, off2, col, rp, rows);
+  gen_compact_kernel<<<(uint32_t)chunk_grid(rows, kRowsPerCta), kGenThreads, 0, s>>>(
+      a, off, raw, off2, col, rp, rows);
   chk(cudaGetLastError());
   chk(cudaStreamSynchronize(s));  // the upload reads row_ptr back with a plain copy
   if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": compact").c_str());

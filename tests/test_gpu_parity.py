@@ -320,6 +320,27 @@ def test_unsorted_rows_rejected(B):
         B.GraphSet([_G(g.n, rp, col)])
 
 
+def test_upload_from_device_arrays(B):
+    """CSR arrays already on the device (CB_DEVICE_PTRS), still being copied
+    there by work queued on the upload's stream: the handle gives
+    bit-identical scores to the upload of the same graphs from host arrays."""
+    ens = synth.er_ensemble_uneven(n_inst=7, n_lo=2_000, n_hi=40_000, config=313)
+    with B.GraphSet(ens.graphs, path=FORMATS) as gh:
+        ref = B.ensemble_scores(gh, 25, B.CB_FP32)[1].cpu().numpy()
+    st = torch.cuda.Stream()
+    host = [(torch.from_numpy(g.row_ptr.astype(np.uint32).view(np.int32)).pin_memory(),
+             torch.from_numpy(g.col.astype(np.uint32).view(np.int32)).pin_memory())
+            for g in ens.graphs]
+    with torch.cuda.stream(st):
+        torch.cuda._sleep(20_000_000)  # the copies below land well after the call returns
+        dev = [_G(g.n, rp.to("cuda", non_blocking=True), cl.to("cuda", non_blocking=True))
+               for g, (rp, cl) in zip(ens.graphs, host)]
+    with B.GraphSet(dev, stream=st, path=FORMATS) as gd:
+        got = B.ensemble_scores(gd, 25, B.CB_FP32, stream=st)[1]
+        st.synchronize()
+        assert np.array_equal(got.cpu().numpy(), ref)
+
+
 def test_upload_concurrent_with_compute(B):
     """An upload on a second host thread and stream while this thread runs an
     ensemble (the double-buffered end-to-end pattern): both results are
