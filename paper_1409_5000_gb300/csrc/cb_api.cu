@@ -523,9 +523,7 @@ struct UploadCopies {
 };
 }  // namespace
 
-// A pinned block of `bytes` from the arena, valid until the current upload
-// ends (nullptr if pinned memory cannot be had).
-static char *stage_reserve(size_t bytes) {
+char *cb::stage_reserve(size_t bytes) {
   std::lock_guard<std::recursive_mutex> lk(g_stage_mu);
   const size_t need = (bytes + 255) & ~(size_t)255;
   while (g_stage.ci < g_stage.chunks.size() && g_stage.off + need > g_stage.chunks[g_stage.ci].second) {
@@ -660,6 +658,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   };
   chk(dalloc(&h->col, edge_off + 4));
   chk(dalloc(&h->row_ptr, rp_off));
+  chk(dalloc(&h->d_inst, n_inst));
   UploadCopies cp;
   chk(cp.start(s));
   if (e == cudaSuccess) {
@@ -680,6 +679,19 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     free_graph_arrays(h);
     delete h;
     return cuda_error(e, "cb_graph_upload: allocate / copy");
+  }
+  // The column-blocked format needs only the sizes and the device arrays:
+  // its count and fill passes are queued first, and the host's scans of
+  // row_ptr below run while the device builds it.
+  BlockedBuild bb;
+  int rc = blocked_count(h, s, cp.groups, bb);
+  if (rc == CB_OK) rc = blocked_fill(h, s, bb);
+  if (rc != CB_OK) {
+    cp.finish();
+    free_blocked(h);
+    free_graph_arrays(h);
+    delete h;
+    return rc;
   }
   // heavy rows (degree > kHeavyDeg), in realisation and row order; the row
   // scans run in parallel over realisations
@@ -746,8 +758,8 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   h->total_fin = fin_off;
   h->total_heavy = (uint32_t)h->heavy.size();
   h->total_chunks = chunk_off;
-  h->total_slots = std::max(slot_off, fslot);
-  h->total_groups = std::max(group_off, fgroup);
+  h->total_slots = std::max({h->total_slots, slot_off, fslot});  // the blocked plans are counted in
+  h->total_groups = std::max({h->total_groups, group_off, fgroup});
   uint64_t nsum = 0;
   for (uint32_t r = 0; r < n_inst; ++r) nsum += n[r];
   h->lanes = pick_lanes((double)edge_off / (double)nsum);
@@ -774,7 +786,6 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   for (uint32_t q = 0; q < h->total_heavy; ++q)
     for (uint32_t c = 0; c < h->heavy[q].n_chunks; ++c) chunk_heavy[h->heavy[q].chunk_base + c] = q;
 
-  chk(dalloc(&h->d_inst, n_inst));
   chk(dalloc(&h->d_tile_inst, tile_inst.size()));
   chk(dalloc(&h->d_tile_rows, tile_rows.size()));
   chk(dalloc(&h->d_fin_inst, fin_inst.size()));
@@ -782,6 +793,7 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   chk(dalloc(&h->d_chunk_heavy, chunk_heavy.size()));
   if (e != cudaSuccess) {
     cp.finish();
+    free_blocked(h);
     free_graph_arrays(h);
     delete h;
     return cuda_error(e, "cb_graph_upload: allocate");
@@ -794,13 +806,14 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   chk(stage_h2d(h->d_chunk_heavy, chunk_heavy.data(), chunk_heavy.size() * 4, s));
   if (e != cudaSuccess) {
     cp.finish();
+    free_blocked(h);
     free_graph_arrays(h);
     delete h;
     return cuda_error(e, "cb_graph_upload: copy");
   }
   std::vector<const uint32_t *> rpv(n_inst);
   for (uint32_t r = 0; r < n_inst; ++r) rpv[r] = rp_of(r);
-  int rc = build_blocked(h, rpv, s, cp.groups);
+  rc = blocked_long_rows(h, rpv, s);
   if (rc == CB_OK) rc = build_twophase(h, rpv, s, cp.groups, h->force_pb);
   if (rc == CB_OK) {  // every copy has landed before the handle is returned
     for (const CopyGroup &g : cp.groups) chk(cudaStreamWaitEvent(s, g.ev, 0));

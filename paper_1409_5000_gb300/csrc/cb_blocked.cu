@@ -331,34 +331,15 @@ void free_blocked(cb_graph *h) {
   h->total_bseg = 0;
 }
 
-int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
-                  const std::vector<CopyGroup> &groups) {
-  NvtxRange nvtx_range("column-blocked format");
+int blocked_count(cb_graph *h, cudaStream_t s, const std::vector<CopyGroup> &groups,
+                  BlockedBuild &bb) {
+  NvtxRange nvtx_range("column-blocked format: count");
   if (h->csr_only) return CB_OK;
-  // which realisations, their tiles, segments and reduction plans
+  // which realisations, their tiles, segments and reduction plans (sizes only)
   uint32_t nbt = 0, slot = 0, group = 0;
   uint64_t nseg = 0;
   std::vector<uint32_t> btile_inst;
   std::vector<uint64_t> bseg_base;
-  std::vector<uint32_t> long_ptr(1, 0), long_rows;
-  // long rows per tile, scanned in parallel over realisations
-  std::vector<std::vector<uint32_t>> lrows(h->n_inst), lcount(h->n_inst);
-  parallel_for(h->n_inst, [&](uint32_t r) {
-    const InstDesc &I = h->inst[r];
-    if (h->force_pb || I.n > kBMaxBlocks * kBCol) return;
-    const uint32_t *rp = rp_host[r];
-    const uint32_t ntile = (I.n + kBTileRows - 1) / kBTileRows;
-    for (uint32_t q = 0; q < ntile; ++q) {
-      const uint32_t row0 = q * kBTileRows, row1 = std::min<uint32_t>(row0 + kBTileRows, I.n);
-      uint32_t c = 0;
-      for (uint32_t row = row0; row < row1; ++row)
-        if (rp[row + 1] - rp[row] > kBLongDeg) {
-          lrows[r].push_back(row - row0);
-          ++c;
-        }
-      lcount[r].push_back(c);
-    }
-  });
   for (uint32_t r = 0; r < h->n_inst; ++r) {
     InstDesc &I = h->inst[r];
     I.blocked = !h->force_pb && I.n <= kBMaxBlocks * kBCol ? 1u : 0u;
@@ -372,90 +353,139 @@ int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cud
       btile_inst.push_back(r);
       bseg_base.push_back(nseg);
       nseg += I.nb;
-      long_ptr.push_back(long_ptr.back() + lcount[r][q]);
     }
-    long_rows.insert(long_rows.end(), lrows[r].begin(), lrows[r].end());
     nbt += I.n_btiles;
   }
   h->total_btiles = nbt;
   h->total_bseg = nseg;
   h->total_slots = std::max(h->total_slots, slot);
   h->total_groups = std::max(h->total_groups, group);
+  if (!nbt) return CB_OK;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
-  if (nbt) {
-    const uint64_t nw = nseg * 32;
-    chk(dalloc(&h->d_btile_inst, nbt));
-    chk(dalloc(&h->d_bseg_base, nbt));
-    chk(dalloc(&h->d_bwstart, nw + 1));
-    chk(dalloc(&h->d_bwlen, nw + 1));  // + the sortedness flag of the count pass
-    chk(dalloc(&h->d_bcnt, nseg * kBThreads));
-    chk(dalloc(&h->d_bwscan, nw / 4096 + 2));  // prefix scratch
-    chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
-    chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
-    if (e != cudaSuccess) {
-      free_blocked(h);
-      return cuda_error(e, "blocked format: allocate");
-    }
-    chk(stage_h2d(h->d_btile_inst, btile_inst.data(), nbt * 4, s));
-    chk(stage_h2d(h->d_bseg_base, bseg_base.data(), nbt * 8, s));
-    chk(stage_h2d(h->d_blong_ptr, long_ptr.data(), long_ptr.size() * 4, s));
-    if (!long_rows.empty()) chk(stage_h2d(h->d_blong_rows, long_rows.data(), long_rows.size() * 4, s));
-    chk(stage_h2d(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc), s));
-    // no temporary allocation here: a free synchronises the device, which
-    // would stall an upload behind another thread's kernels
-    uint32_t *d_unsorted = h->d_bwlen + nw;
-    if (e == cudaSuccess) chk(cudaMemsetAsync(d_unsorted, 0, 4, s));
-    // count each group of realisations as soon as its columns are on the device
-    uint32_t r_begin = 0;
-    for (const CopyGroup &g : groups) {
-      chk(cudaStreamWaitEvent(s, g.ev, 0));
-      const uint32_t t0 = h->inst[r_begin].btile_base;
-      const uint32_t t1 = h->inst[g.r_end - 1].btile_base + h->inst[g.r_end - 1].n_btiles;
-      if (t1 > t0 && e == cudaSuccess)
-        bcount_kernel<<<dim3(t1 - t0, kBThreads / kFillThreads), kFillThreads, 0, s>>>(
-            h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr, h->col, h->d_bwlen, h->d_bcnt,
-            d_unsorted, t0);
-      r_begin = g.r_end;
-    }
-    chk(cudaGetLastError());
-    // stream offsets on the device: bwstart = 32 x the exclusive prefix of
-    // the lengths; only the total and the sortedness flag come back
-    if (e == cudaSuccess) chk(exclusive_scan(h->d_bwlen, nw, h->d_bwstart, h->d_bwscan, s));
-    if (e == cudaSuccess)
-      times32_kernel<<<(uint32_t)((nw + 1 + 255) / 256), 256, 0, s>>>(h->d_bwstart, nw + 1);
-    uint64_t tot = 0;
-    uint32_t unsorted = 0;
-    chk(cudaMemcpyAsync(&tot, h->d_bwstart + nw, 8, cudaMemcpyDeviceToHost, s));
-    chk(cudaMemcpyAsync(&unsorted, d_unsorted, 4, cudaMemcpyDeviceToHost, s));
-    chk(cudaStreamSynchronize(s));
-    if (e == cudaSuccess && unsorted) {
-      free_blocked(h);
-      return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
-    }
-    const uint64_t alloc = tot + 16;
-    chk(dalloc(&h->d_belem, alloc));
-    if (e == cudaSuccess) {
-      uint32_t nbmax = 1;
-      for (uint32_t r = 0; r < h->n_inst; ++r) nbmax = std::max(nbmax, h->inst[r].nb);
-      const size_t shm = fill_smem_bytes(nbmax);
-      if (shm > 48 * 1024)
-        chk(cudaFuncSetAttribute(bfill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      bfill_kernel<<<dim3(nbt, kBThreads / kFillThreads), kFillThreads, shm, s>>>(
-          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->d_bwlen, h->d_bcnt, h->row_ptr,
-          h->col, h->d_belem, nbmax);
-      chk(cudaGetLastError());
-      chk(cudaStreamSynchronize(s));
-    }
-  } else {
-    chk(stage_h2d(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc), s));
-    chk(cudaStreamSynchronize(s));
-  }
+  const uint64_t nw = nseg * 32;
+  chk(dalloc(&h->d_btile_inst, nbt));
+  chk(dalloc(&h->d_bseg_base, nbt));
+  chk(dalloc(&h->d_bwstart, nw + 1));
+  chk(dalloc(&h->d_bwlen, nw + 1));  // + the sortedness flag of the count pass
+  chk(dalloc(&h->d_bcnt, nseg * kBThreads));
+  chk(dalloc(&h->d_bwscan, nw / 4096 + 2));  // prefix scratch
+  bb.result = reinterpret_cast<uint64_t *>(stage_reserve(16));
+  if (e == cudaSuccess && !bb.result) e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     free_blocked(h);
-    return cuda_error(e, "blocked format: build");
+    return cuda_error(e, "blocked format: allocate");
+  }
+  chk(stage_h2d(h->d_btile_inst, btile_inst.data(), nbt * 4, s));
+  chk(stage_h2d(h->d_bseg_base, bseg_base.data(), nbt * 8, s));
+  chk(stage_h2d(h->d_inst, h->inst.data(), h->n_inst * sizeof(InstDesc), s));
+  // no temporary allocation here: a free synchronises the device, which
+  // would stall an upload behind another thread's kernels
+  uint32_t *d_unsorted = h->d_bwlen + nw;
+  if (e == cudaSuccess) chk(cudaMemsetAsync(d_unsorted, 0, 4, s));
+  // count each group of realisations as soon as its columns are on the device
+  uint32_t r_begin = 0;
+  for (const CopyGroup &g : groups) {
+    chk(cudaStreamWaitEvent(s, g.ev, 0));
+    const uint32_t t0 = h->inst[r_begin].btile_base;
+    const uint32_t t1 = h->inst[g.r_end - 1].btile_base + h->inst[g.r_end - 1].n_btiles;
+    if (t1 > t0 && e == cudaSuccess)
+      bcount_kernel<<<dim3(t1 - t0, kBThreads / kFillThreads), kFillThreads, 0, s>>>(
+          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->row_ptr, h->col, h->d_bwlen, h->d_bcnt,
+          d_unsorted, t0);
+    r_begin = g.r_end;
+  }
+  chk(cudaGetLastError());
+  // stream offsets on the device: bwstart = 32 x the exclusive prefix of
+  // the lengths; only the total and the sortedness flag come back
+  if (e == cudaSuccess) chk(exclusive_scan(h->d_bwlen, nw, h->d_bwstart, h->d_bwscan, s));
+  if (e == cudaSuccess)
+    times32_kernel<<<(uint32_t)((nw + 1 + 255) / 256), 256, 0, s>>>(h->d_bwstart, nw + 1);
+  bb.result[0] = 0;
+  bb.result[1] = 0;
+  chk(cudaMemcpyAsync(bb.result, h->d_bwstart + nw, 8, cudaMemcpyDeviceToHost, s));
+  chk(cudaMemcpyAsync(bb.result + 1, d_unsorted, 4, cudaMemcpyDeviceToHost, s));
+  chk(cudaEventCreateWithFlags(&bb.ev, cudaEventDisableTiming));
+  if (e == cudaSuccess) chk(cudaEventRecord(bb.ev, s));
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    free_blocked(h);
+    return cuda_error(e, "blocked format: count");
+  }
+  return CB_OK;
+}
+
+int blocked_fill(cb_graph *h, cudaStream_t s, BlockedBuild &bb) {
+  NvtxRange nvtx_range("column-blocked format: fill");
+  if (h->csr_only || !h->total_btiles) return CB_OK;
+  cudaError_t e = cudaEventSynchronize(bb.ev);
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  if (e == cudaSuccess && bb.result[1]) {
+    free_blocked(h);
+    return set_error(CB_ERR_ARG, "cb_graph_upload: column indices of every row must be sorted ascending");
+  }
+  const uint64_t alloc = bb.result[0] + 16;
+  chk(dalloc(&h->d_belem, alloc));
+  if (e == cudaSuccess) {
+    uint32_t nbmax = 1;
+    for (uint32_t r = 0; r < h->n_inst; ++r) nbmax = std::max(nbmax, h->inst[r].nb);
+    const size_t shm = fill_smem_bytes(nbmax);
+    if (shm > 48 * 1024)
+      chk(cudaFuncSetAttribute(bfill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    if (e == cudaSuccess)
+      bfill_kernel<<<dim3(h->total_btiles, kBThreads / kFillThreads), kFillThreads, shm, s>>>(
+          h->d_inst, h->d_btile_inst, h->d_bseg_base, h->d_bwstart, h->d_bwlen, h->d_bcnt,
+          h->row_ptr, h->col, h->d_belem, nbmax);
+    chk(cudaGetLastError());
+  }
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    free_blocked(h);
+    return cuda_error(e, "blocked format: fill");
+  }
+  return CB_OK;
+}
+
+int blocked_long_rows(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s) {
+  NvtxRange nvtx_range("column-blocked format: long rows");
+  if (h->csr_only || !h->total_btiles) return CB_OK;
+  // long rows per tile (tile-local indices), scanned in parallel over realisations
+  std::vector<std::vector<uint32_t>> lrows(h->n_inst), lcount(h->n_inst);
+  parallel_for(h->n_inst, [&](uint32_t r) {
+    const InstDesc &I = h->inst[r];
+    const uint32_t *rp = rp_host[r];
+    for (uint32_t q = 0; q < I.n_btiles; ++q) {
+      const uint32_t row0 = q * kBTileRows, row1 = std::min<uint32_t>(row0 + kBTileRows, I.n);
+      uint32_t c = 0;
+      for (uint32_t row = row0; row < row1; ++row)
+        if (rp[row + 1] - rp[row] > kBLongDeg) {
+          lrows[r].push_back(row - row0);
+          ++c;
+        }
+      lcount[r].push_back(c);
+    }
+  });
+  std::vector<uint32_t> long_ptr(1, 0), long_rows;
+  for (uint32_t r = 0; r < h->n_inst; ++r) {
+    for (uint32_t c : lcount[r]) long_ptr.push_back(long_ptr.back() + c);
+    long_rows.insert(long_rows.end(), lrows[r].begin(), lrows[r].end());
+  }
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(dalloc(&h->d_blong_ptr, long_ptr.size()));
+  chk(dalloc(&h->d_blong_rows, std::max<size_t>(long_rows.size(), 1)));
+  chk(stage_h2d(h->d_blong_ptr, long_ptr.data(), long_ptr.size() * 4, s));
+  if (!long_rows.empty()) chk(stage_h2d(h->d_blong_rows, long_rows.data(), long_rows.size() * 4, s));
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    free_blocked(h);
+    return cuda_error(e, "blocked format: long rows");
   }
   return CB_OK;
 }

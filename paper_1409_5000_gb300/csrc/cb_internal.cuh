@@ -329,6 +329,9 @@ void parallel_for(uint32_t n, const std::function<void(uint32_t)> &fn);
 // copies keep busy for the whole transfer, and hold the host thread with it.
 // The staging buffer is recycled when the upload returns (cb_api.cu).
 cudaError_t stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// A pinned host block of `bytes` from the same staging arena, valid until
+// the upload returns (nullptr if pinned memory cannot be had).
+char *stage_reserve(size_t bytes);
 
 // error plumbing (cb_api.cu)
 // Device memory of handles and workspaces.  By default it comes from a
@@ -390,8 +393,26 @@ struct CopyGroup {
 // out[0..n], out[n] = total; bsum holds n / 4096 + 2 u64 of scratch.
 cudaError_t exclusive_scan(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *bsum,
                            cudaStream_t s);
-int build_blocked(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
-                  const std::vector<CopyGroup> &groups);
+// Column-blocked format builder (cb_blocked.cu), in three calls so that an
+// upload's host work runs while the device builds the format:
+//   blocked_count -- layout from the realisation sizes, the count pass (per
+//     copy group, as its columns land) and the stream prefix, all queued;
+//   blocked_fill  -- waits for the stream total, allocates the streams and
+//     queues the fill pass (no wait for it);
+//   blocked_long_rows -- the rows summed from the CSR, from host row_ptr.
+// h->d_inst must be allocated before blocked_count; the caller synchronises
+// the stream before the handle is used.
+struct BlockedBuild {
+  uint64_t *result = nullptr;  // pinned: stream total, then the sortedness flag
+  cudaEvent_t ev = nullptr;    // recorded after the count pass and its prefix
+  ~BlockedBuild() {
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+int blocked_count(cb_graph *h, cudaStream_t s, const std::vector<CopyGroup> &groups,
+                  BlockedBuild &bb);
+int blocked_fill(cb_graph *h, cudaStream_t s, BlockedBuild &bb);
+int blocked_long_rows(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s);
 void free_blocked(cb_graph *h);
 // two-phase format builder (cb_twophase.cu); force: every realisation, else
 // those above the column-blocked size limit
