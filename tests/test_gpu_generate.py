@@ -29,7 +29,8 @@ def _cpu(n, dbar, seed, tedges):
             for r, x in enumerate(n)]
 
 
-@pytest.mark.parametrize("case", ["small", "uneven", "no_target", "dense", "very_dense", "huge_rows"])
+@pytest.mark.parametrize("case", ["small", "uneven", "no_target", "dense", "very_dense", "huge_rows",
+                                  "tiny"])
 def test_generated_csr_matches_cpu_definition(B, case):
     if case == "small":
         n, dbar, tedges = [500] * 10, 3.2, synth.target_edges(np.arange(15, dtype=np.uint32) * 7, 8, False, 3)
@@ -41,8 +42,11 @@ def test_generated_csr_matches_cpu_definition(B, case):
         n, dbar, tedges = [64, 64, 64], 40.0, [(1, 2)]
     elif case == "very_dense":  # rows of > 64 raw entries: sorted by a CTA in shared memory
         n, dbar, tedges = [64, 96], 200.0, [(1, 2)]
-    else:  # rows of > 32768 raw entries keep the serial sort (one repeated pair)
+    elif case == "huge_rows":  # rows of > 32768 raw entries keep the serial sort (one repeated pair)
         n, dbar, tedges = [2], 33_500.0, None
+    else:  # one-node realisations (every draw a self-loop, the target edge out of range),
+        # realisations shorter than a warp's 32 rows, several per chunk of draws
+        n, dbar, tedges = [1, 37, 2, 1000, 1, 64], 3.0, [(0, 1), (3, 36)]
     seed = synth.seed_for(901, 0)
     ref = _cpu(n, dbar, seed, tedges)
     gs = B.GraphSet.generate_er(n, dbar, seed, tedges)
