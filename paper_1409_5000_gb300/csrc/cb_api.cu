@@ -234,8 +234,10 @@ void free_workspace(Workspace &W) {
 }
 
 static void free_graph_arrays(cb_graph *h) {
-  dev_free(h->col);
-  dev_free(h->row_ptr);
+  if (h->owns_csr) {
+    dev_free(h->col);
+    dev_free(h->row_ptr);
+  }
   dev_free(h->d_inst);
   dev_free(h->d_tile_inst);
   dev_free(h->d_tile_rows);
@@ -551,10 +553,11 @@ cudaError_t cb::stage_h2d(void *dst, const void *src, size_t bytes, cudaStream_t
   return cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, s);
 }
 
-CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
-                           const uint32_t *const *row_ptr, const uint32_t *const *col,
-                           uint32_t flags, void *stream, cb_graph **out) {
-  NvtxRange nvtx_range("cb_graph_upload");
+// own_col / own_rp: device arrays taken over instead of copied (upload_adopt)
+static int upload_impl(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
+                       const uint32_t *const *row_ptr, const uint32_t *const *col,
+                       uint32_t flags, void *stream, cb_graph **out, uint32_t *own_col,
+                       uint32_t *own_rp) {
   if (!out) return set_error(CB_ERR_ARG, "cb_graph_upload: out is null");
   *out = nullptr;
   if (n_inst == 0 || !n || !nnz || !row_ptr || !col)
@@ -656,12 +659,27 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
   auto chk = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
-  chk(dalloc(&h->col, edge_off + 4));
-  chk(dalloc(&h->row_ptr, rp_off));
+  const bool adopt = own_col != nullptr;
+  if (adopt) {  // the arrays are the handle's layout already: no copy
+    for (uint32_t r = 0; r < n_inst; ++r)
+      if (row_ptr[r] != own_rp + h->inst[r].rp_base || (nnz[r] && col[r] != own_col + h->inst[r].edge_base)) {
+        delete h;
+        return set_error(CB_ERR_ARG, "cb_graph_upload: adopted arrays are not concatenated in order");
+      }
+    h->col = own_col;
+    h->row_ptr = own_rp;
+    h->owns_csr = false;
+  } else {
+    chk(dalloc(&h->col, edge_off + 4));
+    chk(dalloc(&h->row_ptr, rp_off));
+  }
   chk(dalloc(&h->d_inst, n_inst));
   UploadCopies cp;
   chk(cp.start(s));
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && adopt) {
+    chk(cudaMemsetAsync(h->col + edge_off, 0, 16, cp.stream));
+    chk(cp.mark(n_inst));
+  } else if (e == cudaSuccess) {
     const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     chk(cudaMemsetAsync(h->col + edge_off, 0, 16, cp.stream));
     const uint64_t per_group = edge_off / kCopyGroups + 1;
@@ -828,8 +846,24 @@ CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *n
     delete h;
     return rc;
   }
+  h->owns_csr = true;
   *out = h;
   return CB_OK;
+}
+
+CB_API int cb_graph_upload(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
+                           const uint32_t *const *row_ptr, const uint32_t *const *col,
+                           uint32_t flags, void *stream, cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_upload");
+  return upload_impl(n_inst, n, nnz, row_ptr, col, flags, stream, out, nullptr, nullptr);
+}
+
+int cb::upload_adopt(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
+                     const uint32_t *const *row_ptr, const uint32_t *const *col,
+                     uint32_t *col_all, uint32_t *rp_all, void *stream, cb_graph **out) {
+  NvtxRange nvtx_range("cb_graph_upload (adopted arrays)");
+  if (!col_all || !rp_all) return set_error(CB_ERR_ARG, "cb_graph_upload: null adopted array");
+  return upload_impl(n_inst, n, nnz, row_ptr, col, CB_DEVICE_PTRS, stream, out, col_all, rp_all);
 }
 
 static void drop_graphs(cb_graph *h) {

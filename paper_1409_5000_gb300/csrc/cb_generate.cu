@@ -590,6 +590,9 @@ struct GenBuffers {
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
+  void release(void *p) {  // p now belongs to someone else
+    ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), p), ptrs.end());
+  }
   ~GenBuffers() {
     for (void *p : ptrs) dev_free(p);
   }
@@ -708,7 +711,7 @@ static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const u
     if (nnz[r] >= 0xffffffffull)
       return fail("a realisation has >= 2^32 entries");
   }
-  chk(B.alloc(&col, std::max<uint64_t>(hb[n_inst], 1)));
+  chk(B.alloc(&col, hb[n_inst] + 4));  // + the 16 zero bytes the handle keeps after the columns
   chk(B.alloc(&rp, rows + n_inst));
   if (e != cudaSuccess) return cuda_error(e, (std::string(who) + ": allocate CSR").c_str());
   gen_compact_kernel<<<(uint32_t)chunk_grid(rows, kRowsPerCta), kGenThreads, 0, s>>>(
@@ -721,10 +724,14 @@ static int generate(const GenArgs &kp, const char *who, uint32_t n_inst, const u
     rpp[r] = rp + node_off[r] + r;
     colp[r] = col + hb[r];
   }
-  // the upload copies the arrays (device to device) and builds the tables;
-  // the temporaries are freed when B goes out of scope
-  return cb_graph_upload(n_inst, n, nnz.data(), rpp.data(), colp.data(), CB_DEVICE_PTRS, stream,
-                         out);
+  // the handle takes col and rp over (they are laid out as its own arrays)
+  // and builds its tables; the temporaries are freed when B goes out of scope
+  const int rc = upload_adopt(n_inst, n, nnz.data(), rpp.data(), colp.data(), col, rp, stream, out);
+  if (rc == CB_OK) {
+    B.release(col);
+    B.release(rp);
+  }
+  return rc;
 }
 
 static int check_common(const char *who, uint32_t n_inst, const uint32_t *n, uint32_t n_tedges,

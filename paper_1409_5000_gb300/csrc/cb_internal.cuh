@@ -184,6 +184,7 @@ struct cb_graph {
   int lanes = 8;  // lanes per row for short rows (1, 2, 4, 8, 16, 32)
   int path = CB_PATH_AUTO;  // FP32 SpMV path (cb_graph_set_path)
   uint32_t n_sm = 1;        // SMs of the handle's device
+  bool owns_csr = true;     // false while an upload holds CSR arrays its caller still owns
   std::vector<cb::InstDesc> inst;        // host copy
   std::vector<cb::HeavyRow> heavy;       // host copy
   // device arrays
@@ -416,6 +417,14 @@ int blocked_long_rows(cb_graph *h, const std::vector<const uint32_t *> &rp_host,
 void free_blocked(cb_graph *h);
 // two-phase format builder (cb_twophase.cu); force: every realisation, else
 // those above the column-blocked size limit
+// cb_graph_upload from device arrays that the handle takes over instead of
+// copying (cb_api.cu): col_all holds the realisations' columns concatenated
+// (sum of nnz + 4 entries), rp_all their row_ptr arrays concatenated (sum of
+// n + 1 entries), and row_ptr[r] / col[r] point into them at those offsets.
+// On success the handle owns both; on failure the caller still does.
+int upload_adopt(uint32_t n_inst, const uint32_t *n, const uint64_t *nnz,
+                 const uint32_t *const *row_ptr, const uint32_t *const *col, uint32_t *col_all,
+                 uint32_t *rp_all, void *stream, cb_graph **out);
 int build_twophase(cb_graph *h, const std::vector<const uint32_t *> &rp_host, cudaStream_t s,
                    const std::vector<CopyGroup> &groups, bool force);
 void free_twophase(cb_graph *h);
